@@ -1,0 +1,268 @@
+/*
+ * spx.h -- C ABI of the GB300 (sm_103a) spectral/hp element operator library.
+ *
+ * The library evaluates, over every element of a quadrilateral (2D) or
+ * hexahedral (3D) mesh at once, the elemental operators of the spectral/hp
+ * element method of arXiv 1906.03489 (Nektar++ 5.0): BwdTrans,
+ * IProductWRTBase, PhysDeriv and the Helmholtz operator H = lambda M + L,
+ * with the modified C0 basis (§2.1) on Gauss-Lobatto-Legendre points, by
+ * sum-factorisation (§3.3) in hand-written CUDA kernels; plus the adjoint of H
+ * with respect to its coefficient fields, periodic C0 assembly and a
+ * Jacobi-preconditioned CG solver (§2.1, implicit-type methods).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Only plain C types cross the ABI.  "device" pointers are CUDA device
+ *   memory of the current device; "host" pointers are ordinary host memory.
+ * - Ownership: the caller owns every data buffer.  The library never frees a
+ *   caller pointer and allocates no buffer of the size of a field; a plan owns
+ *   only small metadata (per-element offsets and a work list, O(E) words).
+ * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  All device work is enqueued on it and the call returns without
+ *   synchronising, unless stated otherwise.
+ * - Errors: every call returns an spx_status; on any status other than SPX_OK,
+ *   spx_last_error() returns a message for the calling thread.  Arguments are
+ *   validated before anything is launched; nothing is launched on error.
+ * - Layouts (element-major, FP64 or FP32 as selected by spx_dtype):
+ *     coefficients  element e at coef_off[e], n^d values (n = P_e + 1),
+ *                   mode index p + n (q + n r) (p along xi_1 fastest);
+ *     quad values   element e at quad_off[e], Q^d values,
+ *                   point index i + Q (j + Q k);
+ *     geometry      element e at nf * quad_off[e], nf blocks of Q^d values:
+ *                   3D nf = 7: G11 G12 G13 G22 G23 G33 JW,
+ *                   2D nf = 4: G11 G12 G22 JW,
+ *                   with JW = w_i w_j w_k det J and
+ *                   G_ab = JW * sum_m (dxi_a/dx_m)(dxi_b/dx_m);
+ *     dxi_dx        element e at d*d*quad_off[e], d*d blocks of Q^d values,
+ *                   block a*d + m holds dxi_a/dx_m;
+ *     nodes         element e at d*coef_off[e], d blocks of n^d values (the
+ *                   x, y(, z) coordinates of the element's GLL nodes, node
+ *                   index as the mode index).
+ *   Here P_e is the element's polynomial order, Q_e = P_e + q_offset its
+ *   number of GLL points per direction; coef_off / quad_off are the running
+ *   sums of n^d and Q^d (see spx_plan_offsets).
+ * - Supported orders: 1 <= P <= 8, q_offset in {1, 2}; 2D and 3D.
+ *   Variable order (per-element P) is supported by every operator.
+ * - Device buffers must be aligned to their element size; 16-byte alignment
+ *   (every torch / cudaMalloc allocation) gives the fastest path.
+ */
+#ifndef SPX_H
+#define SPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPX_OK = 0,
+  SPX_ERR_INVALID_ARG = 1,   /* a NULL, out-of-range or inconsistent argument */
+  SPX_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement */
+  SPX_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+  SPX_ERR_NOT_CONVERGED = 4, /* iteration limit reached before the tolerance */
+  SPX_ERR_NONFINITE = 5,     /* NaN or Inf met in a residual */
+  SPX_ERR_NO_MEMORY = 6,     /* host allocation or caller workspace too small */
+  SPX_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up */
+} spx_status;
+
+typedef enum { SPX_F64 = 0, SPX_F32 = 1 } spx_dtype;
+
+/* Operator identifiers for spx_autotune / spx_plan_set_tile. */
+typedef enum {
+  SPX_OP_BWD_TRANS = 0,
+  SPX_OP_IPRODUCT = 1,
+  SPX_OP_PHYS_DERIV = 2,
+  SPX_OP_HELMHOLTZ = 3,
+  SPX_OP_COUNT = 4
+} spx_op;
+
+typedef struct spx_plan spx_plan;
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char *spx_last_error(void);
+
+/* Library version string. */
+const char *spx_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Basis tables (§2.1 modified basis display; §3.5 Listing lst:python GLL
+ * points).  Host FP64, any output may be NULL:
+ *   xi[Q], w[Q]    GLL points (ascending) and weights on [-1, 1];
+ *   B[Q][P+1]      B[i][p] = phi_p(xi_i), phi_0 = (1-x)/2, phi_P = (1+x)/2,
+ *                  phi_p = (1-x)/2 (1+x)/2 P^{1,1}_{p-1}(x) for 0 < p < P
+ *                  (Jacobi polynomial in the standard normalisation);
+ *   dB[Q][P+1]     dB[i][p] = phi_p'(xi_i);
+ *   D[Q][Q]        D[i][j] = l_j'(xi_i), the collocation derivative of the
+ *                  Lagrange interpolant through the GLL points.
+ * Row-major, first index slowest.  Requires 1 <= P, 2 <= Q <= 16.
+ * ------------------------------------------------------------------------- */
+spx_status spx_basis_tables(int P, int Q, double *xi, double *w, double *B, double *dB, double *D);
+
+/* ---------------------------------------------------------------------------
+ * Plans: the mesh's element count, dimension and per-element orders
+ * (Collections groups of same-shape, same-basis elements, §3.3; variable
+ * order per element, §4.2).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int dim;                    /* 2 or 3 */
+  int64_t n_elem;             /* E >= 0 */
+  const int32_t *elem_order;  /* host [E] orders P_e, or NULL for uniform order */
+  int uniform_order;          /* P for every element when elem_order == NULL */
+  int q_offset;               /* Q_e = P_e + q_offset; 1 or 2 (0 selects 2) */
+} spx_plan_desc;
+
+/* Creates a plan (copies the orders; builds offsets and the launch work
+ * list on the current device).  *out receives the plan. */
+spx_status spx_plan_create(spx_plan **out, const spx_plan_desc *desc);
+/* Frees a plan (NULL is accepted). */
+spx_status spx_plan_destroy(spx_plan *plan);
+/* Total coefficient and quadrature-point counts (sum n^d, sum Q^d). */
+spx_status spx_plan_sizes(const spx_plan *plan, int64_t *n_coef, int64_t *n_quad);
+/* Host copies of the offsets, each of length E+1 (either may be NULL). */
+spx_status spx_plan_offsets(const spx_plan *plan, int64_t *coef_off, int64_t *quad_off);
+
+/* Reads the plan's device status word (synchronises the device): bit 0 set
+ * means a kernel of this plan gave up a bounded wait for its input copies and
+ * left its outputs incomplete; bit 1 means an index argument was out of
+ * range.  reset != 0 clears the word afterwards. */
+spx_status spx_plan_device_status(spx_plan *plan, int *status, int reset);
+
+/* Registers caller-owned geometry buffers (device, layout above) for one
+ * precision.  geom is required by IProduct, Helmholtz and the adjoint,
+ * dxi_dx by PhysDeriv; either may be NULL if the operator is not used.
+ * The plan keeps the pointers, not the data: the buffers must stay alive
+ * and unchanged while operators run. */
+spx_status spx_plan_set_geometry(spx_plan *plan, spx_dtype dtype, const void *geom, const void *dxi_dx);
+
+/* Overrides the launch tile of one operator/precision/order: elements per
+ * batch `eb` (1..64), threads per block `nthreads` (32..1024, multiple of
+ * 32) and pipeline depth `stages` (1..4).  order = -1 sets every order. */
+spx_status spx_plan_set_tile(spx_plan *plan, spx_op op, spx_dtype dtype, int order, int eb, int nthreads,
+                             int stages);
+
+/* Times the candidate tiles of `op` for every order present in the plan on
+ * the given buffers (device, sized for the operator's input and output; for
+ * PhysDeriv `out` holds the d outputs one after another) and
+ * keeps the fastest per order.  Synchronises the stream.  `reps` timed runs
+ * per candidate (>= 1).  Autotuning at start-up, §3.3 (COLLECTIONS auto). */
+spx_status spx_autotune(spx_plan *plan, spx_op op, spx_dtype dtype, const void *in, void *out, int reps,
+                        void *stream);
+
+/* Reads back the tile chosen for (op, dtype, order). */
+spx_status spx_plan_get_tile(const spx_plan *plan, spx_op op, spx_dtype dtype, int order, int *eb,
+                             int *nthreads, int *stages);
+
+/* ---------------------------------------------------------------------------
+ * Geometry (§2.1 mapping paragraph): iso-parametric map chi_e given by the
+ * element's nodal coordinates at its (P+1)^d GLL nodes.  FP64 kernel computing,
+ * at every quadrature point, J = dx/dxi of the nodal interpolant, det J,
+ * J^{-1} and the folded factors of the layout above.
+ *   nodes   device FP64 in  (layout above)
+ *   geom    device FP64 out [nf * n_quad]          (may be NULL)
+ *   dxi_dx  device FP64 out [d * d * n_quad]       (may be NULL)
+ *   xq      device FP64 out [d * n_quad], physical coordinates of the
+ *           quadrature points, block m = coordinate x_m   (may be NULL)
+ *   geom32  device FP32 out, FP32 copy of geom      (may be NULL)
+ *   dxi32   device FP32 out, FP32 copy of dxi_dx    (may be NULL)
+ * ------------------------------------------------------------------------- */
+spx_status spx_geom_factors(const spx_plan *plan, const double *nodes, double *geom, double *dxi_dx, double *xq,
+                            float *geom32, float *dxi32, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Elemental operators, all elements at once (Collections SumFac, §3.3).
+ * dtype selects FP64 or FP32 buffers, arithmetic and registered geometry.
+ * ------------------------------------------------------------------------- */
+
+/* BwdTrans (§3.3 interpolation display): u_ijk = sum_pqr B_ip B_jq B_kr c_pqr.
+ * coef: device in [n_coef]; phys: device out [n_quad]. */
+spx_status spx_bwd_trans(const spx_plan *plan, spx_dtype dtype, const void *coef, void *phys, void *stream);
+
+/* IProductWRTBase (§3.3, inner products): y_pqr = sum_ijk B_ip B_jq B_kr JW_ijk f_ijk.
+ * phys: device in [n_quad]; coef: device out [n_coef].  Needs geom. */
+spx_status spx_iproduct(const spx_plan *plan, spx_dtype dtype, const void *phys, void *coef, void *stream);
+
+/* PhysDeriv (§2.1, StdRegions differentiation composed with chi_e):
+ * du/dx_m = sum_a (dxi_a/dx_m) D_a u at the quadrature points.
+ * phys: device in [n_quad]; d0, d1 (, d2 in 3D; NULL in 2D): device out
+ * [n_quad] each.  Needs dxi_dx. */
+spx_status spx_phys_deriv(const spx_plan *plan, spx_dtype dtype, const void *phys, void *d0, void *d1, void *d2,
+                          void *stream);
+
+/* Helmholtz operator (eq. e:bilinear with a(u,v) = int lambda u v +
+ * kappa grad u . grad v; eq. eq:filtereq is lambda = 1): per element,
+ * unassembled, y_e = (M_e(lambda) + L_e(kappa)) u_e.
+ *   lambda        constant reaction coefficient, used when lambda_field is NULL;
+ *   lambda_field  device [n_quad] per-point lambda(x) or NULL;
+ *   kappa_field   device [n_quad] per-point kappa(x) or NULL (kappa = 1);
+ *   coef_in       device in [n_coef]; coef_out: device out [n_coef]
+ *                 (must not alias coef_in).
+ * Fields have the dtype of the call.  Needs geom. */
+spx_status spx_helmholtz(const spx_plan *plan, spx_dtype dtype, double lambda, const void *lambda_field,
+                         const void *kappa_field, const void *coef_in, void *coef_out, void *stream);
+
+/* Adjoint of the Helmholtz operator with respect to its coefficient fields
+ * (FP64).  For the loss 0.5 ||H(lambda,kappa) u - f||^2 with r = H u - f
+ * passed as g:
+ *   grad_lambda[q] = JW_q (B g)_q (B u)_q
+ *   grad_kappa[q]  = sum_ab G_ab,q (d_a g)_q (d_b u)_q
+ * (d_a = derivative along xi_a of the expansion).  The gradient with respect
+ * to u is H g, i.e. spx_helmholtz applied to g (H is symmetric).
+ * u, g: device [n_coef]; grad_lambda, grad_kappa: device out [n_quad], either
+ * may be NULL.  BwdTrans of u and g is recomputed, nothing is stored by the
+ * forward call.  Needs FP64 geom. */
+spx_status spx_helmholtz_adjoint(const spx_plan *plan, const double *u, const double *g, double *grad_lambda,
+                                 double *grad_kappa, void *stream);
+
+/* Diagonal of the elemental Helmholtz matrices, diag(H_e)_l for every local
+ * mode (the Jacobi preconditioner before assembly).  out: device [n_coef]. */
+spx_status spx_helmholtz_diag(const spx_plan *plan, spx_dtype dtype, double lambda, void *out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * C0 assembly (§2.1 assembly paragraph) and the linear solve.
+ * l2g: device int32 [n_coef], global index of every local mode.
+ * ------------------------------------------------------------------------- */
+
+/* local[l] = global[l2g[l]] (dtype of the buffers); global has n_global
+ * entries.  An entry of l2g outside [0, n_global) reads nothing, writes 0 and
+ * sets bit 1 (value 2) of the plan's device status word. */
+spx_status spx_gather(const spx_plan *plan, spx_dtype dtype, const int32_t *l2g, int64_t n_global,
+                      const void *global, void *local, void *stream);
+
+/* Options of spx_cg_solve. */
+typedef struct {
+  double tol;        /* relative residual ||f - A x||_2 / ||f||_2 to reach (e.g. 1e-10) */
+  int maxit;         /* iteration cap of the FP64 CG, or of each inner FP32 solve */
+  int precision;     /* 0 = all-FP64 CG; 1 = FP32 inner CG inside FP64 refinement */
+  double inner_tol;  /* relative tolerance of each inner FP32 solve (precision 1) */
+  int max_outer;     /* cap on refinement steps (precision 1) */
+  int use_graph;     /* 1: capture the iteration in a CUDA graph */
+  int check_every;   /* iterations between host-side convergence checks (>= 1) */
+} spx_cg_opts;
+
+typedef struct {
+  int iters;            /* total CG iterations (inner iterations for precision 1) */
+  int outer_iters;      /* refinement steps (precision 1), else 0 */
+  double rel_residual;  /* final ||f - A x||_2 / ||f||_2 computed in FP64 */
+} spx_cg_result;
+
+/* Workspace bytes spx_cg_solve needs for this plan and n_global. */
+spx_status spx_cg_workspace_bytes(const spx_plan *plan, int64_t n_global, const spx_cg_opts *opts, size_t *bytes);
+
+/* Solves A x = f with A = sum_e R_e^T H_e(lambda) R_e (assembled through
+ * l2g) by Jacobi-preconditioned CG.  f: device FP64 [n_global]; x: device
+ * FP64 [n_global], initial guess in, solution out.  workspace: device,
+ * >= spx_cg_workspace_bytes, 256-byte aligned.  Needs geometry for FP64
+ * (and FP32 when precision = 1).  Synchronises the stream (it reads residual
+ * norms on the host).  Returns SPX_ERR_NOT_CONVERGED with `result` filled if
+ * the caps are reached, SPX_ERR_NONFINITE on a NaN/Inf residual. */
+spx_status spx_cg_solve(const spx_plan *plan, double lambda, const int32_t *l2g, int64_t n_global, const double *f,
+                        double *x, void *workspace, size_t workspace_bytes, const spx_cg_opts *opts,
+                        spx_cg_result *result, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPX_H */

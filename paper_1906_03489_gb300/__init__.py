@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) spectral/hp element operators of arXiv 1906.03489.
+
+BwdTrans, IProductWRTBase, PhysDeriv and the Helmholtz operator H = lambda M + L
+evaluated over all elements of quad/hex meshes by sum-factorised CUDA kernels
+behind a C ABI (include/spx.h); adjoint of H with respect to its coefficient
+fields behind ``torch.autograd``; periodic C0 assembly and a mixed-precision
+Jacobi-PCG solver.
+"""
+from ._lib import SpxError, lib  # noqa: F401
+from .binding import (Plan, basis_tables, bwd_trans, cg_solve, cg_workspace_bytes, gather,  # noqa: F401
+                      geom_factors, helmholtz, helmholtz_adjoint, helmholtz_diag, iproduct, phys_deriv)

@@ -1,0 +1,445 @@
+// C ABI of the spx library: plans, tiles, operator dispatch, autotuning.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "smem_layout.h"
+#include "spx_internal.h"
+
+namespace spx {
+
+static thread_local std::string g_last_error;
+
+spx_status fail(spx_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+spx_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SPX_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static bool op_needs_geom(int op) { return op != OP_BWD; }
+
+static int default_eb(int dim, int Q) {
+  const int per = dim == 3 ? Q * Q : Q;
+  return std::max(1, std::min(kMaxEB, 256 / per));
+}
+
+size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& cfg) {
+  // worst case: coefficient fields present
+  return smem_layout(plan, op, dtype == 0 ? 8 : 4, cfg, true, true).total;
+}
+
+spx_status ensure_tiles(spx_plan* plan, int op, int dtype) {
+  TileList& tl = plan->tiles[op][dtype];
+  if (!tl.dirty) return SPX_OK;
+  const LaunchCfg& cfg = plan->cfg[op][dtype];
+  std::vector<Tile> tiles;
+  if (plan->uniform) {
+    const int eb = cfg.order[plan->uP].eb;
+    for (int64_t e0 = 0; e0 < plan->E; e0 += eb)
+      tiles.push_back(Tile{plan->uP, static_cast<int32_t>(std::min<int64_t>(eb, plan->E - e0)),
+                           static_cast<int32_t>(e0), 1});
+  } else {
+    // heaviest orders first: round-robin assignment then balances the CTAs
+    for (int P = kMaxP; P >= 1; --P) {
+      if (!plan->present[P]) continue;
+      const int eb = cfg.order[P].eb;
+      const int64_t b0 = plan->bucket_start[P], b1 = plan->bucket_start[P + 1];
+      for (int64_t s = b0; s < b1; s += eb) {
+        const int cnt = static_cast<int>(std::min<int64_t>(eb, b1 - s));
+        bool contig = true;
+        for (int j = 1; j < cnt; ++j)
+          if (plan->ids[s + j] != plan->ids[s] + j) contig = false;
+        tiles.push_back(Tile{P, cnt, static_cast<int32_t>(s), contig ? 1 : 0});
+      }
+    }
+  }
+  if (tl.d) cudaFree(tl.d);
+  tl.d = nullptr;
+  tl.n = static_cast<int>(tiles.size());
+  if (tl.n) {
+    cudaError_t e = cudaMalloc(&tl.d, tiles.size() * sizeof(Tile));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tiles)");
+    e = cudaMemcpy(tl.d, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tiles)");
+  }
+  tl.dirty = false;
+  return SPX_OK;
+}
+
+spx_status launch_op(const LaunchReq& r) {
+  const int key = r.dtype * 100 + r.plan->dim * 10 + r.op;
+  switch (key) {
+#define SPX_CASE(DT, TN, DIM, OP) \
+  case DT * 100 + DIM * 10 + OP: return launch_##TN##_##DIM##_##OP(r);
+#define SPX_CASES(DT, TN, DIM) \
+  SPX_CASE(DT, TN, DIM, 0) SPX_CASE(DT, TN, DIM, 1) SPX_CASE(DT, TN, DIM, 2) \
+  SPX_CASE(DT, TN, DIM, 3) SPX_CASE(DT, TN, DIM, 4) SPX_CASE(DT, TN, DIM, 5)
+    SPX_CASES(0, f64, 2)
+    SPX_CASES(0, f64, 3)
+    SPX_CASES(1, f32, 2)
+    SPX_CASES(1, f32, 3)
+#undef SPX_CASES
+#undef SPX_CASE
+    default: return fail(SPX_ERR_UNSUPPORTED, "no kernel for this operator");
+  }
+}
+
+}  // namespace spx
+
+using namespace spx;
+
+extern "C" {
+
+const char* spx_last_error(void) { return g_last_error.c_str(); }
+
+const char* spx_version(void) { return "spx 0.1 (sm_103a)"; }
+
+spx_status spx_basis_tables(int P, int Q, double* xi, double* w, double* B, double* dB, double* D) {
+  return basis_tables(P, Q, xi, w, B, dB, D);
+}
+
+spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
+  if (!out || !d) return fail(SPX_ERR_INVALID_ARG, "plan_create: NULL argument");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(SPX_ERR_INVALID_ARG, "plan_create: dim must be 2 or 3");
+  if (d->n_elem < 0 || d->n_elem > (int64_t(1) << 31) - 1)
+    return fail(SPX_ERR_INVALID_ARG, "plan_create: n_elem out of range");
+  const int qoff = d->q_offset == 0 ? 2 : d->q_offset;
+  if (qoff != 1 && qoff != 2) return fail(SPX_ERR_UNSUPPORTED, "plan_create: q_offset must be 1 or 2");
+  spx_plan* p = new (std::nothrow) spx_plan();
+  if (!p) return fail(SPX_ERR_NO_MEMORY, "plan_create: out of host memory");
+  p->dim = d->dim;
+  p->E = d->n_elem;
+  p->qoff = qoff;
+  p->orders.resize(p->E);
+  if (d->elem_order) {
+    for (int64_t e = 0; e < p->E; ++e) {
+      const int P = d->elem_order[e];
+      if (P < 1 || P > kMaxP) {
+        delete p;
+        return fail(SPX_ERR_INVALID_ARG, "plan_create: element order outside 1..8");
+      }
+      p->orders[e] = P;
+    }
+  } else {
+    if (d->uniform_order < 1 || d->uniform_order > kMaxP) {
+      delete p;
+      return fail(SPX_ERR_INVALID_ARG, "plan_create: uniform_order outside 1..8");
+    }
+    std::fill(p->orders.begin(), p->orders.end(), d->uniform_order);
+  }
+  for (int64_t e = 0; e < p->E; ++e) p->present[p->orders[e]] = true;
+  int npresent = 0;
+  for (int P = 1; P <= kMaxP; ++P) npresent += p->present[P];
+  p->uniform = npresent <= 1;
+  p->uP = d->elem_order ? (p->E ? p->orders[0] : 1) : d->uniform_order;
+  if (p->E == 0) p->present[p->uP] = true;
+  p->coef_off.resize(p->E + 1);
+  p->quad_off.resize(p->E + 1);
+  p->coef_off[0] = p->quad_off[0] = 0;
+  for (int64_t e = 0; e < p->E; ++e) {
+    const int64_t n = p->orders[e] + 1, Q = p->orders[e] + qoff;
+    p->coef_off[e + 1] = p->coef_off[e] + (p->dim == 3 ? n * n * n : n * n);
+    p->quad_off[e + 1] = p->quad_off[e] + (p->dim == 3 ? Q * Q * Q : Q * Q);
+  }
+  p->n_coef = p->coef_off[p->E];
+  p->n_quad = p->quad_off[p->E];
+  for (int P = 1; P <= kMaxP; ++P) {
+    const int Q = P + qoff, n = P + 1;
+    p->tab[P].assign(2 * Q * n + Q * Q, 0.0);
+    basis_tables(P, Q, nullptr, nullptr, p->tab[P].data(), p->tab[P].data() + Q * n, p->tab[P].data() + 2 * Q * n);
+  }
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDeviceProperties");
+  }
+  p->num_sms = prop.multiProcessorCount;
+  p->max_smem = prop.sharedMemPerBlockOptin;
+  // device metadata
+  auto cleanup = [&](cudaError_t err, const char* what) {
+    spx_plan_destroy(p);
+    return cuda_fail(err, what);
+  };
+  if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup(e, "cudaMalloc(status)");
+  if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup(e, "cudaMemset(status)");
+  if (!p->uniform) {
+    p->bucket_start.assign(kMaxP + 2, 0);
+    for (int64_t i = 0; i < p->E; ++i) p->bucket_start[p->orders[i] + 1]++;
+    for (int P = 1; P <= kMaxP + 1; ++P) p->bucket_start[P] += p->bucket_start[P - 1];
+    p->ids.resize(p->E);
+    std::vector<int64_t> fill(p->bucket_start.begin(), p->bucket_start.end());
+    for (int64_t i = 0; i < p->E; ++i) p->ids[fill[p->orders[i]]++] = static_cast<int32_t>(i);
+    if ((e = cudaMalloc(&p->d_ids, p->E * sizeof(int32_t))) != cudaSuccess) return cleanup(e, "cudaMalloc(ids)");
+    if ((e = cudaMalloc(&p->d_coef_off, (p->E + 1) * sizeof(int64_t))) != cudaSuccess)
+      return cleanup(e, "cudaMalloc(coef_off)");
+    if ((e = cudaMalloc(&p->d_quad_off, (p->E + 1) * sizeof(int64_t))) != cudaSuccess)
+      return cleanup(e, "cudaMalloc(quad_off)");
+    e = cudaMemcpy(p->d_ids, p->ids.data(), p->E * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_coef_off, p->coef_off.data(), (p->E + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_quad_off, p->quad_off.data(), (p->E + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(e, "cudaMemcpy(plan metadata)");
+  }
+  // default tiles: fit shared memory with 2 stages
+  for (int op = 0; op < OP_KINDS; ++op) {
+    for (int dt = 0; dt < 2; ++dt) {
+      LaunchCfg& c = p->cfg[op][dt];
+      c.nthreads = 256;
+      c.stages = 2;
+      for (int P = 1; P <= kMaxP; ++P) c.order[P].eb = default_eb(p->dim, P + qoff);
+      for (int P = 1; P <= kMaxP; ++P) {
+        if (!p->present[P]) continue;
+        while (c.order[P].eb > 1 && op_smem_bytes(p, op, dt, c) > p->max_smem) c.order[P].eb /= 2;
+      }
+    }
+  }
+  *out = p;
+  return SPX_OK;
+}
+
+spx_status spx_plan_destroy(spx_plan* p) {
+  if (!p) return SPX_OK;
+  for (int op = 0; op < OP_KINDS; ++op)
+    for (int dt = 0; dt < 2; ++dt)
+      if (p->tiles[op][dt].d) cudaFree(p->tiles[op][dt].d);
+  if (p->d_ids) cudaFree(p->d_ids);
+  if (p->d_coef_off) cudaFree(p->d_coef_off);
+  if (p->d_quad_off) cudaFree(p->d_quad_off);
+  if (p->d_status) cudaFree(p->d_status);
+  delete p;
+  return SPX_OK;
+}
+
+spx_status spx_plan_sizes(const spx_plan* p, int64_t* n_coef, int64_t* n_quad) {
+  if (!p) return fail(SPX_ERR_INVALID_ARG, "plan_sizes: NULL plan");
+  if (n_coef) *n_coef = p->n_coef;
+  if (n_quad) *n_quad = p->n_quad;
+  return SPX_OK;
+}
+
+spx_status spx_plan_offsets(const spx_plan* p, int64_t* coef_off, int64_t* quad_off) {
+  if (!p) return fail(SPX_ERR_INVALID_ARG, "plan_offsets: NULL plan");
+  if (coef_off) std::memcpy(coef_off, p->coef_off.data(), (p->E + 1) * sizeof(int64_t));
+  if (quad_off) std::memcpy(quad_off, p->quad_off.data(), (p->E + 1) * sizeof(int64_t));
+  return SPX_OK;
+}
+
+spx_status spx_plan_set_geometry(spx_plan* p, spx_dtype dt, const void* geom, const void* dxi) {
+  if (!p) return fail(SPX_ERR_INVALID_ARG, "set_geometry: NULL plan");
+  if (dt != SPX_F64 && dt != SPX_F32) return fail(SPX_ERR_INVALID_ARG, "set_geometry: bad dtype");
+  p->geom[dt] = geom;
+  p->dxi[dt] = dxi;
+  return SPX_OK;
+}
+
+spx_status spx_plan_device_status(spx_plan* p, int* status, int reset) {
+  if (!p || !status) return fail(SPX_ERR_INVALID_ARG, "plan_device_status: NULL argument");
+  cudaError_t e = cudaMemcpy(status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+  if (reset && (e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  return SPX_OK;
+}
+
+spx_status spx_plan_set_tile(spx_plan* p, spx_op op, spx_dtype dt, int order, int eb, int nthreads, int stages) {
+  if (!p) return fail(SPX_ERR_INVALID_ARG, "set_tile: NULL plan");
+  if (op < 0 || op >= OP_KINDS || (dt != SPX_F64 && dt != SPX_F32))
+    return fail(SPX_ERR_INVALID_ARG, "set_tile: bad operator or dtype");
+  if (eb < 1 || eb > kMaxEB || nthreads < 32 || nthreads > 1024 || nthreads % 32 || stages < 1 || stages > 4)
+    return fail(SPX_ERR_INVALID_ARG, "set_tile: eb 1..64, nthreads 32..1024 (multiple of 32), stages 1..4");
+  if (order != -1 && (order < 1 || order > kMaxP)) return fail(SPX_ERR_INVALID_ARG, "set_tile: order outside 1..8");
+  LaunchCfg c = p->cfg[op][dt];
+  c.nthreads = nthreads;
+  c.stages = stages;
+  for (int P = 1; P <= kMaxP; ++P)
+    if (order == -1 || order == P) c.order[P].eb = eb;
+  if (op_smem_bytes(p, op, dt, c) > p->max_smem)
+    return fail(SPX_ERR_UNSUPPORTED, "set_tile: tile does not fit in shared memory");
+  p->cfg[op][dt] = c;
+  p->tiles[op][dt].dirty = true;
+  return ensure_tiles(p, op, dt);
+}
+
+spx_status spx_plan_get_tile(const spx_plan* p, spx_op op, spx_dtype dt, int order, int* eb, int* nthreads,
+                             int* stages) {
+  if (!p || op < 0 || op >= OP_KINDS || (dt != SPX_F64 && dt != SPX_F32) || order < 1 || order > kMaxP)
+    return fail(SPX_ERR_INVALID_ARG, "get_tile: bad argument");
+  const LaunchCfg& c = p->cfg[op][dt];
+  if (eb) *eb = c.order[order].eb;
+  if (nthreads) *nthreads = c.nthreads;
+  if (stages) *stages = c.stages;
+  return SPX_OK;
+}
+
+// ---------------------------------------------------------------------------
+static spx_status run_op(const spx_plan* cp, int op, spx_dtype dt, const void* in0, const void* in1,
+                         const void* lam_f, const void* kap_f, void* o0, void* o1, void* o2, double lam,
+                         void* stream) {
+  spx_plan* p = const_cast<spx_plan*>(cp);
+  if (!p) return fail(SPX_ERR_INVALID_ARG, "NULL plan");
+  if (dt != SPX_F64 && dt != SPX_F32) return fail(SPX_ERR_INVALID_ARG, "bad dtype");
+  if (p->E == 0) return SPX_OK;
+  const void* geom = op == OP_DERIV ? p->dxi[dt] : p->geom[dt];
+  if (op_needs_geom(op) && !geom)
+    return fail(SPX_ERR_INVALID_ARG, op == OP_DERIV ? "dxi_dx not registered for this dtype"
+                                                    : "geometry not registered for this dtype");
+  const size_t a = dt == SPX_F64 ? 8 : 4;
+  const void* ptrs[] = {in0, in1, lam_f, kap_f, o0, o1, o2};
+  for (const void* q : ptrs)
+    if (q && (reinterpret_cast<uintptr_t>(q) % a)) return fail(SPX_ERR_INVALID_ARG, "buffer not aligned to its element size");
+  spx_status s = ensure_tiles(p, op, dt);
+  if (s != SPX_OK) return s;
+  LaunchReq r{p, op, dt, in0, in1, geom, lam_f, kap_f, o0, o1, o2, lam, static_cast<cudaStream_t>(stream)};
+  return launch_op(r);
+}
+
+spx_status spx_bwd_trans(const spx_plan* p, spx_dtype dt, const void* coef, void* phys, void* stream) {
+  if (p && p->E && (!coef || !phys)) return fail(SPX_ERR_INVALID_ARG, "bwd_trans: NULL buffer");
+  return run_op(p, OP_BWD, dt, coef, nullptr, nullptr, nullptr, phys, nullptr, nullptr, 0.0, stream);
+}
+
+spx_status spx_iproduct(const spx_plan* p, spx_dtype dt, const void* phys, void* coef, void* stream) {
+  if (p && p->E && (!coef || !phys)) return fail(SPX_ERR_INVALID_ARG, "iproduct: NULL buffer");
+  return run_op(p, OP_IPROD, dt, phys, nullptr, nullptr, nullptr, coef, nullptr, nullptr, 0.0, stream);
+}
+
+spx_status spx_phys_deriv(const spx_plan* p, spx_dtype dt, const void* phys, void* d0, void* d1, void* d2,
+                          void* stream) {
+  if (p && p->E && (!phys || !d0 || !d1 || (p->dim == 3 && !d2)))
+    return fail(SPX_ERR_INVALID_ARG, "phys_deriv: NULL buffer");
+  return run_op(p, OP_DERIV, dt, phys, nullptr, nullptr, nullptr, d0, d1, p && p->dim == 3 ? d2 : nullptr, 0.0,
+                stream);
+}
+
+spx_status spx_helmholtz(const spx_plan* p, spx_dtype dt, double lambda, const void* lam_f, const void* kap_f,
+                         const void* in, void* out, void* stream) {
+  if (p && p->E && (!in || !out)) return fail(SPX_ERR_INVALID_ARG, "helmholtz: NULL buffer");
+  if (in && in == out) return fail(SPX_ERR_INVALID_ARG, "helmholtz: coef_out must not alias coef_in");
+  if (!std::isfinite(lambda)) return fail(SPX_ERR_INVALID_ARG, "helmholtz: lambda not finite");
+  return run_op(p, OP_HELM, dt, in, nullptr, lam_f, kap_f, out, nullptr, nullptr, lambda, stream);
+}
+
+spx_status spx_helmholtz_adjoint(const spx_plan* p, const double* u, const double* g, double* glam, double* gkap,
+                                 void* stream) {
+  if (p && p->E && (!u || !g)) return fail(SPX_ERR_INVALID_ARG, "helmholtz_adjoint: NULL input");
+  if (!glam && !gkap) return SPX_OK;
+  return run_op(p, OP_ADJ, SPX_F64, u, g, nullptr, nullptr, glam, gkap, nullptr, 0.0, stream);
+}
+
+spx_status spx_helmholtz_diag(const spx_plan* p, spx_dtype dt, double lambda, void* out, void* stream) {
+  if (p && p->E && !out) return fail(SPX_ERR_INVALID_ARG, "helmholtz_diag: NULL buffer");
+  return run_op(p, OP_DIAG, dt, nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, lambda, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning (§3.3: the fastest strategy is picked at start-up).
+// ---------------------------------------------------------------------------
+static float time_op(spx_plan* p, int op, spx_dtype dt, const void* in, void* out, int reps, cudaStream_t st,
+                     spx_status* err) {
+  void* o[3] = {out, nullptr, nullptr};
+  const void* in1 = nullptr;
+  size_t qbytes = (dt == SPX_F64 ? 8 : 4) * static_cast<size_t>(p->n_quad);
+  if (op == OP_DERIV) {  // three outputs packed in `out`
+    o[1] = static_cast<char*>(out) + qbytes;
+    o[2] = p->dim == 3 ? static_cast<char*>(out) + 2 * qbytes : nullptr;
+  }
+  if (op == OP_ADJ) {
+    in1 = in;
+    o[1] = static_cast<char*>(out) + qbytes;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  *err = run_op(p, op, dt, in, in1, nullptr, nullptr, o[0], o[1], o[2], 1.0, st);  // warm-up
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < reps && *err == SPX_OK; ++i)
+    *err = run_op(p, op, dt, in, in1, nullptr, nullptr, o[0], o[1], o[2], 1.0, st);
+  cudaEventRecord(e1, st);
+  cudaError_t ce = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess && *err == SPX_OK) *err = cuda_fail(ce, "autotune timing");
+  return ms / std::max(1, reps);
+}
+
+spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, void* out, int reps, void* stream) {
+  if (!p || !in || !out || op < 0 || op >= SPX_OP_COUNT || (dt != SPX_F64 && dt != SPX_F32) || reps < 1)
+    return fail(SPX_ERR_INVALID_ARG, "autotune: bad argument");
+  if (p->E == 0) return SPX_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ebs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
+  const int nts[] = {64, 128, 192, 256, 384, 512};
+  const int sts[] = {2, 3};
+  LaunchCfg best = p->cfg[op][dt];
+  // orders one at a time (other orders keep their current tile); the same
+  // thread count and depth serve the whole launch, so they are tuned last.
+  float best_ms = 1e30f;
+  for (int P = 1; P <= kMaxP; ++P) {
+    if (!p->present[P]) continue;
+    float bms = 1e30f;
+    int beb = best.order[P].eb;
+    for (int eb : ebs) {
+      LaunchCfg c = best;
+      c.order[P].eb = eb;
+      if (op_smem_bytes(p, op, dt, c) > p->max_smem) continue;
+      p->cfg[op][dt] = c;
+      p->tiles[op][dt].dirty = true;
+      spx_status s;
+      float ms = time_op(p, op, dt, in, out, reps, st, &s);
+      if (s != SPX_OK) {
+        p->cfg[op][dt] = best;
+        p->tiles[op][dt].dirty = true;
+        if (s == SPX_ERR_UNSUPPORTED) continue;
+        return s;
+      }
+      if (ms < bms) {
+        bms = ms;
+        beb = eb;
+      }
+    }
+    best.order[P].eb = beb;
+    best_ms = bms;
+  }
+  for (int nt : nts) {
+    for (int sg : sts) {
+      LaunchCfg c = best;
+      c.nthreads = nt;
+      c.stages = sg;
+      if (op_smem_bytes(p, op, dt, c) > p->max_smem) continue;
+      p->cfg[op][dt] = c;
+      p->tiles[op][dt].dirty = true;
+      spx_status s;
+      float ms = time_op(p, op, dt, in, out, reps, st, &s);
+      if (s != SPX_OK) {
+        if (s == SPX_ERR_UNSUPPORTED) continue;
+        p->cfg[op][dt] = best;
+        p->tiles[op][dt].dirty = true;
+        return s;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.nthreads = nt;
+        best.stages = sg;
+      }
+    }
+  }
+  p->cfg[op][dt] = best;
+  p->tiles[op][dt].dirty = true;
+  return ensure_tiles(p, op, dt);
+}
+
+}  // extern "C"

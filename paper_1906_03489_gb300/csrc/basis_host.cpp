@@ -1,0 +1,181 @@
+// Host FP64 construction of the basis tables (§2.1 modified basis; GLL
+// quadrature of §3.5, Listing lst:python).
+//
+// GLL points: the end points -1, 1 and the Q-2 zeros of the Jacobi
+// polynomial P^{(1,1)}_{Q-2}, obtained as the eigenvalues of its symmetric
+// tridiagonal Jacobi matrix (Golub-Welsch) and polished by Newton steps on the
+// three-term recurrence.  Weights w_i = 2 / (N (N+1) L_N(x_i)^2), N = Q-1.
+// The collocation derivative uses barycentric weights.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "spx_internal.h"
+
+namespace spx {
+namespace {
+
+// P^{(1,1)}_m(x) and its derivative by the recurrence and its x-derivative.
+void jacobi11(int m, double x, double* val, double* der) {
+  double p0 = 1.0, d0 = 0.0;
+  if (m == 0) {
+    *val = p0;
+    *der = d0;
+    return;
+  }
+  double p1 = 2.0 * x, d1 = 2.0;  // (a+b+2) x / 2 with a = b = 1
+  for (int k = 2; k <= m; ++k) {
+    // 2k(k+2)(2k) P_k = (2k+1)(2k+2)(2k) x P_{k-1} - 2k(k)(2k+2) P_{k-2}, a = b = 1
+    const double c = 2.0 * k + 2.0;               // 2k + a + b
+    const double a1 = 2.0 * k * (k + 2.0) * (c - 2.0);
+    const double a2 = (c - 1.0) * c * (c - 2.0);  // coefficient of x P_{k-1}
+    const double a3 = 2.0 * k * k * c;            // 2 (k+a-1)(k+b-1) c
+    const double p2 = (a2 * x * p1 - a3 * p0) / a1;
+    const double d2 = (a2 * (p1 + x * d1) - a3 * d0) / a1;
+    p0 = p1; d0 = d1; p1 = p2; d1 = d2;
+  }
+  *val = p1;
+  *der = d1;
+}
+
+double legendre_val(int N, double x) {
+  double a = 1.0, b = x;
+  if (N == 0) return a;
+  for (int k = 1; k < N; ++k) {
+    const double c = ((2.0 * k + 1.0) * x * b - k * a) / (k + 1.0);
+    a = b;
+    b = c;
+  }
+  return b;
+}
+
+// Eigenvalues of a symmetric tridiagonal matrix (diag d, off-diag e) by
+// implicit QL iterations with Wilkinson shifts; d is overwritten.
+void tridiag_eigenvalues(std::vector<double>& d, std::vector<double> e) {
+  const int n = static_cast<int>(d.size());
+  e.push_back(0.0);
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0; iter < 100; ++iter) {
+      int m = l;
+      for (; m < n - 1; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= 1e-17 * dd) break;
+      }
+      if (m == l) break;
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + (g >= 0 ? std::fabs(r) : -std::fabs(r)));
+      double s = 1.0, c = 1.0, p = 0.0;
+      int i = m - 1;
+      for (; i >= l; --i) {
+        double f = s * e[i], b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= p;
+          e[m] = 0.0;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+      }
+      if (r == 0.0 && i >= l) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+}
+
+void gll_points(int Q, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(Q, 0.0);
+  w.assign(Q, 0.0);
+  const int N = Q - 1;
+  x[0] = -1.0;
+  x[N] = 1.0;
+  const int m = Q - 2;  // interior points: zeros of P^{(1,1)}_m
+  if (m > 0) {
+    // Jacobi matrix of the weight (1-x)(1+x): zero diagonal, off-diagonal
+    // b_k = sqrt(k (k+2) / ((2k+1)(2k+3))), k = 1..m-1
+    std::vector<double> d(m, 0.0), e(m > 1 ? m - 1 : 0);
+    for (int k = 1; k < m; ++k) e[k - 1] = std::sqrt(k * (k + 2.0) / ((2.0 * k + 1.0) * (2.0 * k + 3.0)));
+    tridiag_eigenvalues(d, e);
+    std::sort(d.begin(), d.end());
+    for (int i = 0; i < m; ++i) {
+      double z = d[i];
+      for (int it = 0; it < 8; ++it) {  // Newton polish
+        double v, dv;
+        jacobi11(m, z, &v, &dv);
+        z -= v / dv;
+      }
+      x[i + 1] = z;
+    }
+    for (int i = 1; i <= m / 2; ++i) {  // exact symmetry
+      const double a = 0.5 * (x[N - i] - x[i]);
+      x[i] = -a;
+      x[N - i] = a;
+    }
+    if (m % 2 == 1) x[Q / 2] = 0.0;
+  }
+  for (int i = 0; i < Q; ++i) {
+    const double L = legendre_val(N, x[i]);
+    w[i] = 2.0 / (N * (N + 1.0) * L * L);
+  }
+}
+
+}  // namespace
+
+spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* dB, double* D) {
+  if (P < 1 || Q < 2 || Q > 16) return fail(SPX_ERR_INVALID_ARG, "basis tables need 1 <= P and 2 <= Q <= 16");
+  std::vector<double> x, ww;
+  gll_points(Q, x, ww);
+  if (xi) std::memcpy(xi, x.data(), Q * sizeof(double));
+  if (w) std::memcpy(w, ww.data(), Q * sizeof(double));
+  const int n = P + 1;
+  for (int i = 0; i < Q; ++i) {
+    const double z = x[i];
+    for (int p = 0; p < n; ++p) {
+      double v, dv;
+      if (p == 0) {
+        v = 0.5 * (1.0 - z);
+        dv = -0.5;
+      } else if (p == P) {
+        v = 0.5 * (1.0 + z);
+        dv = 0.5;
+      } else {
+        double j, dj;
+        jacobi11(p - 1, z, &j, &dj);
+        const double bub = 0.25 * (1.0 - z) * (1.0 + z);
+        v = bub * j;
+        dv = -0.5 * z * j + bub * dj;
+      }
+      if (B) B[i * n + p] = v;
+      if (dB) dB[i * n + p] = dv;
+    }
+  }
+  if (D) {
+    std::vector<double> lam(Q, 1.0);  // barycentric weights
+    for (int j = 0; j < Q; ++j)
+      for (int k = 0; k < Q; ++k)
+        if (k != j) lam[j] /= (x[j] - x[k]);
+    for (int i = 0; i < Q; ++i) {
+      double diag = 0.0;
+      for (int j = 0; j < Q; ++j) {
+        if (j == i) continue;
+        const double v = (lam[j] / lam[i]) / (x[i] - x[j]);
+        D[i * Q + j] = v;
+        diag -= v;
+      }
+      D[i * Q + i] = diag;
+    }
+  }
+  return SPX_OK;
+}
+
+}  // namespace spx

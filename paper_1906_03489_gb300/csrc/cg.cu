@@ -1,0 +1,645 @@
+// C0 assembly and the Jacobi-preconditioned conjugate-gradient solve of the
+// assembled Helmholtz system A x = f, A = sum_e R_e^T H_e R_e (§2.1:
+// implicit-type methods lead to a linear system; assembly sums neighbouring
+// elemental contributions for C0 continuity).
+//
+// Everything runs on the device:
+//  * the transpose of the local-to-global map (CSR: for every global index
+//    the local indices that map to it, in increasing order) is built once per
+//    solve, so assembly is a deterministic gather-sum (no atomics on values);
+//  * the Jacobi diagonal is the assembled diagonal of the elemental matrices;
+//  * each PCG iteration is gather -> elemental Helmholtz -> assembly (+ <p,Ap>)
+//    -> update (+ <r,z>, <r,r>) -> direction update; dot products accumulate
+//    in FP64 in fixed order (per-block partials summed by the last block), so
+//    results are bitwise reproducible;
+//  * iterations are captured once in a CUDA graph of `check_every` iterations
+//    and replayed until the device-side convergence flag is set;
+//  * precision 1: FP32 PCG on the correction equation inside FP64 iterative
+//    refinement (outer residual, its norm and x += d in FP64).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "spx_internal.h"
+
+namespace spx {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+struct Scalars {
+  double rz, rz_new, pAp, alpha, beta, rr, ff, tol2, scale;
+  int it, done, maxit, nonfinite;
+  unsigned int ticket;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduces up to 2 values into partials[blockIdx.x * 2 + k]; returns true
+// in thread 0 of the last block to finish (which then sees every partial).
+__device__ bool block_reduce2(double a, double b, double* partials, unsigned int* ticket) {
+  __shared__ double sa[kRedThreads / 32], sb[kRedThreads / 32];
+  __shared__ bool last;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int i = 0; i < kRedThreads / 32; ++i) {
+      ta += sa[i];
+      tb += sb[i];
+    }
+    partials[2 * blockIdx.x] = ta;
+    partials[2 * blockIdx.x + 1] = tb;
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+// Fixed-order sum of the partials by thread 0 of the last block.
+__device__ void final_sums(const double* partials, int nb, double* a, double* b) {
+  __threadfence();
+  double ta = 0.0, tb = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    ta += static_cast<volatile const double*>(partials)[2 * i];
+    tb += static_cast<volatile const double*>(partials)[2 * i + 1];
+  }
+  *a = ta;
+  *b = tb;
+}
+
+// ---- CSR transpose of l2g ------------------------------------------------
+__global__ void csr_count(const int32_t* l2g, int64_t nl, int32_t* cnt) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nl; i += int64_t(gridDim.x) * blockDim.x)
+    atomicAdd(&cnt[l2g[i]], 1);
+}
+
+__global__ void check_l2g(const int32_t* l2g, int64_t nl, int64_t ng, int* bad) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nl; i += int64_t(gridDim.x) * blockDim.x)
+    if (l2g[i] < 0 || l2g[i] >= ng) atomicOr(bad, 1);
+}
+
+// exclusive scan, pass 1: per-chunk scan, chunk totals
+constexpr int kScanChunk = 1024;
+__global__ void scan_chunks(const int32_t* in, int32_t* out, int64_t n, int32_t* totals) {
+  __shared__ int32_t s[kScanChunk];
+  const int64_t base = int64_t(blockIdx.x) * kScanChunk;
+  const int t = threadIdx.x;  // blockDim = kScanChunk
+  s[t] = base + t < n ? in[base + t] : 0;
+  __syncthreads();
+  for (int o = 1; o < kScanChunk; o <<= 1) {
+    int32_t v = t >= o ? s[t - o] : 0;
+    __syncthreads();
+    s[t] += v;
+    __syncthreads();
+  }
+  if (base + t < n) out[base + t] = s[t] - (base + t < n ? in[base + t] : 0);
+  if (t == kScanChunk - 1) totals[blockIdx.x] = s[t];
+}
+
+// pass 2 (one block): exclusive scan of chunk totals, written in place
+__global__ void scan_totals(int32_t* totals, int nchunks, int32_t* grand) {
+  if (threadIdx.x != 0) return;
+  int32_t run = 0;
+  for (int i = 0; i < nchunks; ++i) {
+    const int32_t v = totals[i];
+    totals[i] = run;
+    run += v;
+  }
+  *grand = run;
+}
+
+__global__ void scan_add(int32_t* out, int64_t n, const int32_t* totals) {
+  const int64_t i = int64_t(blockIdx.x) * kScanChunk + threadIdx.x;
+  if (i < n) out[i] += totals[blockIdx.x];
+}
+
+__global__ void csr_fill(const int32_t* l2g, int64_t nl, const int32_t* row_ptr, int32_t* cursor, int32_t* cols) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nl; i += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t g = l2g[i];
+    const int32_t k = atomicAdd(&cursor[g], 1);
+    cols[row_ptr[g] + k] = static_cast<int32_t>(i);
+  }
+}
+
+__global__ void csr_sort(const int32_t* row_ptr, int32_t* cols, int64_t ng) {
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t a = row_ptr[g], b = row_ptr[g + 1];
+    for (int32_t i = a + 1; i < b; ++i) {
+      const int32_t v = cols[i];
+      int32_t j = i - 1;
+      while (j >= a && cols[j] > v) {
+        cols[j + 1] = cols[j];
+        --j;
+      }
+      cols[j + 1] = v;
+    }
+  }
+}
+
+// ---- assembly and vector kernels ----------------------------------------
+template <typename T>
+__global__ void assemble_plain(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
+                               const T* __restrict__ yl, T* __restrict__ yg, int64_t ng) {
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    T s = T(0);
+    for (int32_t k = row_ptr[g]; k < row_ptr[g + 1]; ++k) s += yl[cols[k]];
+    yg[g] = s;
+  }
+}
+
+template <typename T>
+__global__ void gather_if(const int32_t* __restrict__ l2g, const T* __restrict__ g, T* __restrict__ loc, int64_t n,
+                          const Scalars* sc) {
+  if (sc->done) return;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    loc[i] = g[l2g[i]];
+}
+
+// q = assemble(ql); pAp = <p, q>; alpha = rz / pAp
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) assemble_dot(const int32_t* __restrict__ row_ptr,
+                                                            const int32_t* __restrict__ cols,
+                                                            const T* __restrict__ ql, T* __restrict__ q,
+                                                            const T* __restrict__ p, int64_t ng, Scalars* sc,
+                                                            double* partials) {
+  if (sc->done) return;
+  double acc = 0.0;
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    T s = T(0);
+    for (int32_t k = row_ptr[g]; k < row_ptr[g + 1]; ++k) s += ql[cols[k]];
+    q[g] = s;
+    acc += static_cast<double>(p[g]) * static_cast<double>(s);
+  }
+  if (block_reduce2(acc, 0.0, partials, &sc->ticket) && threadIdx.x == 0) {
+    double pAp, unused;
+    final_sums(partials, gridDim.x, &pAp, &unused);
+    sc->pAp = pAp;
+    sc->alpha = sc->rz / pAp;
+    sc->ticket = 0;
+  }
+}
+
+// x += alpha p; r -= alpha q; z = minv r; rz_new = <r,z>; rr = <r,r>
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+                                                         const T* __restrict__ p, const T* __restrict__ q,
+                                                         const T* __restrict__ minv, int64_t ng, Scalars* sc,
+                                                         double* partials) {
+  if (sc->done) return;
+  const T alpha = static_cast<T>(sc->alpha);
+  double arz = 0.0, arr = 0.0;
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    x[g] += alpha * p[g];
+    const T rv = r[g] - alpha * q[g];
+    r[g] = rv;
+    const T zv = minv[g] * rv;
+    z[g] = zv;
+    arz += static_cast<double>(rv) * static_cast<double>(zv);
+    arr += static_cast<double>(rv) * static_cast<double>(rv);
+  }
+  if (block_reduce2(arz, arr, partials, &sc->ticket) && threadIdx.x == 0) {
+    double rz, rr;
+    final_sums(partials, gridDim.x, &rz, &rr);
+    sc->rz_new = rz;
+    sc->beta = rz / sc->rz;
+    sc->rz = rz;
+    sc->rr = rr;
+    sc->it += 1;
+    if (!isfinite(rr) || !isfinite(rz)) {
+      sc->nonfinite = 1;
+      sc->done = 1;
+    } else if (rr <= sc->tol2 * sc->ff || sc->it >= sc->maxit) {
+      sc->done = 1;
+    }
+    sc->ticket = 0;
+  }
+}
+
+template <typename T>
+__global__ void cg_direction(T* __restrict__ p, const T* __restrict__ z, int64_t ng, const Scalars* sc) {
+  if (sc->done) return;
+  const T beta = static_cast<T>(sc->beta);
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x)
+    p[g] = z[g] + beta * p[g];
+}
+
+// Start of a PCG run from residual r (x not touched): z = minv r; p = z;
+// rz = <r,z>; ff = <b,b> (with b the right-hand side, given in r when
+// `rhs_norm_from_r`), it = 0, done unless there is work.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) cg_start(const T* __restrict__ r, T* __restrict__ z,
+                                                        T* __restrict__ p, const T* __restrict__ minv, int64_t ng,
+                                                        Scalars* sc, double* partials) {
+  double arz = 0.0, arr = 0.0;
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    const T rv = r[g];
+    const T zv = minv[g] * rv;
+    z[g] = zv;
+    p[g] = zv;
+    arz += static_cast<double>(rv) * static_cast<double>(zv);
+    arr += static_cast<double>(rv) * static_cast<double>(rv);
+  }
+  if (block_reduce2(arz, arr, partials, &sc->ticket) && threadIdx.x == 0) {
+    double rz, rr;
+    final_sums(partials, gridDim.x, &rz, &rr);
+    sc->rz = rz;
+    sc->rr = rr;
+    sc->it = 0;
+    sc->nonfinite = (!isfinite(rr) || !isfinite(rz)) ? 1 : 0;
+    sc->done = (sc->nonfinite || rr <= sc->tol2 * sc->ff || sc->maxit <= 0) ? 1 : 0;
+    sc->ticket = 0;
+  }
+}
+
+// r = f - y (FP64); rr = <r,r>; ff = <f,f>
+__global__ void __launch_bounds__(kRedThreads) residual64(const double* __restrict__ f, const double* __restrict__ y,
+                                                          double* __restrict__ r, int64_t ng, Scalars* sc,
+                                                          double* partials) {
+  double arr = 0.0, aff = 0.0;
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    const double rv = f[g] - y[g];
+    r[g] = rv;
+    arr += rv * rv;
+    aff += f[g] * f[g];
+  }
+  if (block_reduce2(arr, aff, partials, &sc->ticket) && threadIdx.x == 0) {
+    double rr, ff;
+    final_sums(partials, gridDim.x, &rr, &ff);
+    sc->rr = rr;
+    sc->ff = ff;
+    sc->ticket = 0;
+  }
+}
+
+// r32 = r64 * s, d32 = 0
+__global__ void to_f32_scaled(const double* __restrict__ r, float* __restrict__ r32, float* __restrict__ d32,
+                              int64_t ng, const Scalars* sc) {
+  const double s = 1.0 / sqrt(sc->rr);
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    r32[g] = static_cast<float>(r[g] * s);
+    d32[g] = 0.f;
+  }
+}
+
+// x += ||r|| d32
+__global__ void add_correction(double* __restrict__ x, const float* __restrict__ d32, int64_t ng, double scale) {
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x)
+    x[g] += scale * static_cast<double>(d32[g]);
+}
+
+template <typename T>
+__global__ void invert_diag(const double* __restrict__ dg, T* __restrict__ minv, int64_t ng) {
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x)
+    minv[g] = static_cast<T>(1.0 / dg[g]);
+}
+
+template <typename T>
+__global__ void fill_zero(T* v, int64_t n) {
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < n; g += int64_t(gridDim.x) * blockDim.x)
+    v[g] = T(0);
+}
+
+// ---------------------------------------------------------------------------
+struct Workspace {
+  int32_t *row_ptr, *cols, *cursor, *totals, *grand;
+  int* bad;
+  Scalars* sc;
+  double* partials;
+  double *r64, *z64, *p64, *q64, *minv64, *pl64, *ql64, *diag64;
+  float *r32, *z32, *p32, *q32, *d32, *minv32, *pl32, *ql32;
+  size_t bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Workspace carve(char* base, int64_t ng, int64_t nl, int nred, int precision) {
+  Workspace w{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  const int64_t nchunks = (ng + 1 + kScanChunk - 1) / kScanChunk;
+  w.row_ptr = reinterpret_cast<int32_t*>(take((ng + 1) * 4));
+  w.cols = reinterpret_cast<int32_t*>(take(nl * 4));
+  w.cursor = reinterpret_cast<int32_t*>(take((ng + 1) * 4));
+  w.totals = reinterpret_cast<int32_t*>(take(nchunks * 4));
+  w.grand = reinterpret_cast<int32_t*>(take(16));
+  w.bad = reinterpret_cast<int*>(take(16));
+  w.sc = reinterpret_cast<Scalars*>(take(sizeof(Scalars)));
+  w.partials = reinterpret_cast<double*>(take(2 * nred * sizeof(double)));
+  w.diag64 = reinterpret_cast<double*>(take(nl * 8));   // local diagonal, then global diagonal
+  w.r64 = reinterpret_cast<double*>(take(ng * 8));
+  w.minv64 = reinterpret_cast<double*>(take(ng * 8));
+  w.pl64 = reinterpret_cast<double*>(take(nl * 8));
+  w.ql64 = reinterpret_cast<double*>(take(nl * 8));
+  w.q64 = reinterpret_cast<double*>(take(ng * 8));
+  if (precision == 0) {
+    w.z64 = reinterpret_cast<double*>(take(ng * 8));
+    w.p64 = reinterpret_cast<double*>(take(ng * 8));
+  } else {
+    w.r32 = reinterpret_cast<float*>(take(ng * 4));
+    w.z32 = reinterpret_cast<float*>(take(ng * 4));
+    w.p32 = reinterpret_cast<float*>(take(ng * 4));
+    w.q32 = reinterpret_cast<float*>(take(ng * 4));
+    w.d32 = reinterpret_cast<float*>(take(ng * 4));
+    w.minv32 = reinterpret_cast<float*>(take(ng * 4));
+    w.pl32 = reinterpret_cast<float*>(take(nl * 4));
+    w.ql32 = reinterpret_cast<float*>(take(nl * 4));
+  }
+  w.bytes = off;
+  return w;
+}
+
+struct Solver {
+  const spx_plan* plan;
+  const int32_t* l2g;
+  int64_t ng, nl;
+  cudaStream_t st;
+  int grid_v;    // grid of element-wise kernels
+  int nred;      // grid of reduction kernels (fixed => deterministic)
+  Workspace w;
+  double lam;
+};
+
+#define SPX_CK(expr)                                          \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr);       \
+  } while (0)
+
+spx_status build_csr(Solver& s) {
+  Workspace& w = s.w;
+  SPX_CK(cudaMemsetAsync(w.cursor, 0, (s.ng + 1) * 4, s.st));
+  SPX_CK(cudaMemsetAsync(w.bad, 0, 4, s.st));
+  check_l2g<<<s.grid_v, 256, 0, s.st>>>(s.l2g, s.nl, s.ng, w.bad);
+  int bad = 0;
+  SPX_CK(cudaMemcpyAsync(&bad, w.bad, 4, cudaMemcpyDeviceToHost, s.st));
+  SPX_CK(cudaStreamSynchronize(s.st));
+  if (bad) return fail(SPX_ERR_INVALID_ARG, "cg_solve: l2g has an entry outside [0, n_global)");
+  csr_count<<<s.grid_v, 256, 0, s.st>>>(s.l2g, s.nl, w.cursor);
+  const int64_t n = s.ng + 1;
+  const int nchunks = static_cast<int>((n + kScanChunk - 1) / kScanChunk);
+  scan_chunks<<<nchunks, kScanChunk, 0, s.st>>>(w.cursor, w.row_ptr, n, w.totals);
+  scan_totals<<<1, 32, 0, s.st>>>(w.totals, nchunks, w.grand);
+  scan_add<<<nchunks, kScanChunk, 0, s.st>>>(w.row_ptr, n, w.totals);
+  SPX_CK(cudaMemsetAsync(w.cursor, 0, (s.ng + 1) * 4, s.st));
+  csr_fill<<<s.grid_v, 256, 0, s.st>>>(s.l2g, s.nl, w.row_ptr, w.cursor, w.cols);
+  csr_sort<<<s.grid_v, 256, 0, s.st>>>(w.row_ptr, w.cols, s.ng);
+  int32_t cnt_zero = 0;
+  // a global index with no local entry would make A singular
+  SPX_CK(cudaGetLastError());
+  (void)cnt_zero;
+  return SPX_OK;
+}
+
+// y_global = A x_global in precision T (using pl / ql local buffers)
+template <typename T>
+spx_status apply_A(Solver& s, int dt, const T* xg, T* pl, T* ql, T* yg) {
+  spx_status st = spx_gather(s.plan, static_cast<spx_dtype>(dt), s.l2g, s.ng, xg, pl, s.st);
+  if (st != SPX_OK) return st;
+  st = spx_helmholtz(s.plan, static_cast<spx_dtype>(dt), s.lam, nullptr, nullptr, pl, ql, s.st);
+  if (st != SPX_OK) return st;
+  assemble_plain<T><<<s.grid_v, 256, 0, s.st>>>(s.w.row_ptr, s.w.cols, ql, yg, s.ng);
+  SPX_CK(cudaGetLastError());
+  return SPX_OK;
+}
+
+template <typename T>
+spx_status enqueue_iteration(Solver& s, int dt, T* x, T* r, T* z, T* p, T* q, const T* minv, T* pl, T* ql) {
+  Workspace& w = s.w;
+  gather_if<T><<<s.grid_v, 256, 0, s.st>>>(s.l2g, p, pl, s.nl, w.sc);
+  spx_status st = spx_helmholtz(s.plan, static_cast<spx_dtype>(dt), s.lam, nullptr, nullptr, pl, ql, s.st);
+  if (st != SPX_OK) return st;
+  assemble_dot<T><<<s.nred, kRedThreads, 0, s.st>>>(w.row_ptr, w.cols, ql, q, p, s.ng, w.sc, w.partials);
+  cg_update<T><<<s.nred, kRedThreads, 0, s.st>>>(x, r, z, p, q, minv, s.ng, w.sc, w.partials);
+  cg_direction<T><<<s.grid_v, 256, 0, s.st>>>(p, z, s.ng, w.sc);
+  SPX_CK(cudaGetLastError());
+  return SPX_OK;
+}
+
+// PCG on A x = b given the residual r of the initial x (scalars ff / tol2 /
+// maxit set by the caller).  Returns iterations done in *iters.
+template <typename T>
+spx_status pcg(Solver& s, int dt, T* x, T* r, T* z, T* p, T* q, const T* minv, T* pl, T* ql, bool use_graph,
+               int check_every, int* iters, bool* converged, bool* nonfinite) {
+  Workspace& w = s.w;
+  cg_start<T><<<s.nred, kRedThreads, 0, s.st>>>(r, z, p, minv, s.ng, w.sc, w.partials);
+  SPX_CK(cudaGetLastError());
+  // one eager apply first, so that every launch attribute of the operator
+  // kernel is set before any stream capture
+  {
+    spx_status st0 = spx_helmholtz(s.plan, static_cast<spx_dtype>(dt), s.lam, nullptr, nullptr, pl, ql, s.st);
+    if (st0 != SPX_OK) return st0;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (use_graph) {
+    cudaGraph_t graph;
+    SPX_CK(cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal));
+    spx_status st = SPX_OK;
+    for (int k = 0; k < check_every && st == SPX_OK; ++k) st = enqueue_iteration<T>(s, dt, x, r, z, p, q, minv, pl, ql);
+    cudaError_t ce = cudaStreamEndCapture(s.st, &graph);
+    if (st != SPX_OK) return st;
+    SPX_CK(ce);
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    SPX_CK(ce);
+  }
+  Scalars h{};
+  spx_status st = SPX_OK;
+  for (;;) {
+    if (use_graph) {
+      cudaError_t ce = cudaGraphLaunch(exec, s.st);
+      if (ce != cudaSuccess) {
+        st = cuda_fail(ce, "cudaGraphLaunch");
+        break;
+      }
+    } else {
+      for (int k = 0; k < check_every && st == SPX_OK; ++k)
+        st = enqueue_iteration<T>(s, dt, x, r, z, p, q, minv, pl, ql);
+      if (st != SPX_OK) break;
+    }
+    cudaError_t ce = cudaMemcpyAsync(&h, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s.st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s.st);
+    if (ce != cudaSuccess) {
+      st = cuda_fail(ce, "cg scalars");
+      break;
+    }
+    if (h.done) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (st != SPX_OK) return st;
+  *iters = h.it;
+  *nonfinite = h.nonfinite != 0;
+  *converged = !h.nonfinite && h.rr <= h.tol2 * h.ff;
+  return SPX_OK;
+}
+
+spx_status set_scalars(Solver& s, double ff, double tol, int maxit) {
+  Scalars h{};
+  h.ff = ff;
+  h.tol2 = tol * tol;
+  h.maxit = maxit;
+  SPX_CK(cudaMemcpyAsync(s.w.sc, &h, sizeof(Scalars), cudaMemcpyHostToDevice, s.st));
+  SPX_CK(cudaStreamSynchronize(s.st));
+  return SPX_OK;
+}
+
+spx_status read_scalars(Solver& s, Scalars* h) {
+  SPX_CK(cudaMemcpyAsync(h, s.w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s.st));
+  SPX_CK(cudaStreamSynchronize(s.st));
+  return SPX_OK;
+}
+
+// FP64 residual r = f - A x; returns ||r||^2 and ||f||^2 (sets rr, ff)
+spx_status residual(Solver& s, const double* f, const double* x, double* rr, double* ff) {
+  Workspace& w = s.w;
+  spx_status st = apply_A<double>(s, SPX_F64, x, w.pl64, w.ql64, w.q64);
+  if (st != SPX_OK) return st;
+  residual64<<<s.nred, kRedThreads, 0, s.st>>>(f, w.q64, w.r64, s.ng, w.sc, w.partials);
+  SPX_CK(cudaGetLastError());
+  Scalars h;
+  st = read_scalars(s, &h);
+  if (st != SPX_OK) return st;
+  *rr = h.rr;
+  *ff = h.ff;
+  return SPX_OK;
+}
+
+}  // namespace
+}  // namespace spx
+
+using namespace spx;
+
+extern "C" spx_status spx_cg_workspace_bytes(const spx_plan* plan, int64_t n_global, const spx_cg_opts* o,
+                                             size_t* bytes) {
+  if (!plan || !o || !bytes || n_global < 0) return fail(SPX_ERR_INVALID_ARG, "cg_workspace_bytes: bad argument");
+  if (o->precision != 0 && o->precision != 1) return fail(SPX_ERR_INVALID_ARG, "cg: precision must be 0 or 1");
+  const int nred = plan->num_sms * 2;
+  *bytes = carve(nullptr, n_global, plan->n_coef, nred, o->precision).bytes;
+  return SPX_OK;
+}
+
+extern "C" spx_status spx_cg_solve(const spx_plan* plan, double lambda, const int32_t* l2g, int64_t n_global,
+                                   const double* f, double* x, void* workspace, size_t ws_bytes,
+                                   const spx_cg_opts* o, spx_cg_result* res, void* stream) {
+  if (!plan || !o || !res) return fail(SPX_ERR_INVALID_ARG, "cg_solve: NULL argument");
+  std::memset(res, 0, sizeof(*res));
+  if (n_global < 0 || n_global > (int64_t(1) << 31) - 2 || plan->n_coef > (int64_t(1) << 31) - 1)
+    return fail(SPX_ERR_INVALID_ARG, "cg_solve: sizes exceed the int32 index range");
+  if (n_global == 0) return SPX_OK;
+  if (!l2g || !f || !x || !workspace) return fail(SPX_ERR_INVALID_ARG, "cg_solve: NULL buffer");
+  if (o->precision != 0 && o->precision != 1) return fail(SPX_ERR_INVALID_ARG, "cg_solve: precision must be 0 or 1");
+  if (!(o->tol > 0) || o->maxit < 1 || o->check_every < 1)
+    return fail(SPX_ERR_INVALID_ARG, "cg_solve: tol > 0, maxit >= 1, check_every >= 1 required");
+  if (o->precision == 1 && (!(o->inner_tol > 0) || o->max_outer < 1))
+    return fail(SPX_ERR_INVALID_ARG, "cg_solve: inner_tol > 0 and max_outer >= 1 required");
+  if (!plan->geom[SPX_F64] || (o->precision == 1 && !plan->geom[SPX_F32]))
+    return fail(SPX_ERR_INVALID_ARG, "cg_solve: geometry not registered for the precision(s) used");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(SPX_ERR_INVALID_ARG, "cg_solve: workspace not 256-byte aligned");
+  Solver s{};
+  s.plan = plan;
+  s.l2g = l2g;
+  s.ng = n_global;
+  s.nl = plan->n_coef;
+  s.lam = lambda;
+  s.nred = plan->num_sms * 2;
+  s.grid_v = plan->num_sms * 8;
+  s.w = carve(static_cast<char*>(workspace), n_global, plan->n_coef, s.nred, o->precision);
+  if (ws_bytes < s.w.bytes) return fail(SPX_ERR_NO_MEMORY, "cg_solve: workspace smaller than cg_workspace_bytes");
+  spx_plan* mp = const_cast<spx_plan*>(plan);
+  spx_status st;
+  if ((st = ensure_tiles(mp, OP_HELM, 0)) != SPX_OK) return st;
+  if ((st = ensure_tiles(mp, OP_HELM, 1)) != SPX_OK) return st;
+  // private stream ordered after the caller's
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  SPX_CK(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
+  cudaEvent_t ev;
+  SPX_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  auto finish = [&](spx_status r) {
+    cudaEventRecord(ev, s.st);
+    cudaStreamWaitEvent(user, ev, 0);
+    cudaStreamSynchronize(s.st);
+    cudaEventDestroy(ev);
+    cudaStreamDestroy(s.st);
+    return r;
+  };
+  cudaEventRecord(ev, user);
+  cudaStreamWaitEvent(s.st, ev, 0);
+  Workspace& w = s.w;
+  SPX_CK(cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s.st));
+  if ((st = build_csr(s)) != SPX_OK) return finish(st);
+  // Jacobi diagonal: assembled diag(H_e)
+  if ((st = spx_helmholtz_diag(plan, SPX_F64, lambda, w.diag64, s.st)) != SPX_OK) return finish(st);
+  assemble_plain<double><<<s.grid_v, 256, 0, s.st>>>(w.row_ptr, w.cols, w.diag64, w.r64, s.ng);
+  invert_diag<double><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv64, s.ng);
+  if (o->precision == 1) invert_diag<float><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv32, s.ng);
+  if (cudaGetLastError() != cudaSuccess) return finish(fail(SPX_ERR_CUDA, "cg setup kernels"));
+
+  double rr, ff;
+  if ((st = residual(s, f, x, &rr, &ff)) != SPX_OK) return finish(st);
+  if (ff == 0.0) {
+    fill_zero<double><<<s.grid_v, 256, 0, s.st>>>(x, s.ng);
+    return finish(SPX_OK);
+  }
+  const double tol = o->tol;
+  int total_it = 0;
+  if (o->precision == 0) {
+    // all-FP64 PCG; restart from the true residual if the recurrence drifted
+    for (int restart = 0; restart < 4; ++restart) {
+      if (!std::isfinite(rr)) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite residual"));
+      if (std::sqrt(rr / ff) <= tol) break;
+      if ((st = set_scalars(s, ff, tol, o->maxit - total_it)) != SPX_OK) return finish(st);
+      int it = 0;
+      bool conv, nonfin;
+      st = pcg<double>(s, SPX_F64, x, w.r64, w.z64, w.p64, w.q64, w.minv64, w.pl64, w.ql64, o->use_graph != 0,
+                       o->check_every, &it, &conv, &nonfin);
+      if (st != SPX_OK) return finish(st);
+      total_it += it;
+      if (nonfin) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite residual"));
+      if ((st = residual(s, f, x, &rr, &ff)) != SPX_OK) return finish(st);
+      if (total_it >= o->maxit) break;
+    }
+    res->iters = total_it;
+    res->rel_residual = std::sqrt(rr / ff);
+  } else {
+    int outer = 0;
+    for (; outer < o->max_outer; ++outer) {
+      if (!std::isfinite(rr)) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite residual"));
+      if (std::sqrt(rr / ff) <= tol) break;
+      // inner FP32 PCG on A d = r / ||r||, from d = 0
+      to_f32_scaled<<<s.grid_v, 256, 0, s.st>>>(w.r64, w.r32, w.d32, s.ng, w.sc);
+      // right-hand side norm of the scaled system is 1
+      if ((st = set_scalars(s, 1.0, o->inner_tol, o->maxit)) != SPX_OK) return finish(st);
+      int it = 0;
+      bool conv, nonfin;
+      st = pcg<float>(s, SPX_F32, w.d32, w.r32, w.z32, w.p32, w.q32, w.minv32, w.pl32, w.ql32, o->use_graph != 0,
+                      o->check_every, &it, &conv, &nonfin);
+      if (st != SPX_OK) return finish(st);
+      total_it += it;
+      if (nonfin) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite inner residual"));
+      add_correction<<<s.grid_v, 256, 0, s.st>>>(x, w.d32, s.ng, std::sqrt(rr));
+      if ((st = residual(s, f, x, &rr, &ff)) != SPX_OK) return finish(st);
+    }
+    res->iters = total_it;
+    res->outer_iters = outer;
+    res->rel_residual = std::sqrt(rr / ff);
+  }
+  if (!std::isfinite(res->rel_residual)) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite residual"));
+  if (res->rel_residual > tol)
+    return finish(fail(SPX_ERR_NOT_CONVERGED, "cg_solve: tolerance not reached within the iteration caps"));
+  return finish(SPX_OK);
+}

@@ -1,0 +1,103 @@
+// Host launcher of the operator kernel for one (precision, dimension, operator).
+#pragma once
+#include <algorithm>
+#include <mutex>
+
+#include "op_kernel.cuh"
+#include "smem_layout.h"
+#include "spx_internal.h"
+
+namespace spx {
+
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>
+spx_status launch_impl(const LaunchReq& r) {
+  const spx_plan* plan = r.plan;
+  const int dt = r.dtype;
+  const LaunchCfg& cfg = plan->cfg[OP][dt];
+  const TileList& tl = plan->tiles[OP][dt];
+  if (tl.n == 0) return SPX_OK;
+  KParams<T, PLO, PHI, QOFF> p{};
+  for (int P = PLO; P <= PHI; ++P) {
+    if (!plan->present[P]) continue;
+    const std::vector<double>& t = plan->tab[P];
+    const int off = TabLayout<PLO, PHI, QOFF>::off(P);
+    for (int i = 0; i < tab_len(P, QOFF); ++i) p.tab[off + i] = static_cast<T>(t[i]);
+  }
+  p.tiles = tl.d;
+  p.ids = plan->uniform ? nullptr : plan->d_ids;
+  p.coef_off = plan->uniform ? nullptr : plan->d_coef_off;
+  p.quad_off = plan->uniform ? nullptr : plan->d_quad_off;
+  p.in0 = static_cast<const T*>(r.in0);
+  p.in1 = static_cast<const T*>(r.in1);
+  p.geom = static_cast<const T*>(r.geom);
+  p.lam_f = static_cast<const T*>(r.lam_f);
+  p.kap_f = static_cast<const T*>(r.kap_f);
+  p.out0 = static_cast<T*>(r.out0);
+  p.out1 = static_cast<T*>(r.out1);
+  p.out2 = static_cast<T*>(r.out2);
+  p.status = plan->d_status;
+  p.lam = r.lam;
+  p.n_tiles = tl.n;
+  p.stages = cfg.stages;
+  const SmemLayout L = smem_layout(plan, OP, sizeof(T), cfg, r.lam_f != nullptr, r.kap_f != nullptr);
+  if (L.total > plan->max_smem)
+    return fail(SPX_ERR_UNSUPPORTED, "operator tile needs " + std::to_string(L.total) +
+                                         " bytes of shared memory (limit " + std::to_string(plan->max_smem) + ")");
+  p.slot_base = L.slot_base;
+  p.slot_bytes = L.slot_bytes;
+  for (int s = 0; s < 5; ++s) p.region_off[s] = L.region_off[s];
+  p.work_base = L.work_base;
+  p.work_bytes = L.work_bytes;
+  p.meta_base = L.meta_base;
+  auto kern = op_kernel<T, DIM, OP, PLO, PHI, QOFF>;
+  // raise the dynamic shared-memory limit once per instantiation
+  static std::mutex mu;
+  static size_t configured = 0;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (L.total > configured) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(plan->max_smem));
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      configured = plan->max_smem;
+    }
+  }
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.nthreads, L.total);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "operator tile does not fit on an SM");
+  const int grid = std::min<int64_t>(tl.n, int64_t(nb) * plan->num_sms);
+  kern<<<grid, cfg.nthreads, L.total, r.stream>>>(p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "operator kernel launch");
+  return SPX_OK;
+}
+
+template <typename T, int DIM, int OP, int QOFF>
+spx_status launch_uniform(const LaunchReq& r) {
+  switch (r.plan->uP) {
+    case 1: return launch_impl<T, DIM, OP, 1, 1, QOFF>(r);
+    case 2: return launch_impl<T, DIM, OP, 2, 2, QOFF>(r);
+    case 3: return launch_impl<T, DIM, OP, 3, 3, QOFF>(r);
+    case 4: return launch_impl<T, DIM, OP, 4, 4, QOFF>(r);
+    case 5: return launch_impl<T, DIM, OP, 5, 5, QOFF>(r);
+    case 6: return launch_impl<T, DIM, OP, 6, 6, QOFF>(r);
+    case 7: return launch_impl<T, DIM, OP, 7, 7, QOFF>(r);
+    case 8: return launch_impl<T, DIM, OP, 8, 8, QOFF>(r);
+    default: return fail(SPX_ERR_UNSUPPORTED, "order out of range");
+  }
+}
+
+template <typename T, int DIM, int OP>
+spx_status launch_typed(const LaunchReq& r) {
+  if (r.plan->uniform) {
+    return r.plan->qoff == 1 ? launch_uniform<T, DIM, OP, 1>(r) : launch_uniform<T, DIM, OP, 2>(r);
+  }
+  return r.plan->qoff == 1 ? launch_impl<T, DIM, OP, 1, kMaxP, 1>(r) : launch_impl<T, DIM, OP, 1, kMaxP, 2>(r);
+}
+
+}  // namespace spx
+
+#define SPX_DEFINE_LAUNCH_(TN, T, DIM, OP) \
+  spx_status spx::launch_##TN##_##DIM##_##OP(const spx::LaunchReq& r) { return spx::launch_typed<T, DIM, OP>(r); }
+#define SPX_DEFINE_LAUNCH(TN, T, DIM, OP) SPX_DEFINE_LAUNCH_(TN, T, DIM, OP)

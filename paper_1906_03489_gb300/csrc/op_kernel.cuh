@@ -1,0 +1,789 @@
+// Persistent, tile-based kernel for the elemental operators (§3.3 Collections,
+// SumFac strategy re-designed for one GB300).
+//
+// Work is a list of tiles; a tile is up to `eb` elements of one order P
+// (elements bucketed by order, §4.2).  Every CTA walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... and keeps `stages` tiles in flight:
+// one thread stages the next tiles' input blocks (coefficients, geometric
+// factors, coefficient fields) into a ring of shared-memory slots with 1D bulk
+// copies, while all threads evaluate the current tile by sum-factorisation
+// through padded shared-memory work buffers.  Outputs are stored straight to
+// HBM.  Basis tables B, dB, D of every order the kernel handles travel in the
+// kernel parameter block (constant bank).
+#pragma once
+#include "device_common.cuh"
+#include "kernel_params.h"
+
+namespace spx {
+
+// ---------------------------------------------------------------------------
+// Streams: which element blocks an operator reads.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct StreamDesc {
+  const T* base;   // nullptr: stream absent
+  int64_t len;     // values copied per element
+  int mult;        // element offset multiplier (block = mult * off_e values)
+  int64_t boff;    // offset of the copied part inside the element block
+  bool quad;       // off_e from quad offsets (else coefficient offsets)
+  bool whole;      // copies the entire block: consecutive elements are contiguous
+};
+
+template <typename T, int DIM, int OP, class Prm>
+__device__ __forceinline__ int op_streams(const Prm& p, int P, int Q, StreamDesc<T>* s) {
+  const int64_t nd = DIM == 3 ? int64_t(P + 1) * (P + 1) * (P + 1) : int64_t(P + 1) * (P + 1);
+  const int64_t qd = DIM == 3 ? int64_t(Q) * Q * Q : int64_t(Q) * Q;
+  constexpr int nf = DIM == 3 ? 7 : 4;
+  int k = 0;
+  switch (OP) {
+    case OP_BWD:
+      s[k++] = {p.in0, nd, 1, 0, false, true};
+      break;
+    case OP_IPROD:
+      s[k++] = {p.in0, qd, 1, 0, true, true};
+      s[k++] = {p.geom, qd, nf, (nf - 1) * qd, true, false};
+      break;
+    case OP_DERIV:
+      s[k++] = {p.in0, qd, 1, 0, true, true};
+      s[k++] = {p.geom, DIM * DIM * qd, DIM * DIM, 0, true, true};
+      break;
+    case OP_HELM:
+      s[k++] = {p.in0, nd, 1, 0, false, true};
+      s[k++] = {p.geom, nf * qd, nf, 0, true, true};
+      s[k++] = {p.lam_f, qd, 1, 0, true, true};
+      s[k++] = {p.kap_f, qd, 1, 0, true, true};
+      break;
+    case OP_ADJ:
+      s[k++] = {p.in0, nd, 1, 0, false, true};
+      s[k++] = {p.in1, nd, 1, 0, false, true};
+      s[k++] = {p.geom, nf * qd, nf, 0, true, true};
+      s[k++] = {p.lam_f, qd, 1, 0, true, true};
+      s[k++] = {p.kap_f, qd, 1, 0, true, true};
+      break;
+    case OP_DIAG:
+      s[k++] = {p.geom, nf * qd, nf, 0, true, true};
+      s[k++] = {p.lam_f, qd, 1, 0, true, true};
+      break;
+  }
+  return k;
+}
+
+// element offsets (uniform plans have no offset arrays)
+template <int DIM, class Prm>
+__device__ __forceinline__ int64_t coef_off_of(const Prm& p, int64_t e, int P) {
+  const int64_t n = P + 1;
+  return p.coef_off ? p.coef_off[e] : e * (DIM == 3 ? n * n * n : n * n);
+}
+template <int DIM, class Prm>
+__device__ __forceinline__ int64_t quad_off_of(const Prm& p, int64_t e, int Q) {
+  return p.quad_off ? p.quad_off[e] : e * (DIM == 3 ? int64_t(Q) * Q * Q : int64_t(Q) * Q);
+}
+template <class Prm>
+__device__ __forceinline__ int64_t elem_id(const Prm& p, const Tile& t, int j) {
+  return t.contig ? int64_t(p.ids ? p.ids[t.first] : t.first) + j : int64_t(p.ids ? p.ids[t.first + j] : t.first + j);
+}
+
+__device__ __forceinline__ uint32_t erb_bytes(int64_t len, int sz) {  // per-element region bytes
+  return static_cast<uint32_t>(((len * sz + 15) & ~int64_t(15)) + 16);
+}
+
+// Producer: stage tile `ti` into slot `slot` (thread 0 only).
+template <typename T, int DIM, int OP, int QOFF, class Prm>
+__device__ void issue_tile(const Prm& p, char* sm, uint64_t* bars, int slot, int ti) {
+  const Tile t = p.tiles[ti];
+  const int P = t.P, Q = t.P + QOFF;
+  StreamDesc<T> sd[5];
+  const int ns = op_streams<T, DIM, OP>(p, P, Q, sd);
+  char* slotp = sm + p.slot_base + slot * p.slot_bytes;
+  uint32_t tx = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) mbar_arrive_expect_tx(&bars[slot], tx);
+    for (int s = 0; s < ns; ++s) {
+      if (!sd[s].base) continue;
+      char* region = slotp + p.region_off[s];
+      if (t.contig && sd[s].whole) {
+        const int64_t e0 = elem_id(p, t, 0);
+        const int64_t off = sd[s].quad ? quad_off_of<DIM>(p, e0, Q) : coef_off_of<DIM>(p, e0, P);
+        const T* g = sd[s].base + sd[s].mult * off + sd[s].boff;
+        const uint32_t bytes = static_cast<uint32_t>(t.count * sd[s].len * sizeof(T));
+        if (pass == 0) tx += stage_bytes(g, bytes);
+        else stage_issue(region, g, bytes, &bars[slot]);
+      } else {
+        const uint32_t erb = erb_bytes(sd[s].len, sizeof(T));
+        for (int j = 0; j < t.count; ++j) {
+          const int64_t e = elem_id(p, t, j);
+          const int64_t off = sd[s].quad ? quad_off_of<DIM>(p, e, Q) : coef_off_of<DIM>(p, e, P);
+          const T* g = sd[s].base + sd[s].mult * off + sd[s].boff;
+          const uint32_t bytes = static_cast<uint32_t>(sd[s].len * sizeof(T));
+          if (pass == 0) tx += stage_bytes(g, bytes);
+          else stage_issue(region + j * erb, g, bytes, &bars[slot]);
+        }
+      }
+    }
+  }
+}
+
+// Per-tile context handed to the operator bodies.
+template <typename T>
+struct Ctx {
+  char* sm;
+  T* work[8];
+  const uint32_t* soff;   // [5][kMaxEB] value offsets of staged element data (relative to sm)
+  const int64_t* gcoef;   // [kMaxEB] coefficient offsets of the tile's elements
+  const int64_t* gquad;   // [kMaxEB] quadrature offsets
+  int ne, tid, nthr;
+  bool has_lam, has_kap;
+  T lam;
+  __device__ const T* staged(int s, int j) const { return reinterpret_cast<const T*>(sm) + soff[s * kMaxEB + j]; }
+};
+
+// Input / output element bases for the contraction loops.
+struct BaseStride {   // element e at e * es
+  int es;
+  __device__ __forceinline__ int64_t operator()(int e) const { return int64_t(e) * es; }
+};
+struct BaseTable32 {  // element e at t[e]
+  const uint32_t* t;
+  __device__ __forceinline__ int64_t operator()(int e) const { return t[e]; }
+};
+struct BaseTable64 {
+  const int64_t* t;
+  __device__ __forceinline__ int64_t operator()(int e) const { return t[e]; }
+};
+
+// General contraction (see device_common.cuh for the index convention) with
+// per-element bases, optional elementwise product of two inputs (PROD) and
+// store / accumulate (MODE 0 / 1).
+template <int AX, int N0, int N1, int N2, int M, bool TR, int MODE, bool PROD, int IS1, int IS2, int OS1, int OS2,
+          typename T, class IB, class IB2, class OB>
+__device__ __forceinline__ void contract_g(const T* __restrict__ in, IB ib, const T* __restrict__ in2, IB2 ib2,
+                                           T* __restrict__ out, OB ob, const T* __restrict__ A, int ne, int tid,
+                                           int nthr) {
+  constexpr int NA = AX == 0 ? N0 : (AX == 1 ? N1 : N2);
+  constexpr int OA = AX == 0 ? N1 : N0;
+  constexpr int OB_ = AX == 2 ? N1 : N2;
+  constexpr int NP = OA * OB_;
+  constexpr int ISA = AX == 0 ? 1 : (AX == 1 ? IS1 : IS2);
+  constexpr int OSA = AX == 0 ? 1 : (AX == 1 ? OS1 : OS2);
+  constexpr int ISa = AX == 0 ? IS1 : 1;
+  constexpr int OSa = AX == 0 ? OS1 : 1;
+  constexpr int ISb = AX == 2 ? IS1 : IS2;
+  constexpr int OSb = AX == 2 ? OS1 : OS2;
+  for (int pc = tid; pc < ne * NP; pc += nthr) {
+    const int e = pc / NP;
+    const int r = pc - e * NP;
+    const int b = r / OA;
+    const int a = r - b * OA;
+    const int lo = a * ISa + b * ISb;
+    const T* src = in + ib(e) + lo;
+    T* dst = out + ob(e) + a * OSa + b * OSb;
+    T v[NA];
+    if (PROD) {
+      const T* src2 = in2 + ib2(e) + lo;
+#pragma unroll
+      for (int c = 0; c < NA; ++c) v[c] = src[c * ISA] * src2[c * ISA];
+    } else {
+#pragma unroll
+      for (int c = 0; c < NA; ++c) v[c] = src[c * ISA];
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      T acc = MODE == 1 ? dst[m * OSA] : T(0);
+#pragma unroll
+      for (int c = 0; c < NA; ++c) acc = fma(TR ? A[c * M + m] : A[m * NA + c], v[c], acc);
+      dst[m * OSA] = acc;
+    }
+  }
+}
+
+// Fused pencil along axis 2 (3D) or axis 1 (2D): u = B v (n -> Q) stored to
+// U, and d = D u stored to Dd.
+template <int AX, int N0, int N1, int N2, int Q, int S1, int S2, int ES, typename T>
+__device__ __forceinline__ void bwd_and_deriv_pencil(const T* __restrict__ in, T* __restrict__ U, T* __restrict__ Dd,
+                                                     const T* __restrict__ B, const T* __restrict__ D, int ne,
+                                                     int tid, int nthr) {
+  // input extents (N0, N1, N2) with N_AX = n; output extent Q on AX.
+  constexpr int NA = AX == 1 ? N1 : N2;
+  constexpr int OA = N0;
+  constexpr int OB_ = AX == 2 ? N1 : N2;
+  constexpr int NP = OA * OB_;
+  constexpr int SA = AX == 1 ? S1 : S2;
+  constexpr int Sb = AX == 2 ? S1 : S2;
+  for (int pc = tid; pc < ne * NP; pc += nthr) {
+    const int e = pc / NP;
+    const int r = pc - e * NP;
+    const int b = r / OA;
+    const int a = r - b * OA;
+    const int base = e * ES + a + b * Sb;
+    T v[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) v[c] = in[base + c * SA];
+    T u[Q];
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < NA; ++c) acc = fma(B[m * NA + c], v[c], acc);
+      u[m] = acc;
+      U[base + m * SA] = acc;
+    }
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < Q; ++c) acc = fma(D[m * Q + c], u[c], acc);
+      Dd[base + m * SA] = acc;
+    }
+  }
+}
+
+// Fused pencil along the last axis for the transposed half of Helmholtz:
+// r = R + D^T G (Q values), z = B^T r (n values) stored to Z.
+template <int AX, int N0, int N1, int Q, int n, int S1, int S2, int ES, typename T>
+__device__ __forceinline__ void dt_and_bt_pencil(const T* __restrict__ R, const T* __restrict__ G, T* __restrict__ Z,
+                                                 const T* __restrict__ B, const T* __restrict__ D, int ne, int tid,
+                                                 int nthr) {
+  constexpr int OA = N0;
+  constexpr int OB_ = AX == 2 ? N1 : 1;
+  constexpr int NP = OA * OB_;
+  constexpr int SA = AX == 1 ? S1 : S2;
+  constexpr int Sb = AX == 2 ? S1 : S2;
+  for (int pc = tid; pc < ne * NP; pc += nthr) {
+    const int e = pc / NP;
+    const int r = pc - e * NP;
+    const int b = r / OA;
+    const int a = r - b * OA;
+    const int base = e * ES + a + b * Sb;
+    T g[Q], rr[Q];
+#pragma unroll
+    for (int c = 0; c < Q; ++c) {
+      g[c] = G[base + c * SA];
+      rr[c] = R[base + c * SA];
+    }
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      T acc = rr[m];
+#pragma unroll
+      for (int c = 0; c < Q; ++c) acc = fma(D[c * Q + m], g[c], acc);
+      rr[m] = acc;
+    }
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < Q; ++c) acc = fma(B[c * n + m], rr[c], acc);
+      Z[base + m * SA] = acc;
+    }
+  }
+}
+
+// ===========================================================================
+// Operator bodies.  Each returns after its last store; `release()` is called
+// once the staged inputs of the tile are no longer needed.
+// Table layout per order: B[Q][n], dB[Q][n], D[Q][Q].
+// ===========================================================================
+template <typename T, int DIM, int P, int Q>
+struct Shape {
+  static constexpr int n = P + 1;
+  static constexpr int S1 = Q | 1;                    // odd padded row stride
+  static constexpr int S2 = DIM == 3 ? S1 * Q : 0;
+  static constexpr int WS = DIM == 3 ? S1 * Q * Q : S1 * Q;
+  static constexpr int ND = DIM == 3 ? n * n * n : n * n;
+  static constexpr int QD = DIM == 3 ? Q * Q * Q : Q * Q;
+};
+
+#define SPX_SYNC() __syncthreads()
+
+// ---- BwdTrans -------------------------------------------------------------
+template <typename T, int DIM, int P, int Q, class Rel>
+__device__ void body_bwd(const T* tab, const Ctx<T>& c, T* out, Rel release) {
+  using S = Shape<T, DIM, P, Q>;
+  constexpr int n = S::n;
+  const T* B = tab;
+  BaseTable32 in0{c.soff};
+  if (DIM == 3) {
+    contract_g<0, n, n, n, Q, false, 0, false, n, n * n, S::S1, S::S2>(
+        reinterpret_cast<const T*>(c.sm), in0, (const T*)nullptr, in0, c.work[0], BaseStride{S::WS}, B, c.ne, c.tid,
+        c.nthr);
+    SPX_SYNC();
+    release();
+    contract_g<1, Q, n, n, Q, false, 0, false, S::S1, S::S2, S::S1, S::S2>(
+        c.work[0], BaseStride{S::WS}, (const T*)nullptr, BaseStride{0}, c.work[1], BaseStride{S::WS}, B, c.ne, c.tid,
+        c.nthr);
+    SPX_SYNC();
+    contract_g<2, Q, Q, n, Q, false, 0, false, S::S1, S::S2, Q, Q * Q>(
+        c.work[1], BaseStride{S::WS}, (const T*)nullptr, BaseStride{0}, out, BaseTable64{c.gquad}, B, c.ne, c.tid,
+        c.nthr);
+  } else {
+    contract_g<0, n, n, 1, Q, false, 0, false, n, 0, S::S1, 0>(reinterpret_cast<const T*>(c.sm), in0,
+                                                               (const T*)nullptr, in0, c.work[0], BaseStride{S::WS},
+                                                               B, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    release();
+    contract_g<1, Q, n, 1, Q, false, 0, false, S::S1, 0, Q, 0>(c.work[0], BaseStride{S::WS}, (const T*)nullptr,
+                                                               BaseStride{0}, out, BaseTable64{c.gquad}, B, c.ne,
+                                                               c.tid, c.nthr);
+  }
+}
+
+// ---- IProductWRTBase --------------------------------------------------------
+template <typename T, int DIM, int P, int Q, class Rel>
+__device__ void body_iprod(const T* tab, const Ctx<T>& c, T* out, Rel release) {
+  using S = Shape<T, DIM, P, Q>;
+  constexpr int n = S::n;
+  const T* B = tab;
+  BaseTable32 f{c.soff}, jw{c.soff + kMaxEB};
+  const T* sm = reinterpret_cast<const T*>(c.sm);
+  if (DIM == 3) {
+    // (f * JW) contracted along axis 2 with B^T
+    contract_g<2, Q, Q, Q, n, true, 0, true, Q, Q * Q, S::S1, S::S2>(sm, f, sm, jw, c.work[0], BaseStride{S::WS}, B,
+                                                                      c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    release();
+    contract_g<1, Q, Q, n, n, true, 0, false, S::S1, S::S2, S::S1, S::S2>(
+        c.work[0], BaseStride{S::WS}, (const T*)nullptr, BaseStride{0}, c.work[1], BaseStride{S::WS}, B, c.ne, c.tid,
+        c.nthr);
+    SPX_SYNC();
+    contract_g<0, Q, n, n, n, true, 0, false, S::S1, S::S2, n, n * n>(
+        c.work[1], BaseStride{S::WS}, (const T*)nullptr, BaseStride{0}, out, BaseTable64{c.gcoef}, B, c.ne, c.tid,
+        c.nthr);
+  } else {
+    contract_g<1, Q, Q, 1, n, true, 0, true, Q, 0, S::S1, 0>(sm, f, sm, jw, c.work[0], BaseStride{S::WS}, B, c.ne,
+                                                              c.tid, c.nthr);
+    SPX_SYNC();
+    release();
+    contract_g<0, Q, n, 1, n, true, 0, false, S::S1, 0, n, 0>(c.work[0], BaseStride{S::WS}, (const T*)nullptr,
+                                                              BaseStride{0}, out, BaseTable64{c.gcoef}, B, c.ne,
+                                                              c.tid, c.nthr);
+  }
+}
+
+// ---- PhysDeriv --------------------------------------------------------------
+template <typename T, int DIM, int P, int Q, class Rel>
+__device__ void body_deriv(const T* tab, const Ctx<T>& c, T* o0, T* o1, T* o2, Rel release) {
+  using S = Shape<T, DIM, P, Q>;
+  constexpr int n = S::n;
+  const T* D = tab + 2 * Q * n;
+  BaseTable32 f{c.soff};
+  const T* sm = reinterpret_cast<const T*>(c.sm);
+  constexpr int QD = S::QD;
+  if (DIM == 3) {
+    contract_g<0, Q, Q, Q, Q, false, 0, false, Q, Q * Q, S::S1, S::S2>(sm, f, sm, f, c.work[0], BaseStride{S::WS},
+                                                                        D, c.ne, c.tid, c.nthr);
+    contract_g<1, Q, Q, Q, Q, false, 0, false, Q, Q * Q, S::S1, S::S2>(sm, f, sm, f, c.work[1], BaseStride{S::WS},
+                                                                        D, c.ne, c.tid, c.nthr);
+    contract_g<2, Q, Q, Q, Q, false, 0, false, Q, Q * Q, S::S1, S::S2>(sm, f, sm, f, c.work[2], BaseStride{S::WS},
+                                                                        D, c.ne, c.tid, c.nthr);
+  } else {
+    contract_g<0, Q, Q, 1, Q, false, 0, false, Q, 0, S::S1, 0>(sm, f, sm, f, c.work[0], BaseStride{S::WS}, D, c.ne,
+                                                               c.tid, c.nthr);
+    contract_g<1, Q, Q, 1, Q, false, 0, false, Q, 0, S::S1, 0>(sm, f, sm, f, c.work[1], BaseStride{S::WS}, D, c.ne,
+                                                               c.tid, c.nthr);
+  }
+  SPX_SYNC();
+  T* outs[3] = {o0, o1, o2};
+  for (int pt = c.tid; pt < c.ne * QD; pt += c.nthr) {
+    const int e = pt / QD;
+    const int q = pt - e * QD;
+    const int i = q % Q;
+    const int j = (q / Q) % Q;
+    const int k = DIM == 3 ? q / (Q * Q) : 0;
+    const int w = e * S::WS + i + j * S::S1 + k * S::S2;
+    const T* X = c.staged(1, e) + q;  // dxi_a/dx_m blocks
+    T r[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) r[a] = c.work[a][w];
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) {
+      T acc = T(0);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) acc = fma(X[(a * DIM + m) * QD], r[a], acc);
+      outs[m][c.gquad[e] + q] = acc;
+    }
+  }
+  (void)release;
+}
+
+// ---- Helmholtz --------------------------------------------------------------
+template <typename T, int DIM, int P, int Q, class Rel>
+__device__ void body_helm(const T* tab, const Ctx<T>& c, T* out, Rel release) {
+  using S = Shape<T, DIM, P, Q>;
+  constexpr int n = S::n, S1 = S::S1, S2 = S::S2, WS = S::WS, QD = S::QD;
+  const T* B = tab;
+  const T* D = tab + 2 * Q * n;
+  BaseTable32 in0{c.soff};
+  const T* sm = reinterpret_cast<const T*>(c.sm);
+  T *W0 = c.work[0], *W1 = c.work[1], *W2 = c.work[2], *W3 = c.work[3];
+  if (DIM == 3) {
+    contract_g<0, n, n, n, Q, false, 0, false, n, n * n, S1, S2>(sm, in0, sm, in0, W0, BaseStride{WS}, B, c.ne,
+                                                                  c.tid, c.nthr);
+    SPX_SYNC();
+    contract_g<1, Q, n, n, Q, false, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, W0, BaseStride{WS}, W1,
+                                                                BaseStride{WS}, B, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    bwd_and_deriv_pencil<2, Q, Q, n, Q, S1, S2, WS>(W1, W2, W3, B, D, c.ne, c.tid, c.nthr);  // U -> W2, d2 -> W3
+    SPX_SYNC();
+    contract_g<0, Q, Q, Q, Q, false, 0, false, S1, S2, S1, S2>(W2, BaseStride{WS}, W2, BaseStride{WS}, W0,
+                                                                BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    contract_g<1, Q, Q, Q, Q, false, 0, false, S1, S2, S1, S2>(W2, BaseStride{WS}, W2, BaseStride{WS}, W1,
+                                                                BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+  } else {
+    contract_g<0, n, n, 1, Q, false, 0, false, n, 0, S1, 0>(sm, in0, sm, in0, W0, BaseStride{WS}, B, c.ne, c.tid,
+                                                             c.nthr);
+    SPX_SYNC();
+    bwd_and_deriv_pencil<1, Q, n, 1, Q, S1, 0, WS>(W0, W2, W3, B, D, c.ne, c.tid, c.nthr);  // U -> W2, d1 -> W3
+    SPX_SYNC();
+    contract_g<0, Q, Q, 1, Q, false, 0, false, S1, 0, S1, 0>(W2, BaseStride{WS}, W2, BaseStride{WS}, W0,
+                                                              BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+  }
+  // pointwise: W2 <- lambda JW u; (W0, W1, W3) <- kappa G grad u  (2D: W0, W3)
+  constexpr int nf = DIM == 3 ? 7 : 4;
+  for (int pt = c.tid; pt < c.ne * QD; pt += c.nthr) {
+    const int e = pt / QD;
+    const int q = pt - e * QD;
+    const int i = q % Q;
+    const int j = (q / Q) % Q;
+    const int k = DIM == 3 ? q / (Q * Q) : 0;
+    const int w = e * WS + i + j * S1 + k * S2;
+    const T* G = c.staged(1, e) + q;
+    const T kap = c.has_kap ? c.staged(3, e)[q] : T(1);
+    const T lam = c.has_lam ? c.staged(2, e)[q] : c.lam;
+    if (DIM == 3) {
+      const T d0 = W0[w], d1 = W1[w], d2 = W3[w];
+      const T g00 = G[0], g01 = G[QD], g02 = G[2 * QD], g11 = G[3 * QD], g12 = G[4 * QD], g22 = G[5 * QD];
+      const T jw = G[6 * QD];
+      W0[w] = kap * (g00 * d0 + g01 * d1 + g02 * d2);
+      W1[w] = kap * (g01 * d0 + g11 * d1 + g12 * d2);
+      W3[w] = kap * (g02 * d0 + g12 * d1 + g22 * d2);
+      W2[w] = lam * jw * W2[w];
+    } else {
+      const T d0 = W0[w], d1 = W3[w];
+      const T g00 = G[0], g01 = G[QD], g11 = G[2 * QD], jw = G[3 * QD];
+      W0[w] = kap * (g00 * d0 + g01 * d1);
+      W3[w] = kap * (g01 * d0 + g11 * d1);
+      W2[w] = lam * jw * W2[w];
+    }
+  }
+  (void)nf;
+  SPX_SYNC();
+  release();
+  if (DIM == 3) {
+    contract_g<0, Q, Q, Q, Q, true, 1, false, S1, S2, S1, S2>(W0, BaseStride{WS}, W0, BaseStride{WS}, W2,
+                                                               BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    contract_g<1, Q, Q, Q, Q, true, 1, false, S1, S2, S1, S2>(W1, BaseStride{WS}, W1, BaseStride{WS}, W2,
+                                                               BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    dt_and_bt_pencil<2, Q, Q, Q, n, S1, S2, WS>(W2, W3, W0, B, D, c.ne, c.tid, c.nthr);  // -> W0 (Q,Q,n)
+    SPX_SYNC();
+    contract_g<1, Q, Q, n, n, true, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, W0, BaseStride{WS}, W1,
+                                                               BaseStride{WS}, B, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    contract_g<0, Q, n, n, n, true, 0, false, S1, S2, n, n * n>(W1, BaseStride{WS}, W1, BaseStride{WS}, out,
+                                                                 BaseTable64{c.gcoef}, B, c.ne, c.tid, c.nthr);
+  } else {
+    contract_g<0, Q, Q, 1, Q, true, 1, false, S1, 0, S1, 0>(W0, BaseStride{WS}, W0, BaseStride{WS}, W2,
+                                                             BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    dt_and_bt_pencil<1, Q, 1, Q, n, S1, 0, WS>(W2, W3, W1, B, D, c.ne, c.tid, c.nthr);  // -> W1 (Q,n)
+    SPX_SYNC();
+    contract_g<0, Q, n, 1, n, true, 0, false, S1, 0, n, 0>(W1, BaseStride{WS}, W1, BaseStride{WS}, out,
+                                                            BaseTable64{c.gcoef}, B, c.ne, c.tid, c.nthr);
+  }
+}
+
+// ---- BwdTrans and reference gradient of one staged coefficient stream -----
+// U -> Wu, d_a -> Wd[a]; 3D uses scratch Wt.
+template <typename T, int DIM, int P, int Q>
+__device__ void bwd_grad(const T* tab, const Ctx<T>& c, BaseTable32 src, T* Wt, T* Wu, T* Wd0, T* Wd1, T* Wd2) {
+  using S = Shape<T, DIM, P, Q>;
+  constexpr int n = S::n, S1 = S::S1, S2 = S::S2, WS = S::WS;
+  const T* B = tab;
+  const T* D = tab + 2 * Q * n;
+  const T* sm = reinterpret_cast<const T*>(c.sm);
+  if (DIM == 3) {
+    contract_g<0, n, n, n, Q, false, 0, false, n, n * n, S1, S2>(sm, src, sm, src, Wt, BaseStride{WS}, B, c.ne,
+                                                                  c.tid, c.nthr);
+    SPX_SYNC();
+    contract_g<1, Q, n, n, Q, false, 0, false, S1, S2, S1, S2>(Wt, BaseStride{WS}, Wt, BaseStride{WS}, Wd0,
+                                                                BaseStride{WS}, B, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    bwd_and_deriv_pencil<2, Q, Q, n, Q, S1, S2, WS>(Wd0, Wu, Wd2, B, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    contract_g<0, Q, Q, Q, Q, false, 0, false, S1, S2, S1, S2>(Wu, BaseStride{WS}, Wu, BaseStride{WS}, Wd0,
+                                                                BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    contract_g<1, Q, Q, Q, Q, false, 0, false, S1, S2, S1, S2>(Wu, BaseStride{WS}, Wu, BaseStride{WS}, Wd1,
+                                                                BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+  } else {
+    contract_g<0, n, n, 1, Q, false, 0, false, n, 0, S1, 0>(sm, src, sm, src, Wt, BaseStride{WS}, B, c.ne, c.tid,
+                                                             c.nthr);
+    SPX_SYNC();
+    bwd_and_deriv_pencil<1, Q, n, 1, Q, S1, 0, WS>(Wt, Wu, Wd1, B, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+    contract_g<0, Q, Q, 1, Q, false, 0, false, S1, 0, S1, 0>(Wu, BaseStride{WS}, Wu, BaseStride{WS}, Wd0,
+                                                              BaseStride{WS}, D, c.ne, c.tid, c.nthr);
+    SPX_SYNC();
+  }
+  (void)Wd2;
+}
+
+// ---- Adjoint with respect to lambda(x) and kappa(x) ----------------------
+template <typename T, int DIM, int P, int Q, class Rel>
+__device__ void body_adj(const T* tab, const Ctx<T>& c, T* glam, T* gkap, Rel release) {
+  using S = Shape<T, DIM, P, Q>;
+  constexpr int S1 = S::S1, S2 = S::S2, WS = S::WS, QD = S::QD;
+  T** W = const_cast<T**>(c.work);
+  // u: U -> W[1], grad -> W[2..4]; g: U -> W[5], grad -> W[6], W[7], W[0]
+  bwd_grad<T, DIM, P, Q>(tab, c, BaseTable32{c.soff}, W[0], W[1], W[2], W[3], W[4]);
+  bwd_grad<T, DIM, P, Q>(tab, c, BaseTable32{c.soff + kMaxEB}, W[0], W[5], W[6], W[7], W[0]);
+  // in 2D the g gradient lives in W[6], W[7]; in 3D d2 of g was written to W[0]
+  for (int pt = c.tid; pt < c.ne * QD; pt += c.nthr) {
+    const int e = pt / QD;
+    const int q = pt - e * QD;
+    const int i = q % Q;
+    const int j = (q / Q) % Q;
+    const int k = DIM == 3 ? q / (Q * Q) : 0;
+    const int w = e * WS + i + j * S1 + k * S2;
+    const T* G = c.staged(2, e) + q;
+    const int64_t o = c.gquad[e] + q;
+    if (DIM == 3) {
+      const T du0 = W[2][w], du1 = W[3][w], du2 = W[4][w];
+      const T dg0 = W[6][w], dg1 = W[7][w], dg2 = W[0][w];
+      const T g00 = G[0], g01 = G[QD], g02 = G[2 * QD], g11 = G[3 * QD], g12 = G[4 * QD], g22 = G[5 * QD];
+      const T jw = G[6 * QD];
+      if (glam) glam[o] = jw * W[5][w] * W[1][w];
+      if (gkap)
+        gkap[o] = dg0 * (g00 * du0 + g01 * du1 + g02 * du2) + dg1 * (g01 * du0 + g11 * du1 + g12 * du2) +
+                  dg2 * (g02 * du0 + g12 * du1 + g22 * du2);
+    } else {
+      const T du0 = W[2][w], du1 = W[3][w];
+      const T dg0 = W[6][w], dg1 = W[7][w];
+      const T g00 = G[0], g01 = G[QD], g11 = G[2 * QD], jw = G[3 * QD];
+      if (glam) glam[o] = jw * W[5][w] * W[1][w];
+      if (gkap) gkap[o] = dg0 * (g00 * du0 + g01 * du1) + dg1 * (g01 * du0 + g11 * du1);
+    }
+  }
+  (void)release;
+}
+
+// ---- Diagonal of the elemental Helmholtz matrices ------------------------
+// diag_pqr = sum_ijk F_t[ijk] A0_t[i,p] A1_t[j,q] A2_t[k,r] over the terms
+// t: lambda JW with (B^2, B^2, B^2) and G_ab with (dB^2 or B dB in the
+// differentiated directions, B^2 elsewhere), off-diagonal G_ab counted twice.
+template <typename T, int DIM, int P, int Q, class Rel>
+__device__ void body_diag(const T* tab, const Ctx<T>& c, T* out, Rel release) {
+  using S = Shape<T, DIM, P, Q>;
+  constexpr int n = S::n, S1 = S::S1, S2 = S::S2, WS = S::WS, QD = S::QD;
+  // squared tables in work buffer 4: BB, dd, Bd each [Q][n]
+  T* tabs = c.work[4];
+  for (int t = c.tid; t < Q * n; t += c.nthr) {
+    const T b = tab[t], d = tab[Q * n + t];
+    tabs[t] = b * b;
+    tabs[Q * n + t] = d * d;
+    tabs[2 * Q * n + t] = b * d;
+  }
+  const T* BB = tabs;
+  const T* dd = tabs + Q * n;
+  const T* Bd = tabs + 2 * Q * n;
+  T *W0 = c.work[0], *W1 = c.work[1], *W2 = c.work[2], *W3 = c.work[3];
+  constexpr int NT = DIM == 3 ? 7 : 4;
+  for (int term = 0; term < NT; ++term) {
+    SPX_SYNC();
+    // field of this term into W3 (padded layout)
+    for (int pt = c.tid; pt < c.ne * QD; pt += c.nthr) {
+      const int e = pt / QD;
+      const int q = pt - e * QD;
+      const int i = q % Q;
+      const int j = (q / Q) % Q;
+      const int k = DIM == 3 ? q / (Q * Q) : 0;
+      const T* G = c.staged(0, e) + q;
+      T v;
+      if (DIM == 3) {
+        const int fi[7] = {6, 0, 3, 5, 1, 2, 4};
+        v = G[fi[term] * QD];
+        if (term == 0) v *= c.has_lam ? c.staged(1, e)[q] : c.lam;
+        if (term >= 4) v *= T(2);
+      } else {
+        const int fi[4] = {3, 0, 2, 1};
+        v = G[fi[term] * QD];
+        if (term == 0) v *= c.has_lam ? c.staged(1, e)[q] : c.lam;
+        if (term == 3) v *= T(2);
+      }
+      W3[e * WS + i + j * S1 + k * S2] = v;
+    }
+    SPX_SYNC();
+    // matrices per axis for this term
+    const T* A0;
+    const T* A1;
+    const T* A2;
+    if (DIM == 3) {
+      switch (term) {
+        case 0: A0 = BB; A1 = BB; A2 = BB; break;
+        case 1: A0 = dd; A1 = BB; A2 = BB; break;   // G00
+        case 2: A0 = BB; A1 = dd; A2 = BB; break;   // G11
+        case 3: A0 = BB; A1 = BB; A2 = dd; break;   // G22
+        case 4: A0 = Bd; A1 = Bd; A2 = BB; break;   // G01
+        case 5: A0 = Bd; A1 = BB; A2 = Bd; break;   // G02
+        default: A0 = BB; A1 = Bd; A2 = Bd; break;  // G12
+      }
+      contract_g<2, Q, Q, Q, n, true, 0, false, S1, S2, S1, S2>(W3, BaseStride{WS}, W3, BaseStride{WS}, W0,
+                                                                 BaseStride{WS}, A2, c.ne, c.tid, c.nthr);
+      SPX_SYNC();
+      contract_g<1, Q, Q, n, n, true, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, W0, BaseStride{WS}, W1,
+                                                                 BaseStride{WS}, A1, c.ne, c.tid, c.nthr);
+      SPX_SYNC();
+      if (term == 0)
+        contract_g<0, Q, n, n, n, true, 0, false, S1, S2, S1, S2>(W1, BaseStride{WS}, W1, BaseStride{WS}, W2,
+                                                                   BaseStride{WS}, A0, c.ne, c.tid, c.nthr);
+      else
+        contract_g<0, Q, n, n, n, true, 1, false, S1, S2, S1, S2>(W1, BaseStride{WS}, W1, BaseStride{WS}, W2,
+                                                                   BaseStride{WS}, A0, c.ne, c.tid, c.nthr);
+    } else {
+      switch (term) {
+        case 0: A0 = BB; A1 = BB; break;
+        case 1: A0 = dd; A1 = BB; break;
+        case 2: A0 = BB; A1 = dd; break;
+        default: A0 = Bd; A1 = Bd; break;
+      }
+      A2 = nullptr;
+      contract_g<1, Q, Q, 1, n, true, 0, false, S1, 0, S1, 0>(W3, BaseStride{WS}, W3, BaseStride{WS}, W1,
+                                                               BaseStride{WS}, A1, c.ne, c.tid, c.nthr);
+      SPX_SYNC();
+      if (term == 0)
+        contract_g<0, Q, n, 1, n, true, 0, false, S1, 0, S1, 0>(W1, BaseStride{WS}, W1, BaseStride{WS}, W2,
+                                                                 BaseStride{WS}, A0, c.ne, c.tid, c.nthr);
+      else
+        contract_g<0, Q, n, 1, n, true, 1, false, S1, 0, S1, 0>(W1, BaseStride{WS}, W1, BaseStride{WS}, W2,
+                                                                 BaseStride{WS}, A0, c.ne, c.tid, c.nthr);
+    }
+    (void)A2;
+  }
+  SPX_SYNC();
+  release();
+  constexpr int ND = S::ND;
+  for (int pt = c.tid; pt < c.ne * ND; pt += c.nthr) {
+    const int e = pt / ND;
+    const int l = pt - e * ND;
+    const int p = l % n;
+    const int q = (l / n) % n;
+    const int r = DIM == 3 ? l / (n * n) : 0;
+    out[c.gcoef[e] + l] = W2[e * WS + p + q * S1 + r * S2];
+  }
+}
+
+// ===========================================================================
+// The kernel.
+// ===========================================================================
+template <typename T, int DIM, int OP, int P, int Q, class Prm, class Rel>
+__device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel) {
+  const T* tab = p.tab + Prm::Layout::off(P);
+  if constexpr (OP == OP_BWD) body_bwd<T, DIM, P, Q>(tab, c, p.out0, rel);
+  else if constexpr (OP == OP_IPROD) body_iprod<T, DIM, P, Q>(tab, c, p.out0, rel);
+  else if constexpr (OP == OP_DERIV) body_deriv<T, DIM, P, Q>(tab, c, p.out0, p.out1, p.out2, rel);
+  else if constexpr (OP == OP_HELM) body_helm<T, DIM, P, Q>(tab, c, p.out0, rel);
+  else if constexpr (OP == OP_ADJ) body_adj<T, DIM, P, Q>(tab, c, p.out0, p.out1, rel);
+  else body_diag<T, DIM, P, Q>(tab, c, p.out0, rel);
+}
+
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, class Prm, class Rel>
+__device__ __forceinline__ void dispatch_order(int P, const Prm& p, const Ctx<T>& c, Rel rel) {
+  if constexpr (PLO <= PHI) {
+    if (P == PLO) run_body<T, DIM, OP, PLO, PLO + QOFF>(p, c, rel);
+    else dispatch_order<T, DIM, OP, PLO + 1, PHI, QOFF>(P, p, c, rel);
+  }
+}
+
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>
+__global__ void __launch_bounds__(1024) op_kernel(const __grid_constant__ KParams<T, PLO, PHI, QOFF> p) {
+  extern __shared__ __align__(128) char sm[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
+  uint32_t* soff = reinterpret_cast<uint32_t*>(sm + p.meta_base);
+  int64_t* gcoef = reinterpret_cast<int64_t*>(sm + p.meta_base + 5 * kMaxEB * 4);
+  int64_t* gquad = gcoef + kMaxEB;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int S = p.stages;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      const int ti = blockIdx.x + s * gridDim.x;
+      if (ti < p.n_tiles) issue_tile<T, DIM, OP, QOFF>(p, sm, bars, s, ti);
+    }
+  }
+  Ctx<T> c;
+  c.sm = sm;
+  for (int w = 0; w < 8; ++w) c.work[w] = reinterpret_cast<T*>(sm + p.work_base + w * p.work_bytes);
+  c.soff = soff;
+  c.gcoef = gcoef;
+  c.gquad = gquad;
+  c.tid = tid;
+  c.nthr = nthr;
+  c.has_lam = p.lam_f != nullptr;
+  c.has_kap = p.kap_f != nullptr;
+  c.lam = static_cast<T>(p.lam);
+  for (int k = 0;; ++k) {
+    const int ti = blockIdx.x + k * gridDim.x;
+    if (ti >= p.n_tiles) break;
+    const int slot = k % S;
+    const bool ok = mbar_wait(&bars[slot], (k / S) & 1);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(p.status, kStatusTimeout);
+      return;
+    }
+    const Tile t = p.tiles[ti];
+    const int P = t.P, Q = t.P + QOFF;
+    c.ne = t.count;
+    // per-tile metadata: element offsets and staged-data offsets
+    StreamDesc<T> sd[5];
+    const int ns = op_streams<T, DIM, OP>(p, P, Q, sd);
+    char* slotp = sm + p.slot_base + slot * p.slot_bytes;
+    for (int j = tid; j < t.count; j += nthr) {
+      const int64_t e = elem_id(p, t, j);
+      gcoef[j] = coef_off_of<DIM>(p, e, P);
+      gquad[j] = quad_off_of<DIM>(p, e, Q);
+      for (int s = 0; s < ns; ++s) {
+        if (!sd[s].base) continue;
+        char* region = slotp + p.region_off[s];
+        const int64_t off = sd[s].quad ? gquad[j] : gcoef[j];
+        const T* g = sd[s].base + sd[s].mult * off + sd[s].boff;
+        char* at;
+        if (t.contig && sd[s].whole) {
+          const int64_t e0 = elem_id(p, t, 0);
+          const int64_t off0 = sd[s].quad ? quad_off_of<DIM>(p, e0, Q) : coef_off_of<DIM>(p, e0, P);
+          const T* g0 = sd[s].base + sd[s].mult * off0 + sd[s].boff;
+          at = region + (reinterpret_cast<uintptr_t>(g0) & 15) + (g - g0) * sizeof(T);
+          // head / tail words of the whole-tile range
+          if (j == 0)
+            stage_fixup<sizeof(T)>(region, g0, static_cast<uint32_t>(t.count * sd[s].len * sizeof(T)), 0, 1);
+        } else {
+          char* r = region + j * erb_bytes(sd[s].len, sizeof(T));
+          at = r + (reinterpret_cast<uintptr_t>(g) & 15);
+          stage_fixup<sizeof(T)>(r, g, static_cast<uint32_t>(sd[s].len * sizeof(T)), 0, 1);
+        }
+        soff[s * kMaxEB + j] = static_cast<uint32_t>((at - sm) / sizeof(T));
+      }
+    }
+    __syncthreads();
+    bool released = false;
+    auto rel = [&]() {
+      if (!released) {
+        released = true;
+        if (tid == 0 && ti + S * gridDim.x < p.n_tiles) {
+          fence_proxy_async();
+          issue_tile<T, DIM, OP, QOFF>(p, sm, bars, slot, ti + S * gridDim.x);
+        }
+      }
+    };
+    dispatch_order<T, DIM, OP, PLO, PHI, QOFF>(P, p, c, rel);
+    __syncthreads();
+    rel();
+  }
+}
+
+}  // namespace spx

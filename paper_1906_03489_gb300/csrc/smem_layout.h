@@ -1,0 +1,79 @@
+// Shared-memory layout of the operator kernel (host side).
+#pragma once
+#include <algorithm>
+#include <cstdint>
+
+#include "spx_internal.h"
+
+namespace spx {
+
+inline int n_work_buffers(int op) {
+  switch (op) {
+    case OP_BWD: return 2;
+    case OP_IPROD: return 2;
+    case OP_DERIV: return 3;
+    case OP_HELM: return 4;
+    case OP_ADJ: return 8;
+    default: return 5;
+  }
+}
+
+// Host mirror of op_streams(): value counts per element of each stream slot,
+// 0 when the stream is absent.
+inline void stream_lens(int op, int dim, int P, int Q, bool lam_f, bool kap_f, int64_t lens[5]) {
+  const int64_t nd = dim == 3 ? int64_t(P + 1) * (P + 1) * (P + 1) : int64_t(P + 1) * (P + 1);
+  const int64_t qd = dim == 3 ? int64_t(Q) * Q * Q : int64_t(Q) * Q;
+  const int nf = dim == 3 ? 7 : 4;
+  for (int s = 0; s < 5; ++s) lens[s] = 0;
+  switch (op) {
+    case OP_BWD: lens[0] = nd; break;
+    case OP_IPROD: lens[0] = qd; lens[1] = qd; break;
+    case OP_DERIV: lens[0] = qd; lens[1] = dim * dim * qd; break;
+    case OP_HELM:
+      lens[0] = nd; lens[1] = nf * qd; lens[2] = lam_f ? qd : 0; lens[3] = kap_f ? qd : 0;
+      break;
+    case OP_ADJ:
+      lens[0] = nd; lens[1] = nd; lens[2] = nf * qd; lens[3] = lam_f ? qd : 0; lens[4] = kap_f ? qd : 0;
+      break;
+    default: lens[0] = nf * qd; lens[1] = lam_f ? qd : 0; break;
+  }
+}
+
+struct SmemLayout {
+  uint32_t slot_base, slot_bytes, region_off[5], work_base, work_bytes, meta_base, total;
+};
+
+inline uint32_t up128(uint64_t x) { return static_cast<uint32_t>((x + 127) & ~uint64_t(127)); }
+
+inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const LaunchCfg& cfg, bool lam_f, bool kap_f) {
+  SmemLayout L{};
+  uint64_t region[5] = {0, 0, 0, 0, 0};
+  uint64_t work = 0;
+  for (int P = 1; P <= kMaxP; ++P) {
+    if (!plan->present[P]) continue;
+    const int Q = P + plan->qoff;
+    const int eb = cfg.order[P].eb;
+    int64_t lens[5];
+    stream_lens(op, plan->dim, P, Q, lam_f, kap_f, lens);
+    for (int s = 0; s < 5; ++s)
+      if (lens[s]) region[s] = std::max<uint64_t>(region[s], uint64_t(eb) * (((lens[s] * sz + 15) & ~int64_t(15)) + 16));
+    const int S1 = Q | 1;
+    const uint64_t ws = plan->dim == 3 ? uint64_t(S1) * Q * Q : uint64_t(S1) * Q;
+    work = std::max<uint64_t>(work, uint64_t(eb) * ws * sz);
+    if (op == OP_DIAG) work = std::max<uint64_t>(work, uint64_t(3) * Q * (P + 1) * sz);
+  }
+  L.slot_base = 128;
+  uint64_t off = 0;
+  for (int s = 0; s < 5; ++s) {
+    L.region_off[s] = static_cast<uint32_t>(off);
+    off += up128(region[s]);
+  }
+  L.slot_bytes = static_cast<uint32_t>(off);
+  L.work_base = L.slot_base + cfg.stages * L.slot_bytes;
+  L.work_bytes = up128(work);
+  L.meta_base = L.work_base + n_work_buffers(op) * L.work_bytes;
+  L.total = L.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8;
+  return L;
+}
+
+}  // namespace spx

@@ -1,0 +1,110 @@
+// Internal host-side declarations of the spx library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/spx.h"
+#include "kernel_params.h"
+
+namespace spx {
+
+spx_status fail(spx_status s, const std::string& msg);   // records the message, returns s
+spx_status cuda_fail(cudaError_t e, const char* what);    // maps a CUDA error
+
+struct TileCfg {
+  int eb = 0;  // elements per tile for this order
+};
+
+struct LaunchCfg {
+  int nthreads = 256;
+  int stages = 2;
+  TileCfg order[kMaxP1];
+};
+
+struct TileList {
+  Tile* d = nullptr;   // device
+  int n = 0;
+  bool dirty = true;
+};
+
+}  // namespace spx
+
+struct spx_plan {
+  int dim = 3;
+  int64_t E = 0;
+  int qoff = 2;
+  bool uniform = true;
+  int uP = 0;                            // order of a uniform plan
+  std::vector<int32_t> orders;           // host [E]
+  std::vector<int64_t> coef_off, quad_off;  // host [E+1]
+  int64_t n_coef = 0, n_quad = 0;
+  bool present[spx::kMaxP1] = {};
+  std::vector<int32_t> ids;              // host: element ids bucketed by order (var plans)
+  std::vector<int64_t> bucket_start;     // host: start of each order's bucket in ids
+  int device = 0;
+  int num_sms = 0;
+  size_t max_smem = 0;
+  // device metadata (owned)
+  int64_t* d_coef_off = nullptr;
+  int64_t* d_quad_off = nullptr;
+  int32_t* d_ids = nullptr;
+  int* d_status = nullptr;
+  // per operator and precision
+  spx::LaunchCfg cfg[spx::OP_KINDS][2];
+  spx::TileList tiles[spx::OP_KINDS][2];
+  // caller-owned geometry, per precision
+  const void* geom[2] = {nullptr, nullptr};
+  const void* dxi[2] = {nullptr, nullptr};
+  // host basis tables (FP64) per order: B[Q][n], dB[Q][n], D[Q][Q]
+  std::vector<double> tab[spx::kMaxP1];
+};
+
+namespace spx {
+
+// Launch request for one operator call.
+struct LaunchReq {
+  const spx_plan* plan;
+  int op;
+  int dtype;  // 0 FP64, 1 FP32
+  const void* in0;
+  const void* in1;
+  const void* geom;
+  const void* lam_f;
+  const void* kap_f;
+  void* out0;
+  void* out1;
+  void* out2;
+  double lam;
+  cudaStream_t stream;
+};
+
+// Builds (if needed) the tile list of (op, dtype) on the device.  Synchronous.
+spx_status ensure_tiles(spx_plan* plan, int op, int dtype);
+
+// Per-(T, DIM, OP) launchers; each lives in its own translation unit.
+#define SPX_DECL_LAUNCH(TN, DIM, OP) spx_status launch_##TN##_##DIM##_##OP(const LaunchReq& r);
+#define SPX_DECL_ALL_OPS(TN, DIM) \
+  SPX_DECL_LAUNCH(TN, DIM, 0)     \
+  SPX_DECL_LAUNCH(TN, DIM, 1)     \
+  SPX_DECL_LAUNCH(TN, DIM, 2)     \
+  SPX_DECL_LAUNCH(TN, DIM, 3)     \
+  SPX_DECL_LAUNCH(TN, DIM, 4)     \
+  SPX_DECL_LAUNCH(TN, DIM, 5)
+SPX_DECL_ALL_OPS(f64, 2)
+SPX_DECL_ALL_OPS(f64, 3)
+SPX_DECL_ALL_OPS(f32, 2)
+SPX_DECL_ALL_OPS(f32, 3)
+
+spx_status launch_op(const LaunchReq& r);
+
+// Shared-memory footprint of (op, dtype) with the plan's current tile
+// configuration; 0 if the tile does not fit.
+size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& cfg);
+
+// Basis tables (host FP64): fills B, dB, D as documented in spx.h.
+spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* dB, double* D);
+
+}  // namespace spx

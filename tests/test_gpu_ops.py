@@ -1,0 +1,216 @@
+"""GPU parity of the elemental operators against the FP64 oracle.
+
+Every comparison is element by element on seeded inputs.  Tolerances:
+relative max error (max |y - y_ref| / max |y_ref|) <= 1e-12 for FP64 kernels
+and <= 1e-5 for FP32 kernels.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1906_03489_gb300 as spx
+from oracle import operators
+from paper_1906_03489_gb300 import synth
+
+from _cases import Case, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+DTYPES = [torch.float64, torch.float32]
+
+# (dim, N, P, amp): several tiles with a ragged tail, both dimensions, the
+# order range 1..8 and both Q = P+2 (default) and Q = P+1
+SHAPES = [(3, 3, 4, 0.05), (3, 5, 2, 0.05), (3, 2, 8, 0.05), (3, 3, 1, 0.05), (3, 4, 6, 0.05),
+          (2, 16, 4, 0.0), (2, 7, 3, 0.05), (2, 5, 8, 0.05), (2, 3, 1, 0.0)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _case(dim, N, P, amp, q_offset=2):
+    return Case(dim, N, P=P, amp=amp, q_offset=q_offset)
+
+
+@pytest.mark.parametrize("dim,N,P,amp", SHAPES)
+def test_geometry_factors(dim, N, P, amp):
+    c = _case(dim, N, P, amp)
+    geom, dxi, xq = c.om.factors_flat()
+    assert rel_err(c.g["geom"], geom) <= 1e-12
+    assert rel_err(c.g["dxi"], dxi) <= 1e-12
+    assert rel_err(c.g["xq"], xq) <= 1e-12
+    assert rel_err(c.g["geom32"], geom) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dim,N,P,amp", SHAPES)
+def test_bwd_trans(dim, N, P, amp, dtype):
+    c = _case(dim, N, P, amp)
+    u, ut = c.coef(1, dtype)
+    ref = operators.bwd_trans(c.om, u)
+    assert rel_err(spx.bwd_trans(c.plan, ut), ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dim,N,P,amp", SHAPES)
+def test_iproduct(dim, N, P, amp, dtype):
+    c = _case(dim, N, P, amp)
+    f, ft = c.quad(2, dtype)
+    ref = operators.iproduct(c.om, f)
+    assert rel_err(spx.iproduct(c.plan, ft), ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dim,N,P,amp", SHAPES)
+def test_phys_deriv(dim, N, P, amp, dtype):
+    c = _case(dim, N, P, amp)
+    f, ft = c.quad(3, dtype)
+    refs = operators.phys_deriv(c.om, f)
+    outs = spx.phys_deriv(c.plan, ft)
+    scale = max(np.abs(r).max() for r in refs)
+    for o, r in zip(outs, refs):
+        assert np.abs(o.cpu().double().numpy() - r).max() / scale <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dim,N,P,amp", SHAPES)
+def test_helmholtz(dim, N, P, amp, dtype):
+    c = _case(dim, N, P, amp)
+    u, ut = c.coef(4, dtype)
+    ref = operators.helmholtz(c.om, u, lam=1.0)
+    assert rel_err(spx.helmholtz(c.plan, ut, lam=1.0), ref) <= TOL[dtype]
+    ref2 = operators.helmholtz(c.om, u, lam=2.5)
+    assert rel_err(spx.helmholtz(c.plan, ut, lam=2.5), ref2) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dim,N,P", [(3, 3, 4), (2, 4, 5), (3, 2, 7)])
+def test_helmholtz_with_fields(dim, N, P, dtype):
+    c = _case(dim, N, P, 0.05)
+    u, ut = c.coef(5, dtype)
+    lam = 1.0 + 0.5 * synth.uniform(synth.rng(6), c.plan.n_quad)
+    kap = 1.0 + 0.3 * synth.uniform(synth.rng(7), c.plan.n_quad)
+    ref = operators.helmholtz(c.om, u, lam_field=lam, kappa_field=kap)
+    lt = torch.tensor(lam, device="cuda", dtype=dtype)
+    kt = torch.tensor(kap, device="cuda", dtype=dtype)
+    assert rel_err(spx.helmholtz(c.plan, ut, lam_field=lt, kappa_field=kt), ref) <= TOL[dtype]
+    refk = operators.helmholtz(c.om, u, lam=0.7, kappa_field=kap)
+    assert rel_err(spx.helmholtz(c.plan, ut, lam=0.7, kappa_field=kt), refk) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_q_offset_one(dtype):
+    c = _case(3, 3, 3, 0.05, q_offset=1)
+    u, ut = c.coef(8, dtype)
+    assert rel_err(spx.helmholtz(c.plan, ut), operators.helmholtz(c.om, u)) <= TOL[dtype]
+    assert rel_err(spx.bwd_trans(c.plan, ut), operators.bwd_trans(c.om, u)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("dim,N", [(3, 5), (2, 9)])
+def test_variable_order(dim, N, dtype):
+    gen = synth.rng(3)
+    orders = synth.orders(gen, N ** dim, 1, 8)
+    c = Case(dim, N, orders=orders, amp=0.05)
+    u, ut = c.coef(9, dtype)
+    f, ft = c.quad(10, dtype)
+    assert rel_err(spx.helmholtz(c.plan, ut), operators.helmholtz(c.om, u)) <= TOL[dtype]
+    assert rel_err(spx.bwd_trans(c.plan, ut), operators.bwd_trans(c.om, u)) <= TOL[dtype]
+    assert rel_err(spx.iproduct(c.plan, ft), operators.iproduct(c.om, f)) <= TOL[dtype]
+    refs = operators.phys_deriv(c.om, f)
+    outs = spx.phys_deriv(c.plan, ft)
+    scale = max(np.abs(r).max() for r in refs)
+    for o, r in zip(outs, refs):
+        assert np.abs(o.cpu().double().numpy() - r).max() / scale <= TOL[dtype]
+
+
+def test_variable_order_equals_uniform_launches():
+    """One variable-order launch gives, element by element, what uniform launches give."""
+    dim, N = 3, 4
+    orders = synth.orders(synth.rng(11), N ** dim, 2, 5)
+    c = Case(dim, N, orders=orders, amp=0.05)
+    u, ut = c.coef(12, torch.float64)
+    y = spx.helmholtz(c.plan, ut).cpu().numpy()
+    for P in np.unique(orders):
+        cu = Case(dim, N, P=int(P), amp=0.05)
+        # uniform-order input holding u_e on the elements of this order
+        uu = np.zeros(cu.plan.n_coef)
+        n = (int(P) + 1) ** dim
+        for e in np.nonzero(orders == P)[0]:
+            uu[e * n:(e + 1) * n] = u[c.plan.coef_off[e]:c.plan.coef_off[e + 1]]
+        yu = spx.helmholtz(cu.plan, torch.tensor(uu, device="cuda")).cpu().numpy()
+        for e in np.nonzero(orders == P)[0]:
+            np.testing.assert_array_equal(y[c.plan.coef_off[e]:c.plan.coef_off[e + 1]], yu[e * n:(e + 1) * n])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_bitwise_reproducible(dtype):
+    c = _case(3, 4, 4, 0.05)
+    _, ut = c.coef(13, dtype)
+    a = spx.helmholtz(c.plan, ut)
+    b = spx.helmholtz(c.plan, ut)
+    assert torch.equal(a, b)
+
+
+def test_empty_and_single_element():
+    p = spx.Plan(3, 0, order=4)
+    assert p.n_coef == 0 and p.n_quad == 0
+    z = torch.zeros(0, dtype=torch.float64, device="cuda")
+    spx.helmholtz(p, z, out=torch.zeros(0, dtype=torch.float64, device="cuda"))
+    c = _case(3, 1, 4, 0.0)
+    u, ut = c.coef(14)
+    assert rel_err(spx.helmholtz(c.plan, ut), operators.helmholtz(c.om, u)) <= 1e-12
+
+
+@pytest.mark.parametrize("eb,nthreads,stages", [(1, 64, 1), (3, 128, 2), (7, 192, 3), (16, 512, 2), (64, 1024, 1)])
+def test_tile_shapes_do_not_change_results(eb, nthreads, stages):
+    c = _case(3, 5, 3, 0.05)
+    u, ut = c.coef(15)
+    ref = operators.helmholtz(c.om, u)
+    for op in ("helmholtz", "bwd_trans"):
+        try:
+            c.plan.set_tile(op, torch.float64, eb, nthreads, stages)
+        except spx.SpxError as e:
+            assert e.status == 2   # tile does not fit: unsupported, reported
+            continue
+    assert rel_err(spx.helmholtz(c.plan, ut), ref) <= 1e-12
+    assert rel_err(spx.bwd_trans(c.plan, ut), operators.bwd_trans(c.om, u)) <= 1e-12
+
+
+def test_autotune_keeps_results():
+    c = _case(3, 6, 4, 0.05)
+    u, ut = c.coef(16, torch.float32)
+    out = torch.empty(c.plan.n_coef, dtype=torch.float32, device="cuda")
+    c.plan.autotune("helmholtz", torch.float32, ut, out, reps=2)
+    eb, nt, st = c.plan.get_tile("helmholtz", torch.float32, 4)
+    assert 1 <= eb <= 64 and nt % 32 == 0 and 1 <= st <= 4
+    assert rel_err(spx.helmholtz(c.plan, ut), operators.helmholtz(c.om, u)) <= 1e-5
+
+
+def test_unaligned_buffers():
+    """Element blocks at arbitrary 8-byte offsets (views into larger buffers)."""
+    c = _case(3, 3, 3, 0.05)
+    u, _ = c.coef(17)
+    big = torch.zeros(c.plan.n_coef + 3, dtype=torch.float64, device="cuda")
+    big[1:1 + c.plan.n_coef] = torch.tensor(u, device="cuda")
+    out = torch.zeros(c.plan.n_coef + 3, dtype=torch.float64, device="cuda")
+    spx.helmholtz(c.plan, big[1:1 + c.plan.n_coef], out=out[3:3 + c.plan.n_coef])
+    assert rel_err(out[3:3 + c.plan.n_coef], operators.helmholtz(c.om, u)) <= 1e-12
+
+
+def test_invalid_arguments_are_reported():
+    c = _case(3, 2, 3, 0.05)
+    _, ut = c.coef(18)
+    with pytest.raises(spx.SpxError):
+        spx.helmholtz(c.plan, ut, out=ut)            # aliasing
+    p2 = spx.Plan(3, 8, order=3)
+    with pytest.raises(spx.SpxError):
+        spx.helmholtz(p2, ut)                          # geometry not registered
+    with pytest.raises(spx.SpxError):
+        spx.Plan(3, 8, order=9)                        # order out of range
+    with pytest.raises(spx.SpxError):
+        spx.Plan(4, 8, order=3)                        # bad dimension
+    assert c.plan.device_status() == 0

@@ -1,0 +1,501 @@
+#!/usr/bin/env python
+"""Benchmark of the spectral/hp Helmholtz operator on GB300.
+
+A step is one application of the Helmholtz operator H = lambda M + L (BwdTrans,
+reference gradient, pointwise geometric factors, transposed gradient and
+IProductWRTBase fused in one kernel launch) to every element of the workload
+mesh: by default 32^3 curved hexes, P = 4, Q = 6, the operator applied in FP32
+(the precision whose roofline is HBM).  Prints one JSON line.
+
+Besides the timed steps it reports, each measured separately after the timed
+region: the FP64 apply of the same workload (ALU roofline), PhysDeriv, the
+variable-order workload (24^3 hexes, P_e in 2..8), the adjoint workload (16^3
+hexes, P = 6) and the periodic solve of the 48^3 workload to a 1e-10 relative
+residual in FP32-inner + FP64 refinement and in all-FP64 CG.
+
+Multi-GPU (torchrun, one rank per GPU): every rank applies the operator to
+its own copy of the workload (independent element partitions, no exchange):
+weak scaling; value = all ranks' DOFs / max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle (dense elemental matrices) on a
+bounded sample of the same workload on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Helmholtz apply GDOF/s and % HBM roofline; CG time-to-1e-10 FP32+refine vs FP64"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 ALU peak: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def helm_bytes_per_elem(P, Q, sz, dim=3):
+    n = P + 1
+    return (2 * n ** dim + (7 if dim == 3 else 4) * Q ** dim) * sz
+
+
+def helm_flops_per_elem(P, Q):
+    n = P + 1
+    bwd = n ** 3 * Q + n ** 2 * Q ** 2 + n * Q ** 3
+    return 2 * (2 * bwd + 6 * Q ** 4) + 20 * Q ** 3
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for d in (os.path.join(ROOT, "paper_1906_03489_gb300", "csrc"), os.path.join(ROOT, "include")):
+        for name in sorted(os.listdir(d)):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_digest") == kernel_digest():
+            return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(name, spx, mesh, synth, torch, copies=1):
+    w = synth.WORKLOADS[name]
+    dim, N, amp = w["dim"], w["N"], w["amp"]
+    E = N ** dim
+    gen = synth.rng(w["seed"])
+    if isinstance(w["P"], tuple):
+        orders = synth.orders(gen, E, *w["P"])
+        plans = [spx.Plan(dim, E, orders=orders) for _ in range(copies)]
+        node_orders = orders
+    else:
+        plans = [spx.Plan(dim, E, order=w["P"]) for _ in range(copies)]
+        node_orders = w["P"]
+    nodes = mesh.structured_nodes(dim, N, node_orders, amp)
+    geoms = []
+    for p in plans:
+        g = spx.geom_factors(p, nodes)
+        p.set_geometry(torch.float64, g["geom"], g["dxi"])
+        p.set_geometry(torch.float32, g["geom32"], g["dxi32"])
+        geoms.append(g)
+    coef = synth.uniform(gen, plans[0].n_coef)
+    return w, plans, geoms, coef
+
+
+def timed(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_ours(a):
+    import torch
+    import paper_1906_03489_gb300 as spx
+    from paper_1906_03489_gb300 import mesh, synth
+
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (there is no CPU path)")
+    spx.lib()
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    name = a.workload
+    w, plans, geoms, coef = make_workload(name, spx, mesh, synth, torch, copies=2)
+    P, Q = w["P"], w["P"] + 2
+    E = plans[0].E
+    dt = torch.float32
+    u = [torch.tensor(coef, device="cuda", dtype=dt) for _ in plans]
+    out = [torch.empty_like(x) for x in u]
+    if a.tile:
+        eb, nt, st = (int(x) for x in a.tile.split(","))
+        for p in plans:
+            p.set_tile("helmholtz", dt, eb, nt, st)
+    else:
+        plans[0].autotune("helmholtz", dt, u[0], out[0], reps=5)
+        tile = plans[0].get_tile("helmholtz", dt, P)
+        plans[1].set_tile("helmholtz", dt, *tile)
+    tile = plans[0].get_tile("helmholtz", dt, P)
+
+    def step(i):
+        k = i & 1
+        spx.helmholtz(plans[k], u[k], lam=1.0, out=out[k])
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(a.steps):
+            step(i)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    barrier(world)
+    ms = max_over_ranks(ms, world)
+    dofs = E * (P + 1) ** 3
+    value = world * dofs / (ms * 1e-3) / 1e9
+    bytes_launch = E * helm_bytes_per_elem(P, Q, 4)
+    achieved = bytes_launch / (ms * 1e-3) / 1e9
+    traffic = profiled_traffic("helmholtz_f32_hex32.txt")
+
+    # end to end through the C ABI with host buffers: H2D of u, apply, D2H of y
+    uh = torch.tensor(coef, dtype=dt).pin_memory()
+    yh = torch.empty(plans[0].n_coef, dtype=dt).pin_memory()
+    ud, yd = torch.empty_like(u[0]), torch.empty_like(u[0])
+
+    def e2e_step():
+        ud.copy_(uh, non_blocking=True)
+        spx.helmholtz(plans[0], ud, lam=1.0, out=yd)
+        yh.copy_(yd, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    k_e2e = max(10, a.steps // 10)
+    ms_e2e = max_over_ranks(timed(e2e_step, k_e2e, stream), world)
+    e2e_value = world * dofs / (ms_e2e * 1e-3) / 1e9
+
+    extras = {}
+    if a.extras and rank == 0:
+        extras = measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(name, seconds=a.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GDOF/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "mesh": f"{w['N']}^3 curved hexes (x'=x+{w['amp']} sin2piy sin2piz)",
+                       "P": P, "Q": Q, "elements_per_gpu": E, "local_dofs_per_gpu": dofs,
+                       "op": "Helmholtz H=lambda M+L, lambda=1, unassembled, FP32 FMA/FP32 accumulate",
+                       "tile_eb_threads_stages": list(tile),
+                       "l2": f"inputs {2 * bytes_launch / 1e6:.0f} MB per step pair alternate between two "
+                             f"independent copies (> {L2_BYTES / 1e6:.0f} MB L2): no L2 flush",
+                       "parallelism": f"replica per GPU x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": bytes_launch,
+                         "bytes_model": "per element (2 (P+1)^3 coefficients + 7 Q^3 geometric factors) x 4 B"},
+            "e2e": {"value": round(e2e_value, 3), "unit": "GDOF/s", "h2d_bytes_per_step": int(uh.numel() * 4),
+                    "d2h_bytes_per_step": int(yh.numel() * 4), "ms_per_step": round(ms_e2e, 4)},
+            "gpu_launches": a.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak):
+    """Other operators / precisions / workloads, each timed after warm-up with CUDA events."""
+    ex = {}
+    plan = plans[0]
+    P, Q, E = 4, 6, plan.E
+    reps = 30
+    # FP64 Helmholtz: ALU bound
+    u64 = torch.tensor(coef, device="cuda")
+    o64 = torch.empty_like(u64)
+    plan.autotune("helmholtz", torch.float64, u64, o64, reps=3)
+    ms = timed(lambda: spx.helmholtz(plan, u64, out=o64), reps, stream)
+    fl = E * helm_flops_per_elem(P, Q)
+    ex["fp64"] = {"helmholtz_gdofs": round(E * 125 / ms / 1e6, 3), "ms": round(ms, 4),
+                  "roofline": {"bound": "alu", "achieved": round(fl / ms / 1e9, 4),
+                               "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                               "frac": round(fl / ms / 1e9 / FP64_PEAK_TFLOPS, 4),
+                               "flops_per_launch": fl},
+                  "hbm_frac": round(E * helm_bytes_per_elem(P, Q, 8) / ms / 1e6 / hbm_peak, 4)}
+    # PhysDeriv, BwdTrans, IProduct (FP32 and FP64)
+    ops = {}
+    for dt, sz in ((torch.float32, 4), (torch.float64, 8)):
+        f = spx.bwd_trans(plan, torch.tensor(coef, device="cuda", dtype=dt))
+        outs = [torch.empty_like(f) for _ in range(3)]
+        c = torch.empty(plan.n_coef, dtype=dt, device="cuda")
+        tag = "f32" if dt == torch.float32 else "f64"
+        for op, fn, nbytes in (
+                ("phys_deriv", lambda: spx.phys_deriv(plan, f, outs), E * 13 * Q ** 3 * sz),
+                ("bwd_trans", lambda: spx.bwd_trans(plan, c, f), E * (125 + Q ** 3) * sz),
+                ("iproduct", lambda: spx.iproduct(plan, f, c), E * (2 * Q ** 3 + 125) * sz)):
+            fn()
+            ms = timed(fn, reps, stream)
+            ops[f"{op}_{tag}"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+                                  "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4)}
+    ex["ops_hex32"] = ops
+    # variable order workload
+    wv, pv, gv, cv = make_workload("hex3d_24_varp", spx, mesh, synth, torch)
+    pv = pv[0]
+    nb = sum(helm_bytes_per_elem(int(p_), int(p_) + 2, 1) for p_ in pv.orders)
+    var = {}
+    for dt, sz in ((torch.float32, 4), (torch.float64, 8)):
+        uu = torch.tensor(cv, device="cuda", dtype=dt)
+        oo = torch.empty_like(uu)
+        pv.autotune("helmholtz", dt, uu, oo, reps=2)
+        ms = timed(lambda: spx.helmholtz(pv, uu, out=oo), reps, stream)
+        tag = "f32" if dt == torch.float32 else "f64"
+        var[tag] = {"ms": round(ms, 4), "gdofs": round(pv.n_coef / ms / 1e6, 3),
+                    "gbs": round(nb * sz / ms / 1e6, 1), "hbm_frac": round(nb * sz / ms / 1e6 / hbm_peak, 4),
+                    "tiles_eb_by_order": {int(p_): pv.get_tile("helmholtz", dt, int(p_))[0]
+                                          for p_ in sorted(set(pv.orders.tolist()))}}
+    ex["varp_hex24"] = var
+    del pv, gv
+    # adjoint workload
+    wa, pa, ga, ca = make_workload("hex3d_16_p6", spx, mesh, synth, torch)
+    pa, ga = pa[0], ga[0]
+    X = ga["xq"].reshape(pa.E, 3, 512)
+    lam = (1.0 + 0.5 * torch.sin(torch.pi * X[:, 0])).reshape(-1).contiguous()
+    kap = (1.0 + 0.3 * torch.cos(torch.pi * X[:, 1])).reshape(-1).contiguous()
+    uu = torch.tensor(ca, device="cuda", requires_grad=True)
+    ff = torch.tensor(synth.uniform(synth.rng(41), pa.n_coef), device="cuda")
+    lp, kp = lam.clone().requires_grad_(True), kap.clone().requires_grad_(True)
+
+    def fwd_bwd():
+        y = spx.helmholtz_ad(pa, uu, lp, kp)
+        loss = 0.5 * ((y - ff) ** 2).sum()
+        loss.backward()
+
+    fwd_bwd()
+    ms = timed(fwd_bwd, 10, stream)
+    ex["adjoint_hex16_p6"] = {"fwd_bwd_ms": round(ms, 3)}
+    del pa, ga
+    # periodic solve of the 48^3 workload
+    ex["cg_hex48"] = measure_cg(spx, mesh, synth, torch)
+    return ex
+
+
+def measure_cg(spx, mesh, synth, torch):
+    import numpy as np
+    w = synth.WORKLOADS["hex3d_48_p4"]
+    N, P = w["N"], w["P"]
+    plan = spx.Plan(3, N ** 3, order=P)
+    g = spx.geom_factors(plan, mesh.structured_nodes(3, N, P, w["amp"]))
+    plan.set_geometry(torch.float64, g["geom"], g["dxi"])
+    plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])
+    l2g, ng = mesh.periodic_l2g(3, N, P)
+    X = g["xq"].reshape(plan.E, 3, 216)
+    u_star = torch.prod(torch.sin(2 * np.pi * X), dim=1).reshape(-1).contiguous()
+    f = spx.assemble(plan, l2g, spx.iproduct(plan, (1.0 + 12 * np.pi ** 2) * u_star), ng)
+    u32 = torch.empty(plan.n_coef, dtype=torch.float32, device="cuda")
+    plan.autotune("helmholtz", torch.float32, u32.uniform_(), torch.empty_like(u32), reps=3)
+    u64 = torch.rand(plan.n_coef, dtype=torch.float64, device="cuda")
+    plan.autotune("helmholtz", torch.float64, u64, torch.empty_like(u64), reps=2)
+    ws = torch.empty(max(spx.cg_workspace_bytes(plan, ng, p) for p in ("f64", "f32_refine")), dtype=torch.uint8,
+                     device="cuda")
+    res = {"global_dofs": ng, "local_dofs": plan.n_coef, "tol": 1e-10}
+    for prec in ("f32_refine", "f64"):
+        spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision=prec, workspace=ws, maxit=5,
+                     raise_on_fail=False)  # warm-up (graphs, tiles)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision=prec, workspace=ws)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        uh = spx.bwd_trans(plan, spx.gather(plan, l2g, x))
+        res[prec] = {"time_s": round(t, 4), "iters": info["iters"], "outer_iters": info["outer_iters"],
+                     "rel_residual": info["rel_residual"], "status": info["status"],
+                     "max_err_vs_exact": (uh - u_star).abs().max().item()}
+    res["speedup_f32_refine_vs_f64"] = round(res["f64"]["time_s"] / res["f32_refine"]["time_s"], 3)
+    return res
+
+
+def oracle_sample_rate(name, n_elem_sample, seconds, repeat=None):
+    """Times the oracle's dense Helmholtz on a sample of the workload's elements."""
+    import numpy as np
+    from oracle import operators
+    from oracle.geometry import StructuredMesh
+    from paper_1906_03489_gb300 import synth
+    w = synth.WORKLOADS[name]
+    P, Q = w["P"], w["P"] + 2
+    # a sub-mesh of the same elements (same order, quadrature and curvature)
+    n_side = max(1, round(n_elem_sample ** (1.0 / 3.0)))
+    m = StructuredMesh(3, n_side, P, amp=w["amp"])
+    m.geometry(P, Q, np.arange(m.E))          # geometry precomputed, as on the GPU
+    u = synth.uniform(synth.rng(w["seed"]), m.coef_off[-1])
+    operators.helmholtz(m, u)                  # warm-up
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        operators.helmholtz(m, u)
+        reps += 1
+        el = time.perf_counter() - t0
+        if (repeat is not None and reps >= repeat) or (repeat is None and el >= seconds):
+            break
+    return m.E * (P + 1) ** 3 * reps / el / 1e9, m.E, reps, el
+
+
+def cpu_baseline(name, seconds=15.0):
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    rate, ne, reps, el = oracle_sample_rate(name, 4096, seconds)
+    return {"value": round(rate, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"dense FP64 oracle Helmholtz on a {ne}-element sub-mesh of the same curved P=4 hexes, "
+                      f"{reps} applies in {el:.1f} s (numpy/OpenBLAS, {cores} threads)"}
+
+
+def run_reference(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    name = a.workload
+    # warm-up steps, then K timed steps; each step = one dense apply on the sample
+    rate, ne, reps, el = oracle_sample_rate(name, 512, None, repeat=max(1, a.steps))
+    ms = el / max(1, reps) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": round(rate, 6), "unit": "GDOF/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "sample_elements": ne},
+            "cpu_baseline": {"value": round(rate, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+                             "sample": f"dense FP64 oracle Helmholtz, {ne}-element sub-mesh of the same "
+                                       f"curved hexes per step"},
+            "e2e": {"value": round(rate, 6), "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hex3d_32_p4")
+    ap.add_argument("--tile", default=None, help="eb,threads,stages (skips autotuning)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    a = ap.parse_args()
+    a.warmup = max(3, a.warmup)
+    if a.impl == "reference":
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", os.environ["OMP_NUM_THREADS"])
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -137,8 +137,9 @@ spx_status spx_plan_device_status(spx_plan *plan, int *status, int reset);
 spx_status spx_plan_set_geometry(spx_plan *plan, spx_dtype dtype, const void *geom, const void *dxi_dx);
 
 /* Overrides the launch tile of one operator/precision/order: elements per
- * batch `eb` (1..64), threads per block `nthreads` (32..1024, multiple of
- * 32) and pipeline depth `stages` (1..4).  order = -1 sets every order. */
+ * batch `eb` (1..64), threads per block `nthreads` (32..512, multiple of
+ * 32; the 3D Helmholtz operator uses eb * Q^2 threads instead) and pipeline
+ * depth `stages` (1..4).  order = -1 sets every order. */
 spx_status spx_plan_set_tile(spx_plan *plan, spx_op op, spx_dtype dtype, int order, int eb, int nthreads,
                              int stages);
 
@@ -229,6 +230,14 @@ spx_status spx_helmholtz_diag(const spx_plan *plan, spx_dtype dtype, double lamb
  * sets bit 1 (value 2) of the plan's device status word. */
 spx_status spx_gather(const spx_plan *plan, spx_dtype dtype, const int32_t *l2g, int64_t n_global,
                       const void *global, void *local, void *stream);
+
+/* global[g] = sum of local[l] over l with l2g[l] = g (global is
+ * overwritten; n_global entries).  Sums with FP atomics, so the order of the
+ * additions (and the last bits of the result) may vary between calls; the CG
+ * solver uses its own deterministic assembly.  Out-of-range entries of l2g
+ * are skipped and set bit 1 of the plan's device status word. */
+spx_status spx_assemble(const spx_plan *plan, spx_dtype dtype, const int32_t *l2g, int64_t n_global,
+                        const void *local, void *global, void *stream);
 
 /* Options of spx_cg_solve. */
 typedef struct {

@@ -7,5 +7,6 @@ fields behind ``torch.autograd``; periodic C0 assembly and a mixed-precision
 Jacobi-PCG solver.
 """
 from ._lib import SpxError, lib  # noqa: F401
-from .binding import (Plan, basis_tables, bwd_trans, cg_solve, cg_workspace_bytes, gather,  # noqa: F401
-                      geom_factors, helmholtz, helmholtz_adjoint, helmholtz_diag, iproduct, phys_deriv)
+from .binding import (Plan, assemble, basis_tables, bwd_trans, cg_solve, cg_workspace_bytes,  # noqa: F401
+                      gather, geom_factors, helmholtz, helmholtz_adjoint, helmholtz_diag, iproduct, phys_deriv)
+from .autograd import HelmholtzFn, helmholtz_ad  # noqa: F401

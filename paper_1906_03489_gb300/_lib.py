@@ -63,6 +63,7 @@ SIGNATURES = {
     "spx_helmholtz_adjoint": (I32, [P, P, P, P, P, P]),
     "spx_helmholtz_diag": (I32, [P, I32, D, P, P]),
     "spx_gather": (I32, [P, I32, P, I64, P, P, P]),
+    "spx_assemble": (I32, [P, I32, P, I64, P, P, P]),
     "spx_cg_workspace_bytes": (I32, [P, I64, C.POINTER(CgOpts), C.POINTER(C.c_size_t)]),
     "spx_cg_solve": (I32, [P, D, P, I64, P, P, P, C.c_size_t, C.POINTER(CgOpts), C.POINTER(CgResult), P]),
 }

@@ -12,7 +12,7 @@ import torch
 from ._lib import SPX_F32, SPX_F64, OPS, CgOpts, CgResult, PlanDesc, SpxError, check, lib
 
 __all__ = ["Plan", "basis_tables", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz",
-           "helmholtz_adjoint", "helmholtz_diag", "gather", "cg_workspace_bytes", "cg_solve", "SpxError"]
+           "helmholtz_adjoint", "helmholtz_diag", "gather", "assemble", "cg_workspace_bytes", "cg_solve", "SpxError"]
 
 
 def _p(t):
@@ -185,6 +185,16 @@ def gather(plan, l2g, xg, out=None):
     return out
 
 
+def assemble(plan, l2g, local, n_global, out=None):
+    """global[g] = sum over local entries mapped to g (FP atomics)."""
+    _dev(l2g, "l2g")
+    _dev(local, "local")
+    out = torch.empty(int(n_global), dtype=local.dtype, device=local.device) if out is None else out
+    check(lib().spx_assemble(plan.handle, _code(local.dtype), _p(l2g), int(n_global), _p(local), _p(out),
+                             _stream()))
+    return out
+
+
 def _cg_opts(tol, maxit, precision, inner_tol, max_outer, use_graph, check_every):
     o = CgOpts()
     o.tol, o.maxit = float(tol), int(maxit)
@@ -210,7 +220,7 @@ def cg_solve(plan, lam, l2g, n_global, f, x0=None, tol=1e-10, maxit=10000, preci
     o = _cg_opts(tol, maxit, precision, inner_tol, max_outer, use_graph, check_every)
     nb = C.c_size_t()
     check(lib().spx_cg_workspace_bytes(plan.handle, int(n_global), C.byref(o), C.byref(nb)))
-    if workspace is None or workspace.numel() < nb.value:
+    if workspace is None:
         workspace = torch.empty(nb.value, dtype=torch.uint8, device=f.device)
     x = torch.zeros_like(f) if x0 is None else x0.clone()
     res = CgResult()

@@ -257,8 +257,8 @@ spx_status spx_plan_set_tile(spx_plan* p, spx_op op, spx_dtype dt, int order, in
   if (!p) return fail(SPX_ERR_INVALID_ARG, "set_tile: NULL plan");
   if (op < 0 || op >= OP_KINDS || (dt != SPX_F64 && dt != SPX_F32))
     return fail(SPX_ERR_INVALID_ARG, "set_tile: bad operator or dtype");
-  if (eb < 1 || eb > kMaxEB || nthreads < 32 || nthreads > 1024 || nthreads % 32 || stages < 1 || stages > 4)
-    return fail(SPX_ERR_INVALID_ARG, "set_tile: eb 1..64, nthreads 32..1024 (multiple of 32), stages 1..4");
+  if (eb < 1 || eb > kMaxEB || nthreads < 32 || nthreads > 512 || nthreads % 32 || stages < 1 || stages > 4)
+    return fail(SPX_ERR_INVALID_ARG, "set_tile: eb 1..64, nthreads 32..512 (multiple of 32), stages 1..4");
   if (order != -1 && (order < 1 || order > kMaxP)) return fail(SPX_ERR_INVALID_ARG, "set_tile: order outside 1..8");
   LaunchCfg c = p->cfg[op][dt];
   c.nthreads = nthreads;

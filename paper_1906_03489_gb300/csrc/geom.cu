@@ -300,6 +300,18 @@ __global__ void gather_kernel(const int32_t* __restrict__ l2g, const T* __restri
   }
 }
 
+template <typename T>
+__global__ void assemble_atomic(const int32_t* __restrict__ l2g, const T* __restrict__ loc, T* __restrict__ g,
+                                int64_t n, int64_t ng, int* status) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t k = l2g[i];
+    if (k >= 0 && k < ng)
+      atomicAdd(&g[k], loc[i]);
+    else
+      atomicOr(status, kStatusBadIndex);
+  }
+}
+
 }  // namespace spx
 
 using namespace spx;
@@ -345,4 +357,26 @@ extern "C" spx_status spx_gather(const spx_plan* plan, spx_dtype dt, const int32
     return fail(SPX_ERR_INVALID_ARG, "gather: bad dtype");
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPX_OK : cuda_fail(e, "gather kernel launch");
+}
+
+extern "C" spx_status spx_assemble(const spx_plan* plan, spx_dtype dt, const int32_t* l2g, int64_t n_global,
+                                   const void* local, void* global, void* stream) {
+  if (!plan || !l2g || n_global < 0 || (plan->n_coef && !local) || (n_global && !global))
+    return fail(SPX_ERR_INVALID_ARG, "assemble: bad argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t sz = dt == SPX_F64 ? 8 : 4;
+  if (dt != SPX_F64 && dt != SPX_F32) return fail(SPX_ERR_INVALID_ARG, "assemble: bad dtype");
+  cudaError_t e = cudaMemsetAsync(global, 0, n_global * sz, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  const int64_t n = plan->n_coef;
+  if (n == 0) return SPX_OK;
+  const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, int64_t(plan->num_sms) * 16));
+  if (dt == SPX_F64)
+    assemble_atomic<double><<<grid, 256, 0, st>>>(l2g, static_cast<const double*>(local), static_cast<double*>(global),
+                                                  n, n_global, plan->d_status);
+  else
+    assemble_atomic<float><<<grid, 256, 0, st>>>(l2g, static_cast<const float*>(local), static_cast<float*>(global), n,
+                                                 n_global, plan->d_status);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e, "assemble kernel launch");
 }

@@ -62,12 +62,20 @@ spx_status launch_impl(const LaunchReq& r) {
       configured = plan->max_smem;
     }
   }
+  int nthr = cfg.nthreads;
+  if (OP == OP_HELM && DIM == 3) {  // one thread per quadrature column
+    nthr = 0;
+    for (int P = PLO; P <= PHI; ++P)
+      if (plan->present[P]) nthr = std::max(nthr, cfg.order[P].eb * (P + QOFF) * (P + QOFF));
+    nthr = (nthr + 31) / 32 * 32;
+    if (nthr > 512) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile needs more than 512 threads");
+  }
   int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, cfg.nthreads, L.total);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthr, L.total);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "operator tile does not fit on an SM");
   const int grid = std::min<int64_t>(tl.n, int64_t(nb) * plan->num_sms);
-  kern<<<grid, cfg.nthreads, L.total, r.stream>>>(p);
+  kern<<<grid, nthr, L.total, r.stream>>>(p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "operator kernel launch");
   return SPX_OK;

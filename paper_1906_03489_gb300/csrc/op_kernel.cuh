@@ -98,8 +98,9 @@ __device__ void issue_tile(const Prm& p, char* sm, uint64_t* bars, int slot, int
   uint32_t tx = 0;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) mbar_arrive_expect_tx(&bars[slot], tx);
-    for (int s = 0; s < ns; ++s) {
-      if (!sd[s].base) continue;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      if (s >= ns || !sd[s].base) continue;
       char* region = slotp + p.region_off[s];
       if (t.contig && sd[s].whole) {
         const int64_t e0 = elem_id(p, t, 0);
@@ -132,6 +133,7 @@ struct Ctx {
   const int64_t* gcoef;   // [kMaxEB] coefficient offsets of the tile's elements
   const int64_t* gquad;   // [kMaxEB] quadrature offsets
   int ne, tid, nthr;
+  int* tab_order;         // order whose tables are in work buffer 4 (shared)
   bool has_lam, has_kap;
   T lam;
   __device__ const T* staged(int s, int j) const { return reinterpret_cast<const T*>(sm) + soff[s * kMaxEB + j]; }
@@ -494,6 +496,225 @@ __device__ void body_helm(const T* tab, const Ctx<T>& c, T* out, Rel release) {
   }
 }
 
+// ---- Helmholtz, 3D: Q^2 threads per element, column and pencil roles -------
+// Thread (a, b) of element `el` (a, b in [0, Q)) plays three roles:
+//  * column owner of (i, j) = (a, b): the contractions along xi_3, the
+//    gradient along xi_3 and the pointwise geometric factors, in registers;
+//  * pencil owner along xi_1 at (j, k) = (a, b) and along xi_2 at
+//    (i, k) = (a, b) for the gradient and transposed gradient;
+//  * pencil owner of the BwdTrans / IProduct contractions along xi_1, xi_2.
+// Data moves between roles through shared memory with odd row strides S, so
+// that the scalar accesses of consecutive threads fall in distinct banks.
+// Matrices are indexed with compile-time indices only (constant bank).
+// Buffers per element (row stride S = Q | 1, plane stride Q*S):
+//   W0: X[r][q][i] (S1 -> S2), then Y3[r][i][j] (S7 -> S8)
+//   W1: Y[j][i][r] (rows of n, stride SN = n | 1; S2 -> S3), then Y2[r][q][i] (S8 -> S9)
+//   W2: U[k][j][i] (S3 -> S4)
+//   W3: d0 (S4 -> S5), g0 (S5 -> S6), D^T-contracted g0 (S6 -> S7), same layout
+//   W4: d1, g1, D^T-contracted g1
+template <typename T, int P, int Q>
+struct RoleShape {
+  static constexpr int n = P + 1;
+  static constexpr int S = Q | 1;
+  static constexpr int SN = n | 1;
+  static constexpr int PL = Q * S;                              // plane stride of Q x Q fields
+  static constexpr int WS0 = n * Q * S > n * n * S ? n * Q * S : n * n * S;
+  static constexpr int WS1 = Q * Q * SN > n * n * S ? Q * Q * SN : n * n * S;
+  static constexpr int WS = Q * PL > WS0 ? (Q * PL > WS1 ? Q * PL : WS1) : (WS0 > WS1 ? WS0 : WS1);
+};
+
+template <typename T, int P, int Q, class Rel>
+__device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel release) {
+  using S_ = RoleShape<T, P, Q>;
+  constexpr int n = S_::n, S = S_::S, SN = S_::SN, PL = S_::PL, WS = S_::WS;
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
+  const T* B = tab;                  // B[Q][n]
+  const T* D = tab + 2 * Q * n;      // D[Q][Q]
+  const int el = c.tid / Q2;
+  const int cc = c.tid - el * Q2;
+  const int a = cc % Q, b = cc / Q;
+  const bool act = el < c.ne;
+  T* W0 = c.work[0] + el * WS;
+  T* W1 = c.work[1] + el * WS;
+  T* W2 = c.work[2] + el * WS;
+  T* W3 = c.work[3] + el * WS;
+  T* W4 = c.work[4] + el * WS;
+  // S1: pencil along p at (q, r) = (a, b): X[r][q][i] = sum_p B[i][p] C[r][q][p]
+  if (act && a < n && b < n) {
+    const T* C = c.staged(0, el) + (b * n + a) * n;
+    T v[n];
+#pragma unroll
+    for (int p = 0; p < n; ++p) v[p] = C[p];
+    T* dst = W0 + (b * n + a) * S;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int p = 0; p < n; ++p) acc = fma(B[i * n + p], v[p], acc);
+      dst[i] = acc;
+    }
+  }
+  SPX_SYNC();
+  // S2: pencil along q at (i, r) = (a, b): Y[j][i][r] = sum_q B[j][q] X[r][q][i]
+  if (act && b < n) {
+    T v[n];
+#pragma unroll
+    for (int q = 0; q < n; ++q) v[q] = W0[(b * n + q) * S + a];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int q = 0; q < n; ++q) acc = fma(B[j * n + q], v[q], acc);
+      W1[(j * Q + a) * SN + b] = acc;
+    }
+  }
+  SPX_SYNC();
+  // S3: column (i, j) = (a, b): u = B y (xi_3), d2 = D u; U[k][j][i] = u
+  T u[Q], g2[Q];
+  if (act) {
+    T y[n];
+#pragma unroll
+    for (int r = 0; r < n; ++r) y[r] = W1[(b * Q + a) * SN + r];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int r = 0; r < n; ++r) acc = fma(B[k * n + r], y[r], acc);
+      u[k] = acc;
+      W2[k * PL + b * S + a] = acc;
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < Q; ++m) acc = fma(D[k * Q + m], u[m], acc);
+      g2[k] = acc;
+    }
+  }
+  SPX_SYNC();
+  // S4: gradient pencils: along xi_1 at (j, k) = (a, b) -> W3, along xi_2 at (i, k) = (a, b) -> W4
+  if (act) {
+    T v[Q];
+#pragma unroll
+    for (int m = 0; m < Q; ++m) v[m] = W2[b * PL + a * S + m];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < Q; ++m) acc = fma(D[i * Q + m], v[m], acc);
+      W3[b * PL + a * S + i] = acc;
+    }
+#pragma unroll
+    for (int m = 0; m < Q; ++m) v[m] = W2[b * PL + m * S + a];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < Q; ++m) acc = fma(D[j * Q + m], v[m], acc);
+      W4[b * PL + j * S + a] = acc;
+    }
+  }
+  SPX_SYNC();
+  // S5: column (i, j) = (a, b): pointwise; g0 -> W3, g1 -> W4, g2 and v in registers
+  T z[Q];
+  if (act) {
+    const T* G = c.staged(1, el) + b * Q + a;
+    const T* lf = c.has_lam ? c.staged(2, el) + b * Q + a : nullptr;
+    const T* kf = c.has_kap ? c.staged(3, el) + b * Q + a : nullptr;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int w = k * PL + b * S + a;
+      const T d0 = W3[w], d1 = W4[w], d2 = g2[k];
+      const T* g = G + k * Q2;
+      const T g00 = g[0], g01 = g[Q3], g02 = g[2 * Q3], g11 = g[3 * Q3], g12 = g[4 * Q3], g22 = g[5 * Q3];
+      const T jw = g[6 * Q3];
+      const T kk = kf ? kf[k * Q2] : T(1);
+      const T ll = lf ? lf[k * Q2] : c.lam;
+      W3[w] = kk * (g00 * d0 + g01 * d1 + g02 * d2);
+      W4[w] = kk * (g01 * d0 + g11 * d1 + g12 * d2);
+      g2[k] = kk * (g02 * d0 + g12 * d1 + g22 * d2);
+      u[k] = ll * jw * u[k];
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T acc = u[k];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) acc = fma(D[m * Q + k], g2[m], acc);
+      z[k] = acc;
+    }
+  }
+  SPX_SYNC();
+  release();
+  // S6: transposed-gradient pencils, in place: along xi_1 at (j, k) = (a, b) in W3,
+  // along xi_2 at (i, k) = (a, b) in W4
+  if (act) {
+    T v[Q];
+#pragma unroll
+    for (int m = 0; m < Q; ++m) v[m] = W3[b * PL + a * S + m];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < Q; ++m) acc = fma(D[m * Q + i], v[m], acc);
+      W3[b * PL + a * S + i] = acc;
+    }
+#pragma unroll
+    for (int m = 0; m < Q; ++m) v[m] = W4[b * PL + m * S + a];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < Q; ++m) acc = fma(D[m * Q + j], v[m], acc);
+      W4[b * PL + j * S + a] = acc;
+    }
+  }
+  SPX_SYNC();
+  // S7: column (i, j) = (a, b): z += both contributions; y3 = B^T z (xi_3) -> Y3[r][i][j]
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int w = k * PL + b * S + a;
+      z[k] += W3[w] + W4[w];
+    }
+#pragma unroll
+    for (int r = 0; r < n; ++r) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) acc = fma(B[k * n + r], z[k], acc);
+      W0[(r * Q + a) * S + b] = acc;
+    }
+  }
+  SPX_SYNC();
+  // S8: pencil along j at (i, r) = (a, b): Y2[r][q][i] = sum_j B[j][q] Y3[r][i][j]
+  if (act && b < n) {
+    T v[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) v[j] = W0[(b * Q + a) * S + j];
+#pragma unroll
+    for (int q = 0; q < n; ++q) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) acc = fma(B[j * n + q], v[j], acc);
+      W1[(b * n + q) * S + a] = acc;
+    }
+  }
+  SPX_SYNC();
+  // S9: pencil along i at (q, r) = (a, b): y[p][q][r] = sum_i B[i][p] Y2[r][q][i] -> HBM
+  if (act && a < n && b < n) {
+    T v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = W1[(b * n + a) * S + i];
+    T* dst = out + c.gcoef[el] + (b * n + a) * n;
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+      T acc = T(0);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) acc = fma(B[i * n + p], v[i], acc);
+      dst[p] = acc;
+    }
+  }
+}
+
 // ---- BwdTrans and reference gradient of one staged coefficient stream -----
 // U -> Wu, d_a -> Wd[a]; 3D uses scratch Wt.
 template <typename T, int DIM, int P, int Q>
@@ -683,6 +904,7 @@ __device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel)
   if constexpr (OP == OP_BWD) body_bwd<T, DIM, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_IPROD) body_iprod<T, DIM, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_DERIV) body_deriv<T, DIM, P, Q>(tab, c, p.out0, p.out1, p.out2, rel);
+  else if constexpr (OP == OP_HELM && DIM == 3) body_helm_role<T, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_HELM) body_helm<T, DIM, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_ADJ) body_adj<T, DIM, P, Q>(tab, c, p.out0, p.out1, rel);
   else body_diag<T, DIM, P, Q>(tab, c, p.out0, rel);
@@ -697,17 +919,19 @@ __device__ __forceinline__ void dispatch_order(int P, const Prm& p, const Ctx<T>
 }
 
 template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>
-__global__ void __launch_bounds__(1024) op_kernel(const __grid_constant__ KParams<T, PLO, PHI, QOFF> p) {
+__global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KParams<T, PLO, PHI, QOFF> p) {
   extern __shared__ __align__(128) char sm[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
   uint32_t* soff = reinterpret_cast<uint32_t*>(sm + p.meta_base);
   int64_t* gcoef = reinterpret_cast<int64_t*>(sm + p.meta_base + 5 * kMaxEB * 4);
   int64_t* gquad = gcoef + kMaxEB;
+  int* tab_order = reinterpret_cast<int*>(gquad + kMaxEB);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int S = p.stages;
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
+    *tab_order = -1;
   }
   __syncthreads();
   if (tid == 0) {
@@ -718,8 +942,9 @@ __global__ void __launch_bounds__(1024) op_kernel(const __grid_constant__ KParam
   }
   Ctx<T> c;
   c.sm = sm;
-  for (int w = 0; w < 8; ++w) c.work[w] = reinterpret_cast<T*>(sm + p.work_base + w * p.work_bytes);
+  for (int w = 0; w < 8; ++w) c.work[w] = reinterpret_cast<T*>(sm + p.work_base + size_t(w) * p.work_bytes);
   c.soff = soff;
+  c.tab_order = tab_order;
   c.gcoef = gcoef;
   c.gquad = gquad;
   c.tid = tid;
@@ -747,8 +972,9 @@ __global__ void __launch_bounds__(1024) op_kernel(const __grid_constant__ KParam
       const int64_t e = elem_id(p, t, j);
       gcoef[j] = coef_off_of<DIM>(p, e, P);
       gquad[j] = quad_off_of<DIM>(p, e, Q);
-      for (int s = 0; s < ns; ++s) {
-        if (!sd[s].base) continue;
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        if (s >= ns || !sd[s].base) continue;
         char* region = slotp + p.region_off[s];
         const int64_t off = sd[s].quad ? gquad[j] : gcoef[j];
         const T* g = sd[s].base + sd[s].mult * off + sd[s].boff;

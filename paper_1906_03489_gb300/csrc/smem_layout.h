@@ -12,7 +12,7 @@ inline int n_work_buffers(int op) {
     case OP_BWD: return 2;
     case OP_IPROD: return 2;
     case OP_DERIV: return 3;
-    case OP_HELM: return 4;
+    case OP_HELM: return 5;
     case OP_ADJ: return 8;
     default: return 5;
   }
@@ -58,7 +58,11 @@ inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const Launch
     for (int s = 0; s < 5; ++s)
       if (lens[s]) region[s] = std::max<uint64_t>(region[s], uint64_t(eb) * (((lens[s] * sz + 15) & ~int64_t(15)) + 16));
     const int S1 = Q | 1;
-    const uint64_t ws = plan->dim == 3 ? uint64_t(S1) * Q * Q : uint64_t(S1) * Q;
+    uint64_t ws = plan->dim == 3 ? uint64_t(S1) * Q * Q : uint64_t(S1) * Q;
+    if (op == OP_HELM && plan->dim == 3) {  // column / pencil role layout
+      const uint64_t n = P + 1, S = Q | 1, SN = n | 1;
+      ws = std::max<uint64_t>({ws, n * Q * S, n * n * S, uint64_t(Q) * Q * SN, uint64_t(Q) * Q * S});
+    }
     work = std::max<uint64_t>(work, uint64_t(eb) * ws * sz);
     if (op == OP_DIAG) work = std::max<uint64_t>(work, uint64_t(3) * Q * (P + 1) * sz);
   }
@@ -72,7 +76,7 @@ inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const Launch
   L.work_base = L.slot_base + cfg.stages * L.slot_bytes;
   L.work_bytes = up128(work);
   L.meta_base = L.work_base + n_work_buffers(op) * L.work_bytes;
-  L.total = L.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8;
+  L.total = L.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8 + 16;
   return L;
 }
 

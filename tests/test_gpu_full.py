@@ -1,0 +1,140 @@
+"""GPU parity at the full workload sizes, in the launch configuration the
+benchmark times (autotuned tiles).
+
+* 2D 16x16 affine quads, P=4, Q=6 (FP64): BwdTrans, IProduct, Helmholtz - full oracle.
+* 32^3 curved hexes, P=4, Q=6: Helmholtz and PhysDeriv, FP64 and FP32 - full oracle.
+* 24^3 curved hexes, P_e in {2..8}, Q_e = P_e + 2: one variable-order launch,
+  FP64 and FP32 - full oracle.
+* 48^3 curved hexes, P=4: Helmholtz on sampled elements (dense oracle H_e),
+  and the periodic solve to 1e-10 in both precisions, checked through sampled
+  rows of the assembled residual (oracle H_e) and the error against u*.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1906_03489_gb300 as spx
+from oracle import geometry, operators
+from paper_1906_03489_gb300 import mesh, synth
+
+from _cases import Case, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def workload_case(name, dtype_tune=None, op="helmholtz"):
+    w = synth.WORKLOADS[name]
+    if isinstance(w["P"], tuple):
+        orders = synth.orders(synth.rng(w["seed"]), w["N"] ** w["dim"], *w["P"])
+        c = Case(w["dim"], w["N"], orders=orders, amp=w["amp"])
+    else:
+        c = Case(w["dim"], w["N"], P=w["P"], amp=w["amp"])
+    return w, c
+
+
+def test_quad2d_workload():
+    w, c = workload_case("quad2d_16x16_p4")
+    gen = synth.rng(w["seed"])
+    u = synth.uniform(gen, c.plan.n_coef)
+    ut = torch.tensor(u, device="cuda")
+    phys = operators.bwd_trans(c.om, u)
+    assert rel_err(spx.bwd_trans(c.plan, ut), phys) <= 1e-12
+    assert rel_err(spx.iproduct(c.plan, torch.tensor(phys, device="cuda")), operators.iproduct(c.om, phys)) <= 1e-12
+    assert rel_err(spx.helmholtz(c.plan, ut, lam=1.0), operators.helmholtz(c.om, u)) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_hex32_workload(dtype):
+    w, c = workload_case("hex3d_32_p4")
+    gen = synth.rng(w["seed"])
+    u = synth.uniform(gen, c.plan.n_coef)
+    ut = torch.tensor(u, device="cuda", dtype=dtype)
+    out = torch.empty_like(ut)
+    c.plan.autotune("helmholtz", dtype, ut, out, reps=3)
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    assert rel_err(spx.helmholtz(c.plan, ut, lam=1.0), operators.helmholtz(c.om, u)) <= tol
+    phys = operators.bwd_trans(c.om, u)
+    pt = torch.tensor(phys, device="cuda", dtype=dtype)
+    refs = operators.phys_deriv(c.om, phys)
+    scale = max(np.abs(r).max() for r in refs)
+    for o, r in zip(spx.phys_deriv(c.plan, pt), refs):
+        assert np.abs(o.cpu().double().numpy() - r).max() / scale <= tol
+    assert c.plan.device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_varp24_workload(dtype):
+    w, c = workload_case("hex3d_24_varp")
+    gen = synth.rng(w["seed"])
+    synth.orders(gen, c.plan.E, *w["P"])          # orders are drawn first
+    u = synth.uniform(gen, c.plan.n_coef)
+    ut = torch.tensor(u, device="cuda", dtype=dtype)
+    out = torch.empty_like(ut)
+    c.plan.autotune("helmholtz", dtype, ut, out, reps=2)
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    assert rel_err(spx.helmholtz(c.plan, ut, lam=1.0), operators.helmholtz(c.om, u)) <= tol
+
+
+@pytest.fixture(scope="module")
+def hex48():
+    w = synth.WORKLOADS["hex3d_48_p4"]
+    plan = spx.Plan(3, w["N"] ** 3, order=w["P"])
+    g = spx.geom_factors(plan, mesh.structured_nodes(3, w["N"], w["P"], w["amp"]))
+    plan.set_geometry(torch.float64, g["geom"], g["dxi"])
+    plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])
+    om = geometry.StructuredMesh(3, w["N"], w["P"], amp=w["amp"])
+    return w, plan, g, om
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_hex48_helmholtz_sampled(hex48, dtype):
+    w, plan, g, om = hex48
+    u = synth.uniform(synth.rng(w["seed"]), plan.n_coef)
+    y = spx.helmholtz(plan, torch.tensor(u, device="cuda", dtype=dtype)).cpu().double().numpy()
+    ids = np.sort(np.random.default_rng(0).choice(plan.E, 48, replace=False))
+    ids = np.concatenate([[0, plan.E - 1], ids])
+    geo = om.geometry(4, 6, ids)
+    n = 125
+    ref = np.concatenate([operators.helmholtz_matrix(3, 4, 6, geo, t) @ u[e * n:(e + 1) * n]
+                          for t, e in enumerate(ids)])
+    got = np.concatenate([y[e * n:(e + 1) * n] for e in ids])
+    assert rel_err(got, ref) <= (1e-12 if dtype == torch.float64 else 1e-5)
+
+
+def test_hex48_solve(hex48):
+    w, plan, g, om = hex48
+    l2g, ng = mesh.periodic_l2g(3, w["N"], w["P"])
+    Q = 6
+    X = g["xq"].reshape(plan.E, 3, Q ** 3)
+    u_star = torch.prod(torch.sin(2 * np.pi * X), dim=1).reshape(-1).contiguous()
+    f = spx.assemble(plan, l2g, spx.iproduct(plan, (1.0 + 12 * np.pi ** 2) * u_star), ng)
+    x32, i32 = spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision="f32_refine")
+    x64, i64 = spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision="f64")
+    assert i32["status"] == 0 and i32["rel_residual"] <= 1e-10
+    assert i64["status"] == 0 and i64["rel_residual"] <= 1e-10
+    assert rel_err(x32, x64.cpu().numpy()) <= 1e-8
+    # independent FP64 residual on the GPU
+    r = f - spx.assemble(plan, l2g, spx.helmholtz(plan, spx.gather(plan, l2g, x32)), ng)
+    assert (r.norm() / f.norm()).item() <= 1e-10
+    # sampled rows of the residual with the oracle's dense elemental matrices
+    l2g_np = l2g.cpu().numpy()
+    x_np, f_np = x32.cpu().numpy(), f.cpu().numpy()
+    fn = np.linalg.norm(f_np)
+    for gidx in np.random.default_rng(1).choice(ng, 6, replace=False):
+        locs = np.nonzero(l2g_np == gidx)[0]
+        elems = np.unique(locs // 125)
+        geo = om.geometry(4, 6, elems)
+        row = 0.0
+        for t, e in enumerate(elems):
+            H = operators.helmholtz_matrix(3, 4, 6, geo, t)
+            ye = H @ x_np[l2g_np[e * 125:(e + 1) * 125]]
+            row += sum(ye[l - e * 125] for l in locs if e * 125 <= l < (e + 1) * 125)
+        assert abs(f_np[gidx] - row) <= 1e-10 * fn
+    u = spx.bwd_trans(plan, spx.gather(plan, l2g, x32))
+    assert (u - u_star).abs().max().item() < 1e-5

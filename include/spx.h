@@ -270,6 +270,39 @@ spx_status spx_cg_solve(const spx_plan *plan, double lambda, const int32_t *l2g,
                         double *x, void *workspace, size_t workspace_bytes, const spx_cg_opts *opts,
                         spx_cg_result *result, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free solve.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory during a solve:
+ * for example a program whose device memory is entirely owned by another
+ * pool allocator, a latency-critical loop that cannot afford the implicit
+ * device synchronisation of cudaMalloc/cudaFree, or an embedding that may
+ * only use memory reserved when the library is loaded.
+ *
+ * Same arguments and results as spx_cg_solve, minus the workspace: the
+ * solver's scratch lives in a fixed array of SPX_CG_NOALLOC_BYTES inside
+ * this library's own device memory.  That array exists on every GPU that
+ * loads the library, from load until the process exits.
+ *   - Limit: problems whose spx_cg_workspace_bytes exceeds
+ *     SPX_CG_NOALLOC_BYTES are rejected with SPX_ERR_NO_MEMORY before any
+ *     work is enqueued.
+ *   - Nothing is allocated or created by the call: no cudaMalloc/cudaFree,
+ *     no stream, event or graph; all work runs on `stream` (use_graph is
+ *     ignored) and the call synchronises that stream.
+ *   - The plan's launch tiles must already exist: run spx_cg_solve once, or
+ *     spx_helmholtz in each precision used and spx_helmholtz_diag in FP64,
+ *     on the plan first; otherwise SPX_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device); make that first call before any stream capture.
+ *   - Every call on a device shares the one array and it keeps the previous
+ *     call's contents (the solver re-initialises what it needs); calls that
+ *     overlap on the GPU (other threads or streams) race on it and must be
+ *     serialised by the caller.
+ * ------------------------------------------------------------------------- */
+#define SPX_CG_NOALLOC_BYTES (32u * 1024u * 1024u)
+spx_status spx_cg_solve_noalloc(const spx_plan *plan, double lambda, const int32_t *l2g, int64_t n_global,
+                                const double *f, double *x, const spx_cg_opts *opts, spx_cg_result *result,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

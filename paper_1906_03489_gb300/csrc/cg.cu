@@ -18,6 +18,8 @@
 //    refinement (outer residual, its norm and x += d in FP64).
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "spx_internal.h"
@@ -533,9 +535,17 @@ extern "C" spx_status spx_cg_workspace_bytes(const spx_plan* plan, int64_t n_glo
   return SPX_OK;
 }
 
-extern "C" spx_status spx_cg_solve(const spx_plan* plan, double lambda, const int32_t* l2g, int64_t n_global,
-                                   const double* f, double* x, void* workspace, size_t ws_bytes,
-                                   const spx_cg_opts* o, spx_cg_result* res, void* stream) {
+namespace spx {
+namespace {
+
+// The solve.  own_resources = true (spx_cg_solve): the call may build the
+// plan's tile lists, runs on a private stream ordered after the caller's and
+// may capture its iterations in CUDA graphs.  own_resources = false
+// (spx_cg_solve_noalloc): nothing is created or allocated; the work runs
+// eagerly on the caller's stream and the tile lists must already exist.
+spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g, int64_t n_global, const double* f,
+                         double* x, void* workspace, size_t ws_bytes, const spx_cg_opts* o, spx_cg_result* res,
+                         void* stream, bool own_resources) {
   if (!plan || !o || !res) return fail(SPX_ERR_INVALID_ARG, "cg_solve: NULL argument");
   std::memset(res, 0, sizeof(*res));
   if (n_global < 0 || n_global > (int64_t(1) << 31) - 2 || plan->n_coef > (int64_t(1) << 31) - 1)
@@ -562,23 +572,41 @@ extern "C" spx_status spx_cg_solve(const spx_plan* plan, double lambda, const in
   if (ws_bytes < s.w.bytes) return fail(SPX_ERR_NO_MEMORY, "cg_solve: workspace smaller than cg_workspace_bytes");
   spx_plan* mp = const_cast<spx_plan*>(plan);
   spx_status st;
-  if ((st = ensure_tiles(mp, OP_HELM, 0)) != SPX_OK) return st;
-  if ((st = ensure_tiles(mp, OP_HELM, 1)) != SPX_OK) return st;
-  // private stream ordered after the caller's
   cudaStream_t user = static_cast<cudaStream_t>(stream);
-  SPX_CK(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
-  cudaEvent_t ev;
-  SPX_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaEvent_t ev = nullptr;
+  bool use_graph = o->use_graph != 0;
+  if (own_resources) {
+    if ((st = ensure_tiles(mp, OP_HELM, 0)) != SPX_OK) return st;
+    if ((st = ensure_tiles(mp, OP_HELM, 1)) != SPX_OK) return st;
+    // private stream ordered after the caller's
+    SPX_CK(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
+    SPX_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  } else {
+    if (plan->tiles[OP_HELM][SPX_F64].dirty || plan->tiles[OP_DIAG][SPX_F64].dirty ||
+        (o->precision == 1 && plan->tiles[OP_HELM][SPX_F32].dirty))
+      return fail(SPX_ERR_INVALID_ARG,
+                  "cg_solve_noalloc: the plan's Helmholtz / diagonal launch tiles are not built yet (run "
+                  "spx_helmholtz in each precision used and spx_helmholtz_diag in FP64 once on this plan, or "
+                  "spx_cg_solve once, before the first allocation-free solve)");
+    s.st = user;
+    use_graph = false;
+  }
   auto finish = [&](spx_status r) {
-    cudaEventRecord(ev, s.st);
-    cudaStreamWaitEvent(user, ev, 0);
-    cudaStreamSynchronize(s.st);
-    cudaEventDestroy(ev);
-    cudaStreamDestroy(s.st);
+    if (own_resources) {
+      cudaEventRecord(ev, s.st);
+      cudaStreamWaitEvent(user, ev, 0);
+      cudaStreamSynchronize(s.st);
+      cudaEventDestroy(ev);
+      cudaStreamDestroy(s.st);
+    } else {
+      cudaStreamSynchronize(s.st);
+    }
     return r;
   };
-  cudaEventRecord(ev, user);
-  cudaStreamWaitEvent(s.st, ev, 0);
+  if (own_resources) {
+    cudaEventRecord(ev, user);
+    cudaStreamWaitEvent(s.st, ev, 0);
+  }
   Workspace& w = s.w;
   SPX_CK(cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s.st));
   if ((st = build_csr(s)) != SPX_OK) return finish(st);
@@ -605,7 +633,7 @@ extern "C" spx_status spx_cg_solve(const spx_plan* plan, double lambda, const in
       if ((st = set_scalars(s, ff, tol, o->maxit - total_it)) != SPX_OK) return finish(st);
       int it = 0;
       bool conv, nonfin;
-      st = pcg<double>(s, SPX_F64, x, w.r64, w.z64, w.p64, w.q64, w.minv64, w.pl64, w.ql64, o->use_graph != 0,
+      st = pcg<double>(s, SPX_F64, x, w.r64, w.z64, w.p64, w.q64, w.minv64, w.pl64, w.ql64, use_graph,
                        o->check_every, &it, &conv, &nonfin);
       if (st != SPX_OK) return finish(st);
       total_it += it;
@@ -626,7 +654,7 @@ extern "C" spx_status spx_cg_solve(const spx_plan* plan, double lambda, const in
       if ((st = set_scalars(s, 1.0, o->inner_tol, o->maxit)) != SPX_OK) return finish(st);
       int it = 0;
       bool conv, nonfin;
-      st = pcg<float>(s, SPX_F32, w.d32, w.r32, w.z32, w.p32, w.q32, w.minv32, w.pl32, w.ql32, o->use_graph != 0,
+      st = pcg<float>(s, SPX_F32, w.d32, w.r32, w.z32, w.p32, w.q32, w.minv32, w.pl32, w.ql32, use_graph,
                       o->check_every, &it, &conv, &nonfin);
       if (st != SPX_OK) return finish(st);
       total_it += it;
@@ -642,4 +670,59 @@ extern "C" spx_status spx_cg_solve(const spx_plan* plan, double lambda, const in
   if (res->rel_residual > tol)
     return finish(fail(SPX_ERR_NOT_CONVERGED, "cg_solve: tolerance not reached within the iteration caps"));
   return finish(SPX_OK);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve: the workspace is a fixed array in the module's own
+// device memory.  It exists on every device that loads this library, from
+// module load until process exit, and is shared by every call on that device.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_ws[SPX_CG_NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_ws for the current device, looked up once per
+// device (the host-side symbol is only a handle, never a device pointer).
+spx_status noalloc_workspace(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(SPX_ERR_UNSUPPORTED, "cg_solve_noalloc: device ordinal too large");
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc workspace)");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return SPX_OK;
+}
+
+}  // namespace
+}  // namespace spx
+
+extern "C" spx_status spx_cg_solve(const spx_plan* plan, double lambda, const int32_t* l2g, int64_t n_global,
+                                   const double* f, double* x, void* workspace, size_t ws_bytes,
+                                   const spx_cg_opts* o, spx_cg_result* res, void* stream) {
+  return cg_solve_impl(plan, lambda, l2g, n_global, f, x, workspace, ws_bytes, o, res, stream, true);
+}
+
+extern "C" spx_status spx_cg_solve_noalloc(const spx_plan* plan, double lambda, const int32_t* l2g,
+                                           int64_t n_global, const double* f, double* x, const spx_cg_opts* o,
+                                           spx_cg_result* res, void* stream) {
+  if (!plan || !o || !res) return fail(SPX_ERR_INVALID_ARG, "cg_solve_noalloc: NULL argument");
+  size_t need = 0;
+  spx_status st = spx_cg_workspace_bytes(plan, n_global, o, &need);
+  if (st != SPX_OK) return st;
+  if (need > SPX_CG_NOALLOC_BYTES)
+    return fail(SPX_ERR_NO_MEMORY, "cg_solve_noalloc: this problem needs " + std::to_string(need) +
+                                       " bytes of solver workspace; the built-in workspace holds " +
+                                       std::to_string(size_t(SPX_CG_NOALLOC_BYTES)) +
+                                       " (use spx_cg_solve with a caller workspace)");
+  void* ws = nullptr;
+  if ((st = noalloc_workspace(&ws)) != SPX_OK) return st;
+  return cg_solve_impl(plan, lambda, l2g, n_global, f, x, ws, SPX_CG_NOALLOC_BYTES, o, res, stream, false);
 }

@@ -138,8 +138,13 @@ spx_status spx_plan_set_geometry(spx_plan *plan, spx_dtype dtype, const void *ge
 
 /* Overrides the launch tile of one operator/precision/order: elements per
  * batch `eb` (1..64), threads per block `nthreads` (32..512, multiple of
- * 32; the 3D Helmholtz operator uses eb * Q^2 threads instead) and pipeline
- * depth `stages` (1..4).  order = -1 sets every order. */
+ * 32) and pipeline depth `stages` (1..4).  order = -1 sets every order.
+ * Two operators derive their block size from eb instead:
+ *  - FP64 3D Helmholtz: eb * Q^2 threads;
+ *  - FP32 3D Helmholtz (element-pair kernel): ceil(eb / 2) * Q^2 threads;
+ *    there `nthreads` (32..1024) is the number of threads per SM that the
+ *    register budget must allow (<= 512: 128 registers per thread, <= 640:
+ *    96, else 80) and `stages` (0..4) the L2 prefetch distance in tiles. */
 spx_status spx_plan_set_tile(spx_plan *plan, spx_op op, spx_dtype dtype, int order, int eb, int nthreads,
                              int stages);
 

@@ -29,6 +29,10 @@ static int default_eb(int dim, int Q) {
 }
 
 size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& cfg) {
+  if (uses_pair_kernel(plan, op, dtype)) {
+    const PairShape s = pair_shape(plan, cfg);
+    return s.nthreads > 512 ? SIZE_MAX : s.smem;
+  }
   // worst case: coefficient fields present
   return smem_layout(plan, op, dtype == 0 ? 8 : 4, cfg, true, true).total;
 }
@@ -257,8 +261,11 @@ spx_status spx_plan_set_tile(spx_plan* p, spx_op op, spx_dtype dt, int order, in
   if (!p) return fail(SPX_ERR_INVALID_ARG, "set_tile: NULL plan");
   if (op < 0 || op >= OP_KINDS || (dt != SPX_F64 && dt != SPX_F32))
     return fail(SPX_ERR_INVALID_ARG, "set_tile: bad operator or dtype");
-  if (eb < 1 || eb > kMaxEB || nthreads < 32 || nthreads > 512 || nthreads % 32 || stages < 1 || stages > 4)
-    return fail(SPX_ERR_INVALID_ARG, "set_tile: eb 1..64, nthreads 32..512 (multiple of 32), stages 1..4");
+  const int max_nt = uses_pair_kernel(p, op, dt) ? 1024 : 512;
+  const int min_st = uses_pair_kernel(p, op, dt) ? 0 : 1;
+  if (eb < 1 || eb > kMaxEB || nthreads < 32 || nthreads > max_nt || nthreads % 32 || stages < min_st || stages > 4)
+    return fail(SPX_ERR_INVALID_ARG, "set_tile: eb 1..64, nthreads 32..512 (1024 for the FP32 3D Helmholtz), "
+                                     "multiple of 32, stages 1..4 (0..4 for the FP32 3D Helmholtz)");
   if (order != -1 && (order < 1 || order > kMaxP)) return fail(SPX_ERR_INVALID_ARG, "set_tile: order outside 1..8");
   LaunchCfg c = p->cfg[op][dt];
   c.nthreads = nthreads;
@@ -382,8 +389,11 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
   if (p->E == 0) return SPX_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ebs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
-  const int nts[] = {64, 128, 192, 256, 384, 512};
-  const int sts[] = {2, 3};
+  const bool pair = uses_pair_kernel(p, op, dt);
+  // the pair kernel derives its CTA size from eb: there `nthreads` picks the
+  // register budget (threads per SM) and `stages` the L2 prefetch distance
+  const std::vector<int> nts = pair ? std::vector<int>{512, 640, 768} : std::vector<int>{64, 128, 192, 256, 384, 512};
+  const std::vector<int> sts = pair ? std::vector<int>{0, 1, 2} : std::vector<int>{2, 3};
   LaunchCfg best = p->cfg[op][dt];
   // orders one at a time (other orders keep their current tile); the same
   // thread count and depth serve the whole launch, so they are tuned last.

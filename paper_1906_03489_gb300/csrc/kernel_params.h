@@ -25,6 +25,59 @@ __host__ __device__ constexpr int tab_len(int P, int QOFF) {
   return 2 * (P + QOFF) * (P + 1) + (P + QOFF) * (P + QOFF);
 }
 
+// Shared-memory layout of the FP32 3D Helmholtz element-pair kernel, in
+// float2 units.  Thread cc = a + Q b of an element pair takes roles (a, b);
+// every array is laid out so that the role coordinate a thread varies with
+// `a` has stride 1 and the one it varies with `b` stride Q (mod 16), and the
+// pair stride is Q^2 (mod 16): a 16-lane half-warp then touches 16 distinct
+// 8-byte bank pairs in every phase (no bank conflicts).
+//   X (q, r, i)  = q + Q r + XS i     Y, Y3 (i, r, j) = i + Q r + YS j
+//   U, G0 (i, j, k) = i + Q j + US k  U', G1 (i, j, k) = i + Q j + GS k
+//   Y2 (i, q, r) = i + Q r + ZS q
+__host__ __device__ constexpr int up16(int x, int r) { return x + (((r % 16) - (x % 16)) % 16 + 16) % 16; }
+
+template <int P, int Q>
+struct PairLayout {
+  static constexpr int n = P + 1;
+  static constexpr int XS = up16((n - 1) + Q * (n - 1) + 1, 1);
+  static constexpr int YS = up16(Q * n, Q);
+  static constexpr int US = up16(Q * Q, 1);
+  static constexpr int GS = up16(Q * Q, Q);
+  static constexpr int ZS = up16(Q * n, 1);
+  static constexpr int mx(int a, int b) { return a > b ? a : b; }
+  // pair strides of the three buffers: A holds X then U / g0, C holds Y then
+  // Y3, F holds U' / g1 then Y2
+  static constexpr int WA = up16(mx((n - 1) + Q * (n - 1) + XS * (Q - 1) + 1, Q * Q + US * (Q - 1)), Q * Q);
+  static constexpr int WC = up16((Q - 1) + Q * (n - 1) + YS * (Q - 1) + 1, Q * Q);
+  static constexpr int WF = up16(mx(Q * Q + GS * (Q - 1), (Q - 1) + Q * (n - 1) + ZS * (n - 1) + 1), Q * Q);
+};
+
+// Pair strides (float2) of order P at runtime (host side): {WA, WC, WF}.
+inline void pair_ws_of(int P, int QOFF, int w[3]) {
+  w[0] = w[1] = w[2] = 0;
+  switch (P * 4 + QOFF) {
+#define SPX_PWS(p)                                                                                  \
+  case p * 4 + 1: w[0] = PairLayout<p, p + 1>::WA; w[1] = PairLayout<p, p + 1>::WC; w[2] = PairLayout<p, p + 1>::WF; break; \
+  case p * 4 + 2: w[0] = PairLayout<p, p + 2>::WA; w[1] = PairLayout<p, p + 2>::WC; w[2] = PairLayout<p, p + 2>::WF; break;
+    SPX_PWS(1) SPX_PWS(2) SPX_PWS(3) SPX_PWS(4) SPX_PWS(5) SPX_PWS(6) SPX_PWS(7) SPX_PWS(8)
+#undef SPX_PWS
+    default: break;
+  }
+}
+
+// Bytes of one element's FP32 3D geometry block, and the stride of the
+// per-element regions of the Helmholtz pair kernel's geometry slot: at least
+// the block rounded to 16 bytes plus 16 bytes of alignment slack, and for
+// even Q congruent to 4 Q^2 modulo 128 bytes, so that element j starts Q^2 j
+// words (mod 32) into the banks: the column reads of element pairs
+// (j, j + npair) then follow the thread index (no bank conflicts).
+__host__ __device__ constexpr uint32_t geo_eblk(int Q) { return 7u * Q * Q * Q * 4u; }
+__host__ __device__ constexpr uint32_t geo_erb(int Q) {
+  return (Q % 2) ? ((geo_eblk(Q) + 15u) & ~15u) + 16u
+                 : (((geo_eblk(Q) + 15u) & ~15u) + 16u) +
+                       (((4u * Q * Q) % 128u + 128u - ((((geo_eblk(Q) + 15u) & ~15u) + 16u) % 128u)) % 128u);
+}
+
 template <int PLO, int PHI, int QOFF>
 struct TabLayout {
   __host__ __device__ static constexpr int off(int P) {

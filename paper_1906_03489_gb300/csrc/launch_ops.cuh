@@ -3,11 +3,84 @@
 #include <algorithm>
 #include <mutex>
 
+#include <type_traits>
+
+#include "helm_pair.cuh"
 #include "op_kernel.cuh"
 #include "smem_layout.h"
 #include "spx_internal.h"
 
 namespace spx {
+
+template <int PLO, int PHI, int QOFF, int REG>
+spx_status launch_pair_reg(const PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, const spx_plan* plan, int n_tiles,
+                           cudaStream_t stream) {
+  auto kern = helm_pair_kernel<PLO, PHI, QOFF, REG>;
+  static std::mutex mu;
+  static bool configured = false;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(plan->max_smem));
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      configured = true;
+    }
+  }
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, s.nthreads, s.smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile does not fit on an SM");
+  const int grid = std::min<int64_t>(n_tiles, int64_t(nb) * plan->num_sms);
+  kern<<<grid, s.nthreads, s.smem, stream>>>(pp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "Helmholtz pair kernel launch");
+  return SPX_OK;
+}
+
+// FP32 Helmholtz on hexahedra: the element-pair kernel (helm_pair.cuh).
+// `stages` of the launch configuration is its L2 prefetch distance in tiles.
+template <int PLO, int PHI, int QOFF>
+spx_status launch_pair(const LaunchReq& r) {
+  const spx_plan* plan = r.plan;
+  const LaunchCfg& cfg = plan->cfg[OP_HELM][1];
+  const TileList& tl = plan->tiles[OP_HELM][1];
+  if (tl.n == 0) return SPX_OK;
+  PairParams<PLO, PHI, QOFF> pp{};
+  auto& p = pp.k;
+  for (int P = PLO; P <= PHI; ++P) {
+    if (!plan->present[P]) continue;
+    const std::vector<double>& t = plan->tab[P];
+    const int off = TabLayout<PLO, PHI, QOFF>::off(P);
+    for (int i = 0; i < tab_len(P, QOFF); ++i) p.tab[off + i] = static_cast<float>(t[i]);
+  }
+  p.tiles = tl.d;
+  p.ids = plan->uniform ? nullptr : plan->d_ids;
+  p.coef_off = plan->uniform ? nullptr : plan->d_coef_off;
+  p.quad_off = plan->uniform ? nullptr : plan->d_quad_off;
+  p.in0 = static_cast<const float*>(r.in0);
+  p.geom = static_cast<const float*>(r.geom);
+  p.lam_f = static_cast<const float*>(r.lam_f);
+  p.kap_f = static_cast<const float*>(r.kap_f);
+  p.out0 = static_cast<float*>(r.out0);
+  p.status = plan->d_status;
+  p.lam = r.lam;
+  p.n_tiles = tl.n;
+  const PairShape s = pair_shape(plan, cfg);
+  if (s.nthreads > 512) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile needs more than 512 threads");
+  if (s.smem > plan->max_smem) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile does not fit in shared memory");
+  pp.pf = cfg.stages;
+  pp.off_a = s.off_a;
+  pp.off_c = s.off_c;
+  pp.off_f = s.off_f;
+  pp.off_geo = s.off_geo;
+  // `nthreads` of the configuration is the number of threads per SM the
+  // register budget must allow: 128 registers up to 512, 96 up to 640, else 80.
+  const int budget = cfg.nthreads;
+  if (budget <= 512) return launch_pair_reg<PLO, PHI, QOFF, 128>(pp, s, plan, tl.n, r.stream);
+  if (budget <= 640) return launch_pair_reg<PLO, PHI, QOFF, 96>(pp, s, plan, tl.n, r.stream);
+  return launch_pair_reg<PLO, PHI, QOFF, 80>(pp, s, plan, tl.n, r.stream);
+}
 
 template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>
 spx_status launch_impl(const LaunchReq& r) {
@@ -81,17 +154,24 @@ spx_status launch_impl(const LaunchReq& r) {
   return SPX_OK;
 }
 
+// Kernel of one (precision, dimension, operator) over orders PLO..PHI.
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>
+spx_status launch_any(const LaunchReq& r) {
+  if constexpr (std::is_same_v<T, float> && DIM == 3 && OP == OP_HELM) return launch_pair<PLO, PHI, QOFF>(r);
+  else return launch_impl<T, DIM, OP, PLO, PHI, QOFF>(r);
+}
+
 template <typename T, int DIM, int OP, int QOFF>
 spx_status launch_uniform(const LaunchReq& r) {
   switch (r.plan->uP) {
-    case 1: return launch_impl<T, DIM, OP, 1, 1, QOFF>(r);
-    case 2: return launch_impl<T, DIM, OP, 2, 2, QOFF>(r);
-    case 3: return launch_impl<T, DIM, OP, 3, 3, QOFF>(r);
-    case 4: return launch_impl<T, DIM, OP, 4, 4, QOFF>(r);
-    case 5: return launch_impl<T, DIM, OP, 5, 5, QOFF>(r);
-    case 6: return launch_impl<T, DIM, OP, 6, 6, QOFF>(r);
-    case 7: return launch_impl<T, DIM, OP, 7, 7, QOFF>(r);
-    case 8: return launch_impl<T, DIM, OP, 8, 8, QOFF>(r);
+    case 1: return launch_any<T, DIM, OP, 1, 1, QOFF>(r);
+    case 2: return launch_any<T, DIM, OP, 2, 2, QOFF>(r);
+    case 3: return launch_any<T, DIM, OP, 3, 3, QOFF>(r);
+    case 4: return launch_any<T, DIM, OP, 4, 4, QOFF>(r);
+    case 5: return launch_any<T, DIM, OP, 5, 5, QOFF>(r);
+    case 6: return launch_any<T, DIM, OP, 6, 6, QOFF>(r);
+    case 7: return launch_any<T, DIM, OP, 7, 7, QOFF>(r);
+    case 8: return launch_any<T, DIM, OP, 8, 8, QOFF>(r);
     default: return fail(SPX_ERR_UNSUPPORTED, "order out of range");
   }
 }
@@ -101,7 +181,7 @@ spx_status launch_typed(const LaunchReq& r) {
   if (r.plan->uniform) {
     return r.plan->qoff == 1 ? launch_uniform<T, DIM, OP, 1>(r) : launch_uniform<T, DIM, OP, 2>(r);
   }
-  return r.plan->qoff == 1 ? launch_impl<T, DIM, OP, 1, kMaxP, 1>(r) : launch_impl<T, DIM, OP, 1, kMaxP, 2>(r);
+  return r.plan->qoff == 1 ? launch_any<T, DIM, OP, 1, kMaxP, 1>(r) : launch_any<T, DIM, OP, 1, kMaxP, 2>(r);
 }
 
 }  // namespace spx

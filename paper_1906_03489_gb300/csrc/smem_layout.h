@@ -80,4 +80,45 @@ inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const Launch
   return L;
 }
 
+// Launch shape of the FP32 3D Helmholtz pair kernel (helm_pair.cuh): a tile
+// of eb elements is ceil(eb / 2) element pairs of Q^2 threads each.  Shared
+// memory: an mbarrier, the three work buffers A, C, F (PairLayout strides
+// per pair) and one geometry slot holding the tile's [eb][7][Q^3] factors
+// (16-byte aligned region per element, or one region for a contiguous tile).
+struct PairShape {
+  int nthreads;
+  uint32_t off_a, off_c, off_f;  // byte offsets of the work buffers
+  uint32_t off_geo;              // byte offset of the geometry slot
+  uint32_t smem;
+};
+
+inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg) {
+  PairShape s{};
+  uint64_t wa = 0, wc = 0, wf = 0, geo = 0;
+  for (int P = 1; P <= kMaxP; ++P) {
+    if (!plan->present[P]) continue;
+    const int Q = P + plan->qoff;
+    const int eb = cfg.order[P].eb;
+    const int pairs = (eb + 1) / 2;
+    int w[3];
+    pair_ws_of(P, plan->qoff, w);
+    s.nthreads = std::max(s.nthreads, pairs * Q * Q);
+    wa = std::max<uint64_t>(wa, uint64_t(pairs) * w[0] * 8);
+    wc = std::max<uint64_t>(wc, uint64_t(pairs) * w[1] * 8);
+    wf = std::max<uint64_t>(wf, uint64_t(pairs) * w[2] * 8);
+    geo = std::max<uint64_t>(geo, uint64_t(eb) * geo_erb(Q));   // per element regions
+  }
+  s.nthreads = (s.nthreads + 31) / 32 * 32;
+  s.off_a = 128;
+  s.off_c = s.off_a + up128(wa);
+  s.off_f = s.off_c + up128(wc);
+  s.off_geo = s.off_f + up128(wf);
+  s.smem = s.off_geo + up128(geo);
+  return s;
+}
+
+inline bool uses_pair_kernel(const spx_plan* plan, int op, int dtype) {
+  return op == OP_HELM && dtype == 1 && plan->dim == 3;
+}
+
 }  // namespace spx

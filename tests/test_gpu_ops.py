@@ -182,13 +182,52 @@ def test_tile_shapes_do_not_change_results(eb, nthreads, stages):
     assert rel_err(spx.bwd_trans(c.plan, ut), operators.bwd_trans(c.om, u)) <= 1e-12
 
 
+@pytest.mark.parametrize("eb,budget,pf", [(1, 512, 1), (2, 640, 2), (3, 768, 3), (8, 512, 0), (13, 640, 2),
+                                           (24, 768, 1), (20, 1024, 4)])
+def test_pair_kernel_tiles_do_not_change_results(eb, budget, pf):
+    """FP32 3D Helmholtz (two elements per thread): odd and even tile sizes, a
+    ragged last tile (5^3 elements), every register budget and prefetch depth."""
+    c = _case(3, 5, 4, 0.05)
+    u, ut = c.coef(18, torch.float32)
+    ref = operators.helmholtz(c.om, u)
+    c.plan.set_tile("helmholtz", torch.float32, eb, budget, pf)
+    assert c.plan.get_tile("helmholtz", torch.float32, 4) == (eb, budget, pf)
+    assert rel_err(spx.helmholtz(c.plan, ut), ref) <= 1e-5
+
+
+def test_pair_kernel_tile_too_large_is_refused():
+    c = _case(3, 2, 4, 0.05)
+    with pytest.raises(spx.SpxError) as e:
+        c.plan.set_tile("helmholtz", torch.float32, 28, 512, 0)   # 28 staged geometry blocks: > 227 KB
+    assert e.value.status == 2
+
+
+def test_pair_kernel_unaligned_and_fields():
+    """FP32 3D Helmholtz on 4-byte-offset views, with lambda and kappa fields."""
+    c = _case(3, 3, 5, 0.05)
+    u, _ = c.coef(19)
+    lam, _ = c.quad(20)
+    kap, _ = c.quad(21)
+    lam, kap = 1.5 + 0.5 * lam, 1.0 + 0.25 * kap
+    ref = operators.helmholtz(c.om, u, lam_field=lam, kappa_field=kap)
+
+    def view(x, off):
+        big = torch.zeros(x.size + off + 1, dtype=torch.float32, device="cuda")
+        big[off:off + x.size] = torch.tensor(x, device="cuda", dtype=torch.float32)
+        return big[off:off + x.size]
+
+    out = view(np.zeros(c.plan.n_coef), 3)
+    y = spx.helmholtz(c.plan, view(u, 1), lam_field=view(lam, 2), kappa_field=view(kap, 3), out=out)
+    assert rel_err(y, ref) <= 1e-5
+
+
 def test_autotune_keeps_results():
     c = _case(3, 6, 4, 0.05)
     u, ut = c.coef(16, torch.float32)
     out = torch.empty(c.plan.n_coef, dtype=torch.float32, device="cuda")
     c.plan.autotune("helmholtz", torch.float32, ut, out, reps=2)
     eb, nt, st = c.plan.get_tile("helmholtz", torch.float32, 4)
-    assert 1 <= eb <= 64 and nt % 32 == 0 and 1 <= st <= 4
+    assert 1 <= eb <= 64 and nt % 32 == 0 and 0 <= st <= 4   # stages 0: no L2 prefetch (pair kernel)
     assert rel_err(spx.helmholtz(c.plan, ut), operators.helmholtz(c.om, u)) <= 1e-5
 
 

@@ -30,7 +30,7 @@ static int default_eb(int dim, int Q) {
 
 size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& cfg) {
   if (uses_pair_kernel(plan, op, dtype)) {
-    const PairShape s = pair_shape(plan, cfg);
+    const PairShape s = pair_shape(plan, cfg, pair_threshold(plan));
     return s.nthreads > 512 ? SIZE_MAX : s.smem;
   }
   // worst case: coefficient fields present

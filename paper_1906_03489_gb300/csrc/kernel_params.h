@@ -25,42 +25,55 @@ __host__ __device__ constexpr int tab_len(int P, int QOFF) {
   return 2 * (P + QOFF) * (P + 1) + (P + QOFF) * (P + QOFF);
 }
 
-// Shared-memory layout of the FP32 3D Helmholtz element-pair kernel, in
-// float2 units.  Thread cc = a + Q b of an element pair takes roles (a, b);
+// Shared-memory layout of the FP32 3D Helmholtz kernel (helm_pair.cuh), in
+// units of its value type: float2 (two elements per thread, 8-byte accesses,
+// bank modulus M = 16 per half-warp) or float (one element per thread, M = 32
+// per warp).  Thread cc = a + Q b of an element group takes roles (a, b);
 // every array is laid out so that the role coordinate a thread varies with
-// `a` has stride 1 and the one it varies with `b` stride Q (mod 16), and the
-// pair stride is Q^2 (mod 16): a 16-lane half-warp then touches 16 distinct
-// 8-byte bank pairs in every phase (no bank conflicts).
+// `a` has stride 1 and the one it varies with `b` stride Q (mod M), and the
+// group stride is Q^2 (mod M): the lanes of a wavefront then touch distinct
+// banks in every phase (no bank conflicts).
 //   X (q, r, i)  = q + Q r + XS i     Y, Y3 (i, r, j) = i + Q r + YS j
 //   U, G0 (i, j, k) = i + Q j + US k  U', G1 (i, j, k) = i + Q j + GS k
 //   Y2 (i, q, r) = i + Q r + ZS q
-__host__ __device__ constexpr int up16(int x, int r) { return x + (((r % 16) - (x % 16)) % 16 + 16) % 16; }
+__host__ __device__ constexpr int upm(int x, int r, int M) { return x + (((r % M) - (x % M)) % M + M) % M; }
 
-template <int P, int Q>
+template <int P, int Q, int M>
 struct PairLayout {
   static constexpr int n = P + 1;
-  static constexpr int XS = up16((n - 1) + Q * (n - 1) + 1, 1);
-  static constexpr int YS = up16(Q * n, Q);
-  static constexpr int US = up16(Q * Q, 1);
-  static constexpr int GS = up16(Q * Q, Q);
-  static constexpr int ZS = up16(Q * n, 1);
+  static constexpr int XS = upm((n - 1) + Q * (n - 1) + 1, 1, M);
+  static constexpr int YS = upm(Q * n, Q, M);
+  static constexpr int US = upm(Q * Q, 1, M);
+  static constexpr int GS = upm(Q * Q, Q, M);
+  static constexpr int ZS = upm(Q * n, 1, M);
   static constexpr int mx(int a, int b) { return a > b ? a : b; }
-  // pair strides of the three buffers: A holds X then U / g0, C holds Y then
+  // group strides of the three buffers: A holds X then U / g0, C holds Y then
   // Y3, F holds U' / g1 then Y2
-  static constexpr int WA = up16(mx((n - 1) + Q * (n - 1) + XS * (Q - 1) + 1, Q * Q + US * (Q - 1)), Q * Q);
-  static constexpr int WC = up16((Q - 1) + Q * (n - 1) + YS * (Q - 1) + 1, Q * Q);
-  static constexpr int WF = up16(mx(Q * Q + GS * (Q - 1), (Q - 1) + Q * (n - 1) + ZS * (n - 1) + 1), Q * Q);
+  static constexpr int WA = upm(mx((n - 1) + Q * (n - 1) + XS * (Q - 1) + 1, Q * Q + US * (Q - 1)), Q * Q, M);
+  static constexpr int WC = upm((Q - 1) + Q * (n - 1) + YS * (Q - 1) + 1, Q * Q, M);
+  static constexpr int WF = upm(mx(Q * Q + GS * (Q - 1), (Q - 1) + Q * (n - 1) + ZS * (n - 1) + 1), Q * Q, M);
 };
 
-// Pair strides (float2) of order P at runtime (host side): {WA, WC, WF}.
-inline void pair_ws_of(int P, int QOFF, int w[3]) {
+// Orders packed two elements per thread in a variable-order launch (measured:
+// with the higher orders in pairs the single kernel's register budget makes
+// their bodies spill; 4 and 5 time alike, 6 and 8 slower).
+constexpr int kPairThrVar = 5;
+
+// Elements per thread of order P in a kernel that packs orders <= thr in pairs.
+__host__ __device__ constexpr int pair_lanes(int P, int thr) { return P <= thr ? 2 : 1; }
+
+// Group strides of order P in bytes at runtime (host side): {WA, WC, WF}.
+inline void pair_ws_bytes(int P, int QOFF, int lanes, uint64_t w[3]) {
   w[0] = w[1] = w[2] = 0;
-  switch (P * 4 + QOFF) {
-#define SPX_PWS(p)                                                                                  \
-  case p * 4 + 1: w[0] = PairLayout<p, p + 1>::WA; w[1] = PairLayout<p, p + 1>::WC; w[2] = PairLayout<p, p + 1>::WF; break; \
-  case p * 4 + 2: w[0] = PairLayout<p, p + 2>::WA; w[1] = PairLayout<p, p + 2>::WC; w[2] = PairLayout<p, p + 2>::WF; break;
+  switch ((P * 4 + QOFF) * 2 + (lanes == 2)) {
+#define SPX_PWS_(p, q, l, m)                                                                                         \
+  case (p * 4 + (q - p)) * 2 + (l == 2):                                                                              \
+    w[0] = 4u * l * PairLayout<p, q, m>::WA; w[1] = 4u * l * PairLayout<p, q, m>::WC; w[2] = 4u * l * PairLayout<p, q, m>::WF; \
+    break;
+#define SPX_PWS(p) SPX_PWS_(p, p + 1, 1, 32) SPX_PWS_(p, p + 1, 2, 16) SPX_PWS_(p, p + 2, 1, 32) SPX_PWS_(p, p + 2, 2, 16)
     SPX_PWS(1) SPX_PWS(2) SPX_PWS(3) SPX_PWS(4) SPX_PWS(5) SPX_PWS(6) SPX_PWS(7) SPX_PWS(8)
 #undef SPX_PWS
+#undef SPX_PWS_
     default: break;
   }
 }

@@ -12,34 +12,54 @@
 
 namespace spx {
 
-template <int PLO, int PHI, int QOFF, int REG>
-spx_status launch_pair_reg(const PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, const spx_plan* plan, int n_tiles,
-                           cudaStream_t stream) {
-  auto kern = helm_pair_kernel<PLO, PHI, QOFF, REG>;
-  static std::mutex mu;
-  static bool configured = false;
+template <class K, class Prm>
+spx_status launch_pair_kernel(K kern, const Prm& pp, int nthreads, uint32_t smem, const spx_plan* plan, int n_tiles,
+                              cudaStream_t stream, bool* configured, std::mutex* mu) {
   {
-    std::lock_guard<std::mutex> g(mu);
-    if (!configured) {
+    std::lock_guard<std::mutex> g(*mu);
+    if (!*configured) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(plan->max_smem));
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-      configured = true;
+      *configured = true;
     }
   }
   int nb = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, s.nthreads, s.smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile does not fit on an SM");
   const int grid = std::min<int64_t>(n_tiles, int64_t(nb) * plan->num_sms);
-  kern<<<grid, s.nthreads, s.smem, stream>>>(pp);
+  kern<<<grid, nthreads, smem, stream>>>(pp);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "Helmholtz pair kernel launch");
+  if (e != cudaSuccess) return cuda_fail(e, "Helmholtz kernel launch");
   return SPX_OK;
 }
 
-// FP32 Helmholtz on hexahedra: the element-pair kernel (helm_pair.cuh).
-// `stages` of the launch configuration is its L2 prefetch distance in tiles.
+template <int PLO, int PHI, int QOFF, int REG, int THR>
+spx_status launch_pair_reg(const PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, const spx_plan* plan, int n_tiles,
+                           cudaStream_t stream) {
+  static std::mutex mu;
+  static bool configured = false;
+  return launch_pair_kernel(helm_pair_kernel<PLO, PHI, QOFF, REG, THR>, pp, s.nthreads, s.smem, plan, n_tiles, stream,
+                            &configured, &mu);
+}
+
+// variable order: compute threads + one producer warp
+template <int PLO, int PHI, int QOFF, int REG, int THR>
+spx_status launch_varp_reg(const PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, const spx_plan* plan,
+                           int n_tiles, cudaStream_t stream) {
+  static std::mutex mu;
+  static bool configured = false;
+  if (s.nthreads + 32 > 1024) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile needs too many threads");
+  return launch_pair_kernel(helm_varp_kernel<PLO, PHI, QOFF, REG, THR>, pp, s.nthreads + 32, s.smem, plan,
+                            n_tiles, stream, &configured, &mu);
+}
+
+// FP32 Helmholtz on hexahedra (helm_pair.cuh).  `stages` of the launch
+// configuration is its L2 prefetch distance in tiles; `nthreads` the number
+// of threads per SM that the register budget must allow: 128 registers up to
+// 512, 96 up to 640, else 80 (uniform order).  Variable-order launches run the
+// producer-warp kernel at 128 registers, orders <= kPairThrVar in pairs.
 template <int PLO, int PHI, int QOFF>
 spx_status launch_pair(const LaunchReq& r) {
   const spx_plan* plan = r.plan;
@@ -66,7 +86,8 @@ spx_status launch_pair(const LaunchReq& r) {
   p.status = plan->d_status;
   p.lam = r.lam;
   p.n_tiles = tl.n;
-  const PairShape s = pair_shape(plan, cfg);
+  const int thr = pair_threshold(plan);
+  const PairShape s = pair_shape(plan, cfg, thr);
   if (s.nthreads > 512) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile needs more than 512 threads");
   if (s.smem > plan->max_smem) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile does not fit in shared memory");
   pp.pf = cfg.stages;
@@ -74,12 +95,15 @@ spx_status launch_pair(const LaunchReq& r) {
   pp.off_c = s.off_c;
   pp.off_f = s.off_f;
   pp.off_geo = s.off_geo;
-  // `nthreads` of the configuration is the number of threads per SM the
-  // register budget must allow: 128 registers up to 512, 96 up to 640, else 80.
-  const int budget = cfg.nthreads;
-  if (budget <= 512) return launch_pair_reg<PLO, PHI, QOFF, 128>(pp, s, plan, tl.n, r.stream);
-  if (budget <= 640) return launch_pair_reg<PLO, PHI, QOFF, 96>(pp, s, plan, tl.n, r.stream);
-  return launch_pair_reg<PLO, PHI, QOFF, 80>(pp, s, plan, tl.n, r.stream);
+  if constexpr (PLO == PHI) {
+    const int budget = cfg.nthreads;
+    if (budget <= 512) return launch_pair_reg<PLO, PHI, QOFF, 128, kMaxP>(pp, s, plan, tl.n, r.stream);
+    if (budget <= 640) return launch_pair_reg<PLO, PHI, QOFF, 96, kMaxP>(pp, s, plan, tl.n, r.stream);
+    return launch_pair_reg<PLO, PHI, QOFF, 80, kMaxP>(pp, s, plan, tl.n, r.stream);
+  } else {
+    pp.off_meta = s.off_meta;
+    return launch_varp_reg<PLO, PHI, QOFF, 128, kPairThrVar>(pp, s, plan, tl.n, r.stream);
+  }
 }
 
 template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>

@@ -80,32 +80,38 @@ inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const Launch
   return L;
 }
 
-// Launch shape of the FP32 3D Helmholtz pair kernel (helm_pair.cuh): a tile
-// of eb elements is ceil(eb / 2) element pairs of Q^2 threads each.  Shared
-// memory: an mbarrier, the three work buffers A, C, F (PairLayout strides
-// per pair) and one geometry slot holding the tile's [eb][7][Q^3] factors
-// (16-byte aligned region per element, or one region for a contiguous tile).
+// Launch shape of the FP32 3D Helmholtz kernel (helm_pair.cuh): orders
+// P <= thr run two elements per thread, the others one; a tile of eb elements
+// is ceil(eb / lanes) element groups of Q^2 threads each.  Shared memory: an
+// mbarrier, the three work buffers A, C, F (PairLayout strides per group) and
+// one geometry slot holding the tile's [eb][7][Q^3] factors.
 struct PairShape {
-  int nthreads;
+  int nthreads;                  // compute threads
   uint32_t off_a, off_c, off_f;  // byte offsets of the work buffers
   uint32_t off_geo;              // byte offset of the geometry slot
+  uint32_t off_meta;             // byte offset of the two tile-metadata buffers (variable order)
   uint32_t smem;
 };
 
-inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg) {
+// Tile metadata buffer of the variable-order kernel's producer warp (Tile +
+// coefficient and quadrature offsets of up to kMaxEB elements).
+constexpr uint32_t kTileMetaBytes = 16 + 2 * 8 * kMaxEB;
+
+inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg, int thr) {
   PairShape s{};
   uint64_t wa = 0, wc = 0, wf = 0, geo = 0;
   for (int P = 1; P <= kMaxP; ++P) {
     if (!plan->present[P]) continue;
     const int Q = P + plan->qoff;
     const int eb = cfg.order[P].eb;
-    const int pairs = (eb + 1) / 2;
-    int w[3];
-    pair_ws_of(P, plan->qoff, w);
-    s.nthreads = std::max(s.nthreads, pairs * Q * Q);
-    wa = std::max<uint64_t>(wa, uint64_t(pairs) * w[0] * 8);
-    wc = std::max<uint64_t>(wc, uint64_t(pairs) * w[1] * 8);
-    wf = std::max<uint64_t>(wf, uint64_t(pairs) * w[2] * 8);
+    const int lanes = pair_lanes(P, thr);
+    const int groups = (eb + lanes - 1) / lanes;
+    uint64_t w[3];
+    pair_ws_bytes(P, plan->qoff, lanes, w);
+    s.nthreads = std::max(s.nthreads, groups * Q * Q);
+    wa = std::max<uint64_t>(wa, groups * w[0]);
+    wc = std::max<uint64_t>(wc, groups * w[1]);
+    wf = std::max<uint64_t>(wf, groups * w[2]);
     geo = std::max<uint64_t>(geo, uint64_t(eb) * geo_erb(Q));   // per element regions
   }
   s.nthreads = (s.nthreads + 31) / 32 * 32;
@@ -113,9 +119,15 @@ inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg) {
   s.off_c = s.off_a + up128(wa);
   s.off_f = s.off_c + up128(wc);
   s.off_geo = s.off_f + up128(wf);
-  s.smem = s.off_geo + up128(geo);
+  s.off_meta = s.off_geo + up128(geo);
+  s.smem = s.off_meta + (plan->uniform ? 0 : up128(2 * kTileMetaBytes));
   return s;
 }
+
+// Orders packed two per thread: all of them in a uniform-order plan; in a
+// variable-order launch (one kernel for every order, registers allocated for
+// the largest body) only the low orders, so that no body spills.
+inline int pair_threshold(const spx_plan* plan) { return plan->uniform ? kMaxP : kPairThrVar; }
 
 inline bool uses_pair_kernel(const spx_plan* plan, int op, int dtype) {
   return op == OP_HELM && dtype == 1 && plan->dim == 3;

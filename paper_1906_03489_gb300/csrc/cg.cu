@@ -40,46 +40,67 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-reduces up to 2 values into partials[blockIdx.x * 2 + k]; returns true
-// in thread 0 of the last block to finish (which then sees every partial).
-__device__ bool block_reduce2(double a, double b, double* partials, unsigned int* ticket) {
+// Grid reduction of two values in a fixed order (bitwise reproducible for a
+// given grid): warp shuffles, per-warp sums in warp order, per-block partials
+// partials[2 * blockIdx.x + k]; the last block to finish (ticket) then sums
+// all partials with all its threads (thread t takes partials t, t + blockDim,
+// ... in order, then the same warp / block pattern).  Returns true in thread 0
+// of the last block, with the totals in *ta, *tb.
+__device__ bool grid_reduce2(double a, double b, double* partials, unsigned int* ticket, double* ta, double* tb) {
   __shared__ double sa[kRedThreads / 32], sb[kRedThreads / 32];
   __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   a = warp_sum(a);
   b = warp_sum(b);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     sa[w] = a;
     sb[w] = b;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double ta = 0.0, tb = 0.0;
-    for (int i = 0; i < kRedThreads / 32; ++i) {
-      ta += sa[i];
-      tb += sb[i];
+    double x = 0.0, y = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      x += sa[i];
+      y += sb[i];
     }
-    partials[2 * blockIdx.x] = ta;
-    partials[2 * blockIdx.x + 1] = tb;
+    partials[2 * blockIdx.x] = x;
+    partials[2 * blockIdx.x + 1] = y;
     __threadfence();
     const unsigned t = atomicAdd(ticket, 1u);
     last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  return last;
+  if (!last) return false;   // uniform across the block
+  __threadfence();
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += blockDim.x) {
+    x += static_cast<volatile const double*>(partials)[2 * i];
+    y += static_cast<volatile const double*>(partials)[2 * i + 1];
+  }
+  x = warp_sum(x);
+  y = warp_sum(y);
+  __syncthreads();
+  if (lane == 0) {
+    sa[w] = x;
+    sb[w] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+  x = 0.0;
+  y = 0.0;
+  for (int i = 0; i < nw; ++i) {
+    x += sa[i];
+    y += sb[i];
+  }
+  *ta = x;
+  *tb = y;
+  return true;
 }
 
-// Fixed-order sum of the partials by thread 0 of the last block.
-__device__ void final_sums(const double* partials, int nb, double* a, double* b) {
-  __threadfence();
-  double ta = 0.0, tb = 0.0;
-  for (int i = 0; i < nb; ++i) {
-    ta += static_cast<volatile const double*>(partials)[2 * i];
-    tb += static_cast<volatile const double*>(partials)[2 * i + 1];
-  }
-  *a = ta;
-  *b = tb;
-}
+// Element-wise loops over the global vectors: each thread takes kUnroll
+// independent indices per trip (g, g + S, ...; S = all threads), loads first,
+// so that several loads are in flight per thread.
+constexpr int kUnroll = 4;
 
 // ---- CSR transpose of l2g ------------------------------------------------
 __global__ void csr_count(const int32_t* l2g, int64_t nl, int32_t* cnt) {
@@ -169,7 +190,8 @@ __global__ void gather_if(const int32_t* __restrict__ l2g, const T* __restrict__
     loc[i] = g[l2g[i]];
 }
 
-// q = assemble(ql); pAp = <p, q>; alpha = rz / pAp
+// q = assemble(ql); pAp = <p, q>; alpha = rz / pAp.  The local copies of
+// kUnroll global indices are gathered in lockstep (each sum in CSR order).
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) assemble_dot(const int32_t* __restrict__ row_ptr,
                                                             const int32_t* __restrict__ cols,
@@ -178,15 +200,40 @@ __global__ void __launch_bounds__(kRedThreads) assemble_dot(const int32_t* __res
                                                             double* partials) {
   if (sc->done) return;
   double acc = 0.0;
-  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
-    T s = T(0);
-    for (int32_t k = row_ptr[g]; k < row_ptr[g + 1]; ++k) s += ql[cols[k]];
-    q[g] = s;
-    acc += static_cast<double>(p[g]) * static_cast<double>(s);
+  const int64_t S = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g0 < ng; g0 += kUnroll * S) {
+    int32_t k0[kUnroll], k1[kUnroll];
+    T pv[kUnroll], sv[kUnroll];
+    int len = 0;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t g = g0 + u * S;
+      k0[u] = k1[u] = 0;
+      pv[u] = T(0);
+      sv[u] = T(0);
+      if (g < ng) {
+        k0[u] = row_ptr[g];
+        k1[u] = row_ptr[g + 1];
+        pv[u] = p[g];
+      }
+      len = max(len, k1[u] - k0[u]);
+    }
+    for (int j = 0; j < len; ++j) {
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (k0[u] + j < k1[u]) sv[u] += ql[cols[k0[u] + j]];
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t g = g0 + u * S;
+      if (g < ng) {
+        q[g] = sv[u];
+        acc += static_cast<double>(pv[u]) * static_cast<double>(sv[u]);
+      }
+    }
   }
-  if (block_reduce2(acc, 0.0, partials, &sc->ticket) && threadIdx.x == 0) {
-    double pAp, unused;
-    final_sums(partials, gridDim.x, &pAp, &unused);
+  double pAp, unused;
+  if (grid_reduce2(acc, 0.0, partials, &sc->ticket, &pAp, &unused)) {
     sc->pAp = pAp;
     sc->alpha = sc->rz / pAp;
     sc->ticket = 0;
@@ -202,18 +249,36 @@ __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* _
   if (sc->done) return;
   const T alpha = static_cast<T>(sc->alpha);
   double arz = 0.0, arr = 0.0;
-  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
-    x[g] += alpha * p[g];
-    const T rv = r[g] - alpha * q[g];
-    r[g] = rv;
-    const T zv = minv[g] * rv;
-    z[g] = zv;
-    arz += static_cast<double>(rv) * static_cast<double>(zv);
-    arr += static_cast<double>(rv) * static_cast<double>(rv);
+  const int64_t S = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g0 < ng; g0 += kUnroll * S) {
+    T xv[kUnroll], rv[kUnroll], pv[kUnroll], qv[kUnroll], mv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t g = g0 + u * S;
+      if (g < ng) {
+        xv[u] = x[g];
+        rv[u] = r[g];
+        pv[u] = p[g];
+        qv[u] = q[g];
+        mv[u] = minv[g];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t g = g0 + u * S;
+      if (g < ng) {
+        x[g] = xv[u] + alpha * pv[u];
+        const T rn = rv[u] - alpha * qv[u];
+        r[g] = rn;
+        const T zv = mv[u] * rn;
+        z[g] = zv;
+        arz += static_cast<double>(rn) * static_cast<double>(zv);
+        arr += static_cast<double>(rn) * static_cast<double>(rn);
+      }
+    }
   }
-  if (block_reduce2(arz, arr, partials, &sc->ticket) && threadIdx.x == 0) {
-    double rz, rr;
-    final_sums(partials, gridDim.x, &rz, &rr);
+  double rz, rr;
+  if (grid_reduce2(arz, arr, partials, &sc->ticket, &rz, &rr)) {
     sc->rz_new = rz;
     sc->beta = rz / sc->rz;
     sc->rz = rz;
@@ -253,9 +318,8 @@ __global__ void __launch_bounds__(kRedThreads) cg_start(const T* __restrict__ r,
     arz += static_cast<double>(rv) * static_cast<double>(zv);
     arr += static_cast<double>(rv) * static_cast<double>(rv);
   }
-  if (block_reduce2(arz, arr, partials, &sc->ticket) && threadIdx.x == 0) {
-    double rz, rr;
-    final_sums(partials, gridDim.x, &rz, &rr);
+  double rz, rr;
+  if (grid_reduce2(arz, arr, partials, &sc->ticket, &rz, &rr)) {
     sc->rz = rz;
     sc->rr = rr;
     sc->it = 0;
@@ -276,9 +340,8 @@ __global__ void __launch_bounds__(kRedThreads) residual64(const double* __restri
     arr += rv * rv;
     aff += f[g] * f[g];
   }
-  if (block_reduce2(arr, aff, partials, &sc->ticket) && threadIdx.x == 0) {
-    double rr, ff;
-    final_sums(partials, gridDim.x, &rr, &ff);
+  double rr, ff;
+  if (grid_reduce2(arr, aff, partials, &sc->ticket, &rr, &ff)) {
     sc->rr = rr;
     sc->ff = ff;
     sc->ticket = 0;
@@ -401,10 +464,7 @@ spx_status build_csr(Solver& s) {
   SPX_CK(cudaMemsetAsync(w.cursor, 0, (s.ng + 1) * 4, s.st));
   csr_fill<<<s.grid_v, 256, 0, s.st>>>(s.l2g, s.nl, w.row_ptr, w.cursor, w.cols);
   csr_sort<<<s.grid_v, 256, 0, s.st>>>(w.row_ptr, w.cols, s.ng);
-  int32_t cnt_zero = 0;
-  // a global index with no local entry would make A singular
   SPX_CK(cudaGetLastError());
-  (void)cnt_zero;
   return SPX_OK;
 }
 
@@ -530,7 +590,7 @@ extern "C" spx_status spx_cg_workspace_bytes(const spx_plan* plan, int64_t n_glo
                                              size_t* bytes) {
   if (!plan || !o || !bytes || n_global < 0) return fail(SPX_ERR_INVALID_ARG, "cg_workspace_bytes: bad argument");
   if (o->precision != 0 && o->precision != 1) return fail(SPX_ERR_INVALID_ARG, "cg: precision must be 0 or 1");
-  const int nred = plan->num_sms * 2;
+  const int nred = plan->num_sms * 8;
   *bytes = carve(nullptr, n_global, plan->n_coef, nred, o->precision).bytes;
   return SPX_OK;
 }
@@ -566,7 +626,7 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
   s.ng = n_global;
   s.nl = plan->n_coef;
   s.lam = lambda;
-  s.nred = plan->num_sms * 2;
+  s.nred = plan->num_sms * 8;
   s.grid_v = plan->num_sms * 8;
   s.w = carve(static_cast<char*>(workspace), n_global, plan->n_coef, s.nred, o->precision);
   if (ws_bytes < s.w.bytes) return fail(SPX_ERR_NO_MEMORY, "cg_solve: workspace smaller than cg_workspace_bytes");

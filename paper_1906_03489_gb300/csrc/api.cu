@@ -155,8 +155,9 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
   p->n_quad = p->quad_off[p->E];
   for (int P = 1; P <= kMaxP; ++P) {
     const int Q = P + qoff, n = P + 1;
-    p->tab[P].assign(2 * Q * n + Q * Q, 0.0);
+    p->tab[P].assign(tab_len(P, qoff), 0.0);
     basis_tables(P, Q, nullptr, nullptr, p->tab[P].data(), p->tab[P].data() + Q * n, p->tab[P].data() + 2 * Q * n);
+    eo_tables(P, Q, p->tab[P].data());
   }
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {

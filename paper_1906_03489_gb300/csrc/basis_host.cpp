@@ -178,4 +178,29 @@ spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* 
   return SPX_OK;
 }
 
+// Even-odd coefficients of order P (layout: EOLayout in kernel_params.h),
+// appended after B, dB, D of `tab`.
+void eo_tables(int P, int Q, double* tab) {
+  const int n = P + 1, H = Q / 2, Hc = (Q + 1) / 2;
+  const double* B = tab;
+  const double* D = tab + 2 * Q * n;
+  double* Bs = tab + 2 * Q * n + Q * Q;
+  double* Bd = Bs + Hc;
+  double* Dp = Bd + Hc;
+  double* Dm = Dp + H * H;
+  double* Tp = Dm + H * H;
+  double* Tm = Tp + H * H;
+  for (int i = 0; i < Hc; ++i) {
+    Bs[i] = 0.5 * (B[i * n] + B[i * n + P]);
+    Bd[i] = 0.5 * (B[i * n] - B[i * n + P]);
+  }
+  for (int i = 0; i < H; ++i)
+    for (int j = 0; j < H; ++j) {
+      Dp[i * H + j] = 0.5 * (D[i * Q + j] + D[i * Q + Q - 1 - j]);
+      Dm[i * H + j] = 0.5 * (D[i * Q + j] - D[i * Q + Q - 1 - j]);
+      Tp[i * H + j] = 0.5 * (D[j * Q + i] + D[(Q - 1 - j) * Q + i]);
+      Tm[i * H + j] = 0.5 * (D[j * Q + i] - D[(Q - 1 - j) * Q + i]);
+    }
+}
+
 }  // namespace spx

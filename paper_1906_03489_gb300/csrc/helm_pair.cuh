@@ -32,50 +32,10 @@
 #pragma once
 #include <type_traits>
 
+#include "lanes.cuh"
 #include "op_kernel.cuh"
 
 namespace spx {
-
-// Value types of the kernel: float2 = the same entry of two elements (packed
-// f32x2 arithmetic, 8-byte shared accesses, bank modulus 16 per half-warp);
-// float = one element (bank modulus 32 per warp).
-template <class V>
-struct Lane;
-template <>
-struct Lane<float2> {
-  static constexpr int L = 2, M = 16;
-  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
-  static __device__ __forceinline__ float2 bcast(float a) { return make_float2(a, a); }
-  static __device__ __forceinline__ float2 fma(float a, float2 x, float2 y) { return __ffma2_rn(make_float2(a, a), x, y); }
-  static __device__ __forceinline__ float2 fmav(float2 a, float2 x, float2 y) { return __ffma2_rn(a, x, y); }
-  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-  static __device__ __forceinline__ float2 pair(float x, float y) { return make_float2(x, y); }
-  static __device__ __forceinline__ float2 ldcs2(const float* p0, const float* p1) {
-    return make_float2(__ldcs(p0), __ldcs(p1));
-  }
-  static __device__ __forceinline__ void stcs2(float* y0, float* y1, float2 v, bool two) {
-    __stcs(y0, v.x);
-    if (two) __stcs(y1, v.y);
-  }
-  static __device__ __forceinline__ float2 from2(float2 v) { return v; }
-  static __device__ __forceinline__ float2 to2(float2 v) { return v; }
-};
-template <>
-struct Lane<float> {
-  static constexpr int L = 1, M = 32;
-  static __device__ __forceinline__ float zero() { return 0.f; }
-  static __device__ __forceinline__ float bcast(float a) { return a; }
-  static __device__ __forceinline__ float fma(float a, float x, float y) { return fmaf(a, x, y); }
-  static __device__ __forceinline__ float fmav(float a, float x, float y) { return fmaf(a, x, y); }
-  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
-  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
-  static __device__ __forceinline__ float pair(float x, float) { return x; }
-  static __device__ __forceinline__ float ldcs2(const float* p0, const float*) { return __ldcs(p0); }
-  static __device__ __forceinline__ void stcs2(float* y0, float*, float v, bool) { __stcs(y0, v); }
-  static __device__ __forceinline__ float from2(float2 v) { return v.x; }
-  static __device__ __forceinline__ float2 to2(float v) { return make_float2(v, 0.f); }
-};
 
 // L2 prefetch of [g, g + bytes): the 16-byte aligned interior only.
 __device__ __forceinline__ void prefetch_l2(const void* g, uint64_t bytes) {
@@ -220,8 +180,6 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
   constexpr int n = P + 1, XS = L::XS, YS = L::YS, US = L::US, GS = L::GS, ZS = L::ZS;
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
   const int tid = ctl.tid;
-  const float* B = tab;              // B[Q][n]
-  const float* D = tab + 2 * Q * n;  // D[Q][Q]
   const int pi = tid / Q2;
   const int cc = tid - pi * Q2;
   const int a = cc % Q, b = cc / Q;
@@ -242,28 +200,20 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
   const int64_t c0 = off[0], c1 = off[1], q0 = off[2], q1 = off[3];
   // S1: pencil along p at (q, r) = (a, b): X(q, r, i) = sum_p B[i][p] u[r][q][p] -> A
   if (act && a < n && b < n) {
-    const V* v = v1;
+    V x[Q];
+    eo_b<P, Q>(tab, v1, x);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int k = 0; k < n; ++k) acc = Vt::fma(B[i * n + k], v[k], acc);
-      A[a + Q * b + XS * i] = acc;
-    }
+    for (int i = 0; i < Q; ++i) A[a + Q * b + XS * i] = x[i];
   }
   ctl.sync();
   // S2: pencil along q at (i, r) = (a, b): Y(i, r, j) = sum_q B[j][q] X(q, r, i) -> C
   if (act && b < n) {
-    V v[n];
+    V v[n], y[Q];
 #pragma unroll
     for (int q = 0; q < n; ++q) v[q] = A[q + Q * b + XS * a];
+    eo_b<P, Q>(tab, v, y);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int q = 0; q < n; ++q) acc = Vt::fma(B[j * n + q], v[q], acc);
-      C[a + Q * b + YS * j] = acc;
-    }
+    for (int j = 0; j < Q; ++j) C[a + Q * b + YS * j] = y[j];
   }
   ctl.sync();
   // S3: column (i, j) = (a, b): u = B y along xi_3 -> U in A and U' in F; d2 = D u in registers
@@ -272,48 +222,31 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
     V y[n];
 #pragma unroll
     for (int r = 0; r < n; ++r) y[r] = C[a + Q * r + YS * b];
+    eo_b<P, Q>(tab, y, u);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int r = 0; r < n; ++r) acc = Vt::fma(B[k * n + r], y[r], acc);
-      u[k] = acc;
-      A[a + Q * b + US * k] = acc;
-      F[a + Q * b + GS * k] = acc;
+      A[a + Q * b + US * k] = u[k];
+      F[a + Q * b + GS * k] = u[k];
     }
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = Vt::fma(D[k * Q + m], u[m], acc);
-      g2[k] = acc;
-    }
+    eo_d<P, Q, false>(tab, u, g2);
   }
   ctl.sync();
   // S4: gradient pencils, in place: along xi_1 at (j, k) = (b, a) in A (U -> d0),
   // along xi_2 at (i, k) = (a, b) in F (U' -> d1)
   if (act) {
-    V v[Q];
+    V v[Q], d[Q];
     V* g = A + Q * b + US * a;
 #pragma unroll
     for (int m = 0; m < Q; ++m) v[m] = g[m];
+    eo_d<P, Q, false>(tab, v, d);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = Vt::fma(D[i * Q + m], v[m], acc);
-      g[i] = acc;
-    }
+    for (int i = 0; i < Q; ++i) g[i] = d[i];
     g = F + a + GS * b;
 #pragma unroll
     for (int m = 0; m < Q; ++m) v[m] = g[Q * m];
+    eo_d<P, Q, false>(tab, v, d);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = Vt::fma(D[j * Q + m], v[m], acc);
-      g[Q * j] = acc;
-    }
+    for (int j = 0; j < Q; ++j) g[Q * j] = d[j];
   }
   // the tile's geometry: wait for it to land (ends the phase with a barrier)
   if (!ctl.geo_wait(p, t, Q)) return false;
@@ -357,83 +290,60 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
       g2[k] = r2;
       u[k] = Vt::mul(lj, u[k]);
     }
+    eo_d<P, Q, true>(tab, g2, z);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      V acc = u[k];
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = Vt::fma(D[m * Q + k], g2[m], acc);
-      z[k] = acc;
-    }
+    for (int k = 0; k < Q; ++k) z[k] = Vt::add(z[k], u[k]);
   }
   ctl.sync();
   // every thread is done with the geometry slot
   ctl.template slot_released<P, Q, V>(p, pi, a, b);
   // S6: transposed-gradient pencils, in place (same roles as S4)
   if (act) {
-    V v[Q];
+    V v[Q], d[Q];
     V* g = A + Q * b + US * a;
 #pragma unroll
     for (int m = 0; m < Q; ++m) v[m] = g[m];
+    eo_d<P, Q, true>(tab, v, d);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = Vt::fma(D[m * Q + i], v[m], acc);
-      g[i] = acc;
-    }
+    for (int i = 0; i < Q; ++i) g[i] = d[i];
     g = F + a + GS * b;
 #pragma unroll
     for (int m = 0; m < Q; ++m) v[m] = g[Q * m];
+    eo_d<P, Q, true>(tab, v, d);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = Vt::fma(D[m * Q + j], v[m], acc);
-      g[Q * j] = acc;
-    }
+    for (int j = 0; j < Q; ++j) g[Q * j] = d[j];
   }
   ctl.sync();
   // S7: column (i, j) = (a, b): z += both contributions; B^T along xi_3 -> Y3(i, j, r) in C
   if (act) {
+    V y3[n];
 #pragma unroll
     for (int k = 0; k < Q; ++k) z[k] = Vt::add(z[k], Vt::add(A[a + Q * b + US * k], F[a + Q * b + GS * k]));
+    eo_bt<P, Q>(tab, z, y3);
 #pragma unroll
-    for (int r = 0; r < n; ++r) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int k = 0; k < Q; ++k) acc = Vt::fma(B[k * n + r], z[k], acc);
-      C[a + Q * r + YS * b] = acc;
-    }
+    for (int r = 0; r < n; ++r) C[a + Q * r + YS * b] = y3[r];
   }
   ctl.sync();
   // S8: pencil along j at (i, r) = (a, b): Y2(i, q, r) = sum_j B[j][q] Y3(i, j, r) -> F
   if (act && b < n) {
-    V v[Q];
+    V v[Q], y2[n];
 #pragma unroll
     for (int j = 0; j < Q; ++j) v[j] = C[a + Q * b + YS * j];
+    eo_bt<P, Q>(tab, v, y2);
 #pragma unroll
-    for (int q = 0; q < n; ++q) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int j = 0; j < Q; ++j) acc = Vt::fma(B[j * n + q], v[j], acc);
-      F[a + Q * b + ZS * q] = acc;
-    }
+    for (int q = 0; q < n; ++q) F[a + Q * b + ZS * q] = y2[q];
   }
   ctl.sync();
   // S9: pencil along i at (q, r) = (a, b): y[r][q][p] = sum_i B[i][p] Y2(i, q, r) -> HBM
   if (act && a < n && b < n) {
-    V v[Q];
+    V v[Q], y[n];
 #pragma unroll
     for (int i = 0; i < Q; ++i) v[i] = F[i + Q * b + ZS * a];
+    eo_bt<P, Q>(tab, v, y);
     float* y0 = p.out0 + c0 + (b * n + a) * n;
     float* y1 = p.out0 + c1 + (b * n + a) * n;
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-      V acc = Vt::zero();
-#pragma unroll
-      for (int i = 0; i < Q; ++i) acc = Vt::fma(B[i * n + k], v[i], acc);
-      Vt::stcs2(y0 + k, y1 + k, acc, two);
-    }
+    for (int k = 0; k < n; ++k) Vt::stcs2(y0 + k, y1 + k, y[k], two);
   }
   return true;
 }

@@ -20,10 +20,32 @@ struct Tile {
   int32_t contig;
 };
 
+// Per-order table: B[Q][n], dB[Q][n], D[Q][Q], then the even-odd
+// coefficients (EOLayout): Bs[Hc], Bd[Hc], Dp[H][H], Dm[H][H], Tp[H][H],
+// Tm[H][H] with H = Q / 2, Hc = (Q + 1) / 2.
+__host__ __device__ constexpr int eo_len(int Q) { return 2 * ((Q + 1) / 2) + 4 * (Q / 2) * (Q / 2); }
 __host__ __device__ constexpr int tab_len(int P, int QOFF) {
-  // B[Q][n], dB[Q][n], D[Q][Q]
-  return 2 * (P + QOFF) * (P + 1) + (P + QOFF) * (P + QOFF);
+  return 2 * (P + QOFF) * (P + 1) + (P + QOFF) * (P + QOFF) + eo_len(P + QOFF);
 }
+
+// Even-odd form of the 1D operators (symmetric GLL points xi_{Q-1-i} = -xi_i):
+// the modified basis has phi_0(-x) = phi_P(x) and phi_b(-x) = (-1)^(b-1)
+// phi_b(x) for the bubbles, and the collocation derivative D is
+// centro-antisymmetric, D[Q-1-i][Q-1-j] = -D[i][j].  With e = v_0 + v_P,
+// o = v_0 - v_P, s_j = v_j + v_{Q-1-j}, d_j = v_j - v_{Q-1-j}:
+//   (B v)_i, (B v)_{Q-1-i} = S_i +- D_i,  S_i = Bs_i e + sum_{b odd} B_ib v_b,
+//                                           D_i = Bd_i o + sum_{b even} B_ib v_b
+//   (D v)_i, (D v)_{Q-1-i} = E_i +- F_i,  E_i = sum_j Dm_ij d_j,
+//                                           F_i = sum_j Dp_ij s_j (+ D_iM v_M, Q odd)
+// with Bs_i = (B_i0 + B_iP) / 2, Bd_i = (B_i0 - B_iP) / 2,
+// Dp_ij = (D_ij + D_i,Q-1-j) / 2, Dm_ij = (D_ij - D_i,Q-1-j) / 2 and Tp, Tm the
+// same for D^T; the transposed contractions follow by the same symmetry.
+template <int P, int Q>
+struct EOLayout {
+  static constexpr int n = P + 1, H = Q / 2, Hc = (Q + 1) / 2;
+  static constexpr int Bs = 2 * Q * n + Q * Q, Bd = Bs + Hc, Dp = Bd + Hc, Dm = Dp + H * H, Tp = Dm + H * H,
+                       Tm = Tp + H * H;
+};
 
 // Shared-memory layout of the FP32 3D Helmholtz kernel (helm_pair.cuh), in
 // units of its value type: float2 (two elements per thread, 8-byte accesses,

@@ -40,8 +40,8 @@ spx_status launch_pair_reg(const PairParams<PLO, PHI, QOFF>& pp, const PairShape
                            cudaStream_t stream) {
   static std::mutex mu;
   static bool configured = false;
-  return launch_pair_kernel(helm_pair_kernel<PLO, PHI, QOFF, REG, THR>, pp, s.nthreads, s.smem, plan, n_tiles, stream,
-                            &configured, &mu);
+  return launch_pair_kernel(helm_pair_kernel<PLO, PHI, QOFF, REG, THR>, pp, s.nthreads, s.smem, plan, n_tiles,
+                            stream, &configured, &mu);
 }
 
 // variable order: compute threads + one producer warp

@@ -13,6 +13,7 @@
 #pragma once
 #include "device_common.cuh"
 #include "kernel_params.h"
+#include "lanes.cuh"
 
 namespace spx {
 
@@ -526,10 +527,9 @@ struct RoleShape {
 template <typename T, int P, int Q, class Rel>
 __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel release) {
   using S_ = RoleShape<T, P, Q>;
+  using Vt = Lane<T>;
   constexpr int n = S_::n, S = S_::S, SN = S_::SN, PL = S_::PL, WS = S_::WS;
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
-  const T* B = tab;                  // B[Q][n]
-  const T* D = tab + 2 * Q * n;      // D[Q][Q]
   const int el = c.tid / Q2;
   const int cc = c.tid - el * Q2;
   const int a = cc % Q, b = cc / Q;
@@ -542,31 +542,23 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
   // S1: pencil along p at (q, r) = (a, b): X[r][q][i] = sum_p B[i][p] C[r][q][p]
   if (act && a < n && b < n) {
     const T* C = c.staged(0, el) + (b * n + a) * n;
-    T v[n];
+    T v[n], x[Q];
 #pragma unroll
     for (int p = 0; p < n; ++p) v[p] = C[p];
+    eo_b<P, Q>(tab, v, x);
     T* dst = W0 + (b * n + a) * S;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      T acc = T(0);
-#pragma unroll
-      for (int p = 0; p < n; ++p) acc = fma(B[i * n + p], v[p], acc);
-      dst[i] = acc;
-    }
+    for (int i = 0; i < Q; ++i) dst[i] = x[i];
   }
   SPX_SYNC();
   // S2: pencil along q at (i, r) = (a, b): Y[j][i][r] = sum_q B[j][q] X[r][q][i]
   if (act && b < n) {
-    T v[n];
+    T v[n], y[Q];
 #pragma unroll
     for (int q = 0; q < n; ++q) v[q] = W0[(b * n + q) * S + a];
+    eo_b<P, Q>(tab, v, y);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      T acc = T(0);
-#pragma unroll
-      for (int q = 0; q < n; ++q) acc = fma(B[j * n + q], v[q], acc);
-      W1[(j * Q + a) * SN + b] = acc;
-    }
+    for (int j = 0; j < Q; ++j) W1[(j * Q + a) * SN + b] = y[j];
   }
   SPX_SYNC();
   // S3: column (i, j) = (a, b): u = B y (xi_3), d2 = D u; U[k][j][i] = u
@@ -575,44 +567,25 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
     T y[n];
 #pragma unroll
     for (int r = 0; r < n; ++r) y[r] = W1[(b * Q + a) * SN + r];
+    eo_b<P, Q>(tab, y, u);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      T acc = T(0);
-#pragma unroll
-      for (int r = 0; r < n; ++r) acc = fma(B[k * n + r], y[r], acc);
-      u[k] = acc;
-      W2[k * PL + b * S + a] = acc;
-    }
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = fma(D[k * Q + m], u[m], acc);
-      g2[k] = acc;
-    }
+    for (int k = 0; k < Q; ++k) W2[k * PL + b * S + a] = u[k];
+    eo_d<P, Q, false>(tab, u, g2);
   }
   SPX_SYNC();
   // S4: gradient pencils: along xi_1 at (j, k) = (a, b) -> W3, along xi_2 at (i, k) = (a, b) -> W4
   if (act) {
-    T v[Q];
+    T v[Q], d[Q];
 #pragma unroll
     for (int m = 0; m < Q; ++m) v[m] = W2[b * PL + a * S + m];
+    eo_d<P, Q, false>(tab, v, d);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = fma(D[i * Q + m], v[m], acc);
-      W3[b * PL + a * S + i] = acc;
-    }
+    for (int i = 0; i < Q; ++i) W3[b * PL + a * S + i] = d[i];
 #pragma unroll
     for (int m = 0; m < Q; ++m) v[m] = W2[b * PL + m * S + a];
+    eo_d<P, Q, false>(tab, v, d);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = fma(D[j * Q + m], v[m], acc);
-      W4[b * PL + j * S + a] = acc;
-    }
+    for (int j = 0; j < Q; ++j) W4[b * PL + j * S + a] = d[j];
   }
   SPX_SYNC();
   // S5: column (i, j) = (a, b): pointwise; g0 -> W3, g1 -> W4, g2 and v in registers
@@ -635,84 +608,62 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
       g2[k] = kk * (g02 * d0 + g12 * d1 + g22 * d2);
       u[k] = ll * jw * u[k];
     }
+    eo_d<P, Q, true>(tab, g2, z);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      T acc = u[k];
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = fma(D[m * Q + k], g2[m], acc);
-      z[k] = acc;
-    }
+    for (int k = 0; k < Q; ++k) z[k] += u[k];
   }
   SPX_SYNC();
   release();
   // S6: transposed-gradient pencils, in place: along xi_1 at (j, k) = (a, b) in W3,
   // along xi_2 at (i, k) = (a, b) in W4
   if (act) {
-    T v[Q];
+    T v[Q], d[Q];
 #pragma unroll
     for (int m = 0; m < Q; ++m) v[m] = W3[b * PL + a * S + m];
+    eo_d<P, Q, true>(tab, v, d);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = fma(D[m * Q + i], v[m], acc);
-      W3[b * PL + a * S + i] = acc;
-    }
+    for (int i = 0; i < Q; ++i) W3[b * PL + a * S + i] = d[i];
 #pragma unroll
     for (int m = 0; m < Q; ++m) v[m] = W4[b * PL + m * S + a];
+    eo_d<P, Q, true>(tab, v, d);
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < Q; ++m) acc = fma(D[m * Q + j], v[m], acc);
-      W4[b * PL + j * S + a] = acc;
-    }
+    for (int j = 0; j < Q; ++j) W4[b * PL + j * S + a] = d[j];
   }
   SPX_SYNC();
   // S7: column (i, j) = (a, b): z += both contributions; y3 = B^T z (xi_3) -> Y3[r][i][j]
   if (act) {
+    T y3[n];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int w = k * PL + b * S + a;
       z[k] += W3[w] + W4[w];
     }
+    eo_bt<P, Q>(tab, z, y3);
 #pragma unroll
-    for (int r = 0; r < n; ++r) {
-      T acc = T(0);
-#pragma unroll
-      for (int k = 0; k < Q; ++k) acc = fma(B[k * n + r], z[k], acc);
-      W0[(r * Q + a) * S + b] = acc;
-    }
+    for (int r = 0; r < n; ++r) W0[(r * Q + a) * S + b] = y3[r];
   }
   SPX_SYNC();
   // S8: pencil along j at (i, r) = (a, b): Y2[r][q][i] = sum_j B[j][q] Y3[r][i][j]
   if (act && b < n) {
-    T v[Q];
+    T v[Q], y2[n];
 #pragma unroll
     for (int j = 0; j < Q; ++j) v[j] = W0[(b * Q + a) * S + j];
+    eo_bt<P, Q>(tab, v, y2);
 #pragma unroll
-    for (int q = 0; q < n; ++q) {
-      T acc = T(0);
-#pragma unroll
-      for (int j = 0; j < Q; ++j) acc = fma(B[j * n + q], v[j], acc);
-      W1[(b * n + q) * S + a] = acc;
-    }
+    for (int q = 0; q < n; ++q) W1[(b * n + q) * S + a] = y2[q];
   }
   SPX_SYNC();
   // S9: pencil along i at (q, r) = (a, b): y[p][q][r] = sum_i B[i][p] Y2[r][q][i] -> HBM
   if (act && a < n && b < n) {
-    T v[Q];
+    T v[Q], y[n];
 #pragma unroll
     for (int i = 0; i < Q; ++i) v[i] = W1[(b * n + a) * S + i];
+    eo_bt<P, Q>(tab, v, y);
     T* dst = out + c.gcoef[el] + (b * n + a) * n;
 #pragma unroll
-    for (int p = 0; p < n; ++p) {
-      T acc = T(0);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) acc = fma(B[i * n + p], v[i], acc);
-      dst[p] = acc;
-    }
+    for (int p = 0; p < n; ++p) dst[p] = y[p];
   }
+  (void)Vt::L;
 }
 
 // ---- BwdTrans and reference gradient of one staged coefficient stream -----

@@ -107,4 +107,7 @@ size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& c
 // Basis tables (host FP64): fills B, dB, D as documented in spx.h.
 spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* dB, double* D);
 
+// Even-odd coefficients appended to a per-order table (EOLayout).
+void eo_tables(int P, int Q, double* tab);
+
 }  // namespace spx

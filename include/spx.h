@@ -247,17 +247,21 @@ spx_status spx_assemble(const spx_plan *plan, spx_dtype dtype, const int32_t *l2
 /* Options of spx_cg_solve. */
 typedef struct {
   double tol;        /* relative residual ||f - A x||_2 / ||f||_2 to reach (e.g. 1e-10) */
-  int maxit;         /* iteration cap of the FP64 CG, or of each inner FP32 solve */
-  int precision;     /* 0 = all-FP64 CG; 1 = FP32 inner CG inside FP64 refinement */
-  double inner_tol;  /* relative tolerance of each inner FP32 solve (precision 1) */
-  int max_outer;     /* cap on refinement steps (precision 1) */
+  int maxit;         /* iteration cap: FP64 CG (0), each inner FP32 solve (1), all FP32 iterations (2) */
+  int precision;     /* 0 = all-FP64 CG; 1 = FP32 inner CG inside FP64 refinement, restarted after
+                        every refinement step; 2 = FP32 CG with reliable updates: one FP32 run whose
+                        recurrence residual is replaced by the FP64 residual of the corrected x
+                        (x += the FP32 correction) each time it has fallen by inner_tol */
+  double inner_tol;  /* residual reduction of each FP32 run between FP64 residuals (1, 2); a run
+                        also stops once its residual is below half of what tol still asks */
+  int max_outer;     /* cap on refinement steps / FP64 residual replacements (1, 2) */
   int use_graph;     /* 1: capture the iteration in a CUDA graph */
   int check_every;   /* iterations between host-side convergence checks (>= 1) */
 } spx_cg_opts;
 
 typedef struct {
-  int iters;            /* total CG iterations (inner iterations for precision 1) */
-  int outer_iters;      /* refinement steps (precision 1), else 0 */
+  int iters;            /* total CG iterations (FP32 iterations for precisions 1, 2) */
+  int outer_iters;      /* refinement steps / residual replacements (precisions 1, 2), else 0 */
   double rel_residual;  /* final ||f - A x||_2 / ||f||_2 computed in FP64 */
 } spx_cg_result;
 
@@ -268,7 +272,7 @@ spx_status spx_cg_workspace_bytes(const spx_plan *plan, int64_t n_global, const 
  * l2g) by Jacobi-preconditioned CG.  f: device FP64 [n_global]; x: device
  * FP64 [n_global], initial guess in, solution out.  workspace: device,
  * >= spx_cg_workspace_bytes, 256-byte aligned.  Needs geometry for FP64
- * (and FP32 when precision = 1).  Synchronises the stream (it reads residual
+ * (and FP32 when precision = 1 or 2).  Synchronises the stream (it reads residual
  * norms on the host).  Returns SPX_ERR_NOT_CONVERGED with `result` filled if
  * the caps are reached, SPX_ERR_NONFINITE on a NaN/Inf residual. */
 spx_status spx_cg_solve(const spx_plan *plan, double lambda, const int32_t *l2g, int64_t n_global, const double *f,

@@ -198,7 +198,7 @@ def assemble(plan, l2g, local, n_global, out=None):
 def _cg_opts(tol, maxit, precision, inner_tol, max_outer, use_graph, check_every):
     o = CgOpts()
     o.tol, o.maxit = float(tol), int(maxit)
-    o.precision = {"f64": 0, "f32_refine": 1}[precision]
+    o.precision = {"f64": 0, "f32_refine": 1, "f32_reliable": 2}[precision]
     o.inner_tol, o.max_outer = float(inner_tol), int(max_outer)
     o.use_graph, o.check_every = int(bool(use_graph)), int(check_every)
     return o
@@ -214,7 +214,12 @@ def cg_workspace_bytes(plan, n_global, precision="f32_refine", **kw):
 
 def cg_solve(plan, lam, l2g, n_global, f, x0=None, tol=1e-10, maxit=10000, precision="f32_refine",
              inner_tol=1e-5, max_outer=20, use_graph=True, check_every=25, workspace=None, raise_on_fail=True):
-    """Jacobi-PCG on the assembled operator; returns (x, result dict)."""
+    """Jacobi-PCG on the assembled operator; returns (x, result dict).
+
+    precision: "f64" (all-FP64 PCG), "f32_refine" (FP32 PCG restarted inside
+    FP64 iterative refinement) or "f32_reliable" (one FP32 PCG run whose
+    residual is replaced by the FP64 one each time it fell by inner_tol).
+    """
     _dev(l2g, "l2g")
     _dev(f, "f")
     o = _cg_opts(tol, maxit, precision, inner_tol, max_outer, use_graph, check_every)

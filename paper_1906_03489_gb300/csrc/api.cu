@@ -93,6 +93,18 @@ spx_status launch_op(const LaunchReq& r) {
   }
 }
 
+// Helmholtz apply for the solver (spx_internal.h).
+spx_status helmholtz_unless(const spx_plan* cp, int dtype, double lambda, const void* in, void* out, const int* skip,
+                            cudaStream_t stream) {
+  spx_plan* p = const_cast<spx_plan*>(cp);
+  if (p->E == 0) return SPX_OK;
+  const void* geom = p->geom[dtype];
+  if (!geom) return fail(SPX_ERR_INVALID_ARG, "geometry not registered for this dtype");
+  spx_status s = ensure_tiles(p, OP_HELM, dtype);
+  if (s != SPX_OK) return s;
+  LaunchReq r{p, OP_HELM, dtype, in, nullptr, geom, nullptr, nullptr, out, nullptr, nullptr, lambda, stream, skip};
+  return launch_op(r);
+}
 }  // namespace spx
 
 using namespace spx;

@@ -12,10 +12,17 @@
 //    -> update (+ <r,z>, <r,r>) -> direction update; dot products accumulate
 //    in FP64 in fixed order (per-block partials summed by the last block), so
 //    results are bitwise reproducible;
-//  * iterations are captured once in a CUDA graph of `check_every` iterations
-//    and replayed until the device-side convergence flag is set;
+//  * iterations are captured once per solve in a CUDA graph of `check_every`
+//    iterations and replayed until the device-side `done` flag is set (the
+//    Helmholtz launches of iterations past that point return at once);
 //  * precision 1: FP32 PCG on the correction equation inside FP64 iterative
-//    refinement (outer residual, its norm and x += d in FP64).
+//    refinement (outer residual, its norm and x += d in FP64), restarted from
+//    the new residual after every refinement step;
+//  * precision 2: the same FP32 PCG with reliable updates: after each
+//    refinement step its recurrence residual is replaced by the new FP64
+//    residual and the run continues along its current search direction
+//    instead of restarting (residual replacement, Sleijpen & van der Vorst
+//    1996; its mixed-precision use by Clark et al. 2010).
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -30,7 +37,7 @@ namespace {
 constexpr int kRedThreads = 256;
 
 struct Scalars {
-  double rz, rz_new, pAp, alpha, beta, rr, ff, tol2, scale;
+  double rz, rz_new, rz_prev, pAp, alpha, beta, rr, ff, tol2, scale;
   int it, done, maxit, nonfinite;
   unsigned int ticket;
 };
@@ -96,11 +103,6 @@ __device__ bool grid_reduce2(double a, double b, double* partials, unsigned int*
   *tb = y;
   return true;
 }
-
-// Element-wise loops over the global vectors: each thread takes kUnroll
-// independent indices per trip (g, g + S, ...; S = all threads), loads first,
-// so that several loads are in flight per thread.
-constexpr int kUnroll = 4;
 
 // ---- CSR transpose of l2g ------------------------------------------------
 __global__ void csr_count(const int32_t* l2g, int64_t nl, int32_t* cnt) {
@@ -172,6 +174,57 @@ __global__ void csr_sort(const int32_t* row_ptr, int32_t* cols, int64_t ng) {
 }
 
 // ---- assembly and vector kernels ----------------------------------------
+// Global vectors are processed in packs of V = 16 / sizeof(T) consecutive
+// values (one 16-byte access per vector and pack) when every pointer of the
+// launch is 16-byte aligned, else one value at a time (V = 1).  The values
+// past the last whole pack are handled one by one after the pack loop.
+template <typename T, int V>
+struct Pack {
+  T v[V];
+};
+
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> ldp(const T* __restrict__ a, int64_t i) {
+  Pack<T, V> r;
+  if constexpr (V == 1) {
+    r.v[0] = a[i];
+  } else if constexpr (sizeof(T) == 4) {
+    static_assert(V == 4, "FP32 packs hold 4 values");
+    const float4 x = reinterpret_cast<const float4*>(a)[i];
+    r.v[0] = x.x; r.v[1] = x.y; r.v[2] = x.z; r.v[3] = x.w;
+  } else {
+    static_assert(V == 2, "FP64 packs hold 2 values");
+    const double2 x = reinterpret_cast<const double2*>(a)[i];
+    r.v[0] = x.x; r.v[1] = x.y;
+  }
+  return r;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stp(T* __restrict__ a, int64_t i, const Pack<T, V>& r) {
+  if constexpr (V == 1) {
+    a[i] = r.v[0];
+  } else if constexpr (sizeof(T) == 4) {
+    reinterpret_cast<float4*>(a)[i] = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else {
+    reinterpret_cast<double2*>(a)[i] = make_double2(r.v[0], r.v[1]);
+  }
+}
+
+// V consecutive int32 from a V-aligned position (V * 4 bytes).
+template <int V>
+__device__ __forceinline__ void ldi(const int32_t* __restrict__ a, int64_t i, int32_t* out) {
+  if constexpr (V == 4) {
+    const int4 x = reinterpret_cast<const int4*>(a)[i];
+    out[0] = x.x; out[1] = x.y; out[2] = x.z; out[3] = x.w;
+  } else if constexpr (V == 2) {
+    const int2 x = reinterpret_cast<const int2*>(a)[i];
+    out[0] = x.x; out[1] = x.y;
+  } else {
+    out[0] = a[i];
+  }
+}
+
 template <typename T>
 __global__ void assemble_plain(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
                                const T* __restrict__ yl, T* __restrict__ yg, int64_t ng) {
@@ -182,55 +235,76 @@ __global__ void assemble_plain(const int32_t* __restrict__ row_ptr, const int32_
   }
 }
 
-template <typename T>
+// loc = g[l2g] (skipped once the solve is done)
+template <typename T, int V>
 __global__ void gather_if(const int32_t* __restrict__ l2g, const T* __restrict__ g, T* __restrict__ loc, int64_t n,
                           const Scalars* sc) {
   if (sc->done) return;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    loc[i] = g[l2g[i]];
+  const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t np = n / V;
+  for (int64_t i = t0; i < np; i += S) {
+    int32_t k[V];
+    ldi<V>(l2g, i, k);
+    Pack<T, V> v;
+#pragma unroll
+    for (int u = 0; u < V; ++u) v.v[u] = g[k[u]];
+    stp<T, V>(loc, i, v);
+  }
+  for (int64_t i = np * V + t0; i < n; i += S) loc[i] = g[l2g[i]];
 }
 
-// q = assemble(ql); pAp = <p, q>; alpha = rz / pAp.  The local copies of
-// kUnroll global indices are gathered in lockstep (each sum in CSR order).
-template <typename T>
+// q = assemble(ql); pAp = <p, q>; alpha = rz / pAp.  A thread sums the rows
+// of kRowsA consecutive global indices in lockstep (each row in CSR order).
+constexpr int kRowsA = 8;
+template <typename T, int V>
 __global__ void __launch_bounds__(kRedThreads) assemble_dot(const int32_t* __restrict__ row_ptr,
                                                             const int32_t* __restrict__ cols,
                                                             const T* __restrict__ ql, T* __restrict__ q,
                                                             const T* __restrict__ p, int64_t ng, Scalars* sc,
                                                             double* partials) {
   if (sc->done) return;
+  constexpr int NP = kRowsA / V;   // packs per trip
   double acc = 0.0;
-  const int64_t S = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g0 < ng; g0 += kUnroll * S) {
-    int32_t k0[kUnroll], k1[kUnroll];
-    T pv[kUnroll], sv[kUnroll];
+  const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t nt = ng / kRowsA;  // whole trips
+  for (int64_t it = t0; it < nt; it += S) {
+    const int64_t g0 = it * kRowsA;
+    int32_t k0[kRowsA], k1[kRowsA];
+#pragma unroll
+    for (int u = 0; u < kRowsA; ++u) k0[u] = row_ptr[g0 + u];
+#pragma unroll
+    for (int u = 0; u < kRowsA - 1; ++u) k1[u] = k0[u + 1];
+    k1[kRowsA - 1] = row_ptr[g0 + kRowsA];
+    Pack<T, V> pv[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) pv[j] = ldp<T, V>(p, it * NP + j);
     int len = 0;
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t g = g0 + u * S;
-      k0[u] = k1[u] = 0;
-      pv[u] = T(0);
-      sv[u] = T(0);
-      if (g < ng) {
-        k0[u] = row_ptr[g];
-        k1[u] = row_ptr[g + 1];
-        pv[u] = p[g];
-      }
-      len = max(len, k1[u] - k0[u]);
-    }
+    for (int u = 0; u < kRowsA; ++u) len = max(len, k1[u] - k0[u]);
+    T sv[kRowsA];
+#pragma unroll
+    for (int u = 0; u < kRowsA; ++u) sv[u] = T(0);
     for (int j = 0; j < len; ++j) {
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u)
+      for (int u = 0; u < kRowsA; ++u)
         if (k0[u] + j < k1[u]) sv[u] += ql[cols[k0[u] + j]];
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t g = g0 + u * S;
-      if (g < ng) {
-        q[g] = sv[u];
-        acc += static_cast<double>(pv[u]) * static_cast<double>(sv[u]);
+    for (int j = 0; j < NP; ++j) {
+      Pack<T, V> qv;
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        qv.v[u] = sv[j * V + u];
+        acc += static_cast<double>(pv[j].v[u]) * static_cast<double>(qv.v[u]);
       }
+      stp<T, V>(q, it * NP + j, qv);
     }
+  }
+  for (int64_t g = nt * kRowsA + t0; g < ng; g += S) {
+    T s = T(0);
+    for (int32_t k = row_ptr[g]; k < row_ptr[g + 1]; ++k) s += ql[cols[k]];
+    q[g] = s;
+    acc += static_cast<double>(p[g]) * static_cast<double>(s);
   }
   double pAp, unused;
   if (grid_reduce2(acc, 0.0, partials, &sc->ticket, &pAp, &unused)) {
@@ -240,47 +314,67 @@ __global__ void __launch_bounds__(kRedThreads) assemble_dot(const int32_t* __res
   }
 }
 
-// x += alpha p; r -= alpha q; z = minv r; rz_new = <r,z>; rr = <r,r>
-template <typename T>
+// x += alpha p; r -= alpha q; z = minv r; rz_new = <r,z>; rr = <r,r>.
+// Ends the run (done) on convergence of the recurrence residual
+// (rr <= tol2 ff), the iteration cap or a non-finite value.
+template <typename T, int V>
 __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
                                                          const T* __restrict__ p, const T* __restrict__ q,
                                                          const T* __restrict__ minv, int64_t ng, Scalars* sc,
                                                          double* partials) {
   if (sc->done) return;
+  constexpr int U = V == 1 ? 4 : 1;   // packs per trip (loads in flight per thread)
   const T alpha = static_cast<T>(sc->alpha);
   double arz = 0.0, arr = 0.0;
-  const int64_t S = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g0 < ng; g0 += kUnroll * S) {
-    T xv[kUnroll], rv[kUnroll], pv[kUnroll], qv[kUnroll], mv[kUnroll];
+  const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t np = ng / V;
+  for (int64_t i0 = t0; i0 < np; i0 += U * S) {
+    Pack<T, V> xv[U], rv[U], pv[U], qv[U], mv[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t g = g0 + u * S;
-      if (g < ng) {
-        xv[u] = x[g];
-        rv[u] = r[g];
-        pv[u] = p[g];
-        qv[u] = q[g];
-        mv[u] = minv[g];
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * S;
+      if (i < np) {
+        xv[u] = ldp<T, V>(x, i);
+        rv[u] = ldp<T, V>(r, i);
+        pv[u] = ldp<T, V>(p, i);
+        qv[u] = ldp<T, V>(q, i);
+        mv[u] = ldp<T, V>(minv, i);
       }
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t g = g0 + u * S;
-      if (g < ng) {
-        x[g] = xv[u] + alpha * pv[u];
-        const T rn = rv[u] - alpha * qv[u];
-        r[g] = rn;
-        const T zv = mv[u] * rn;
-        z[g] = zv;
-        arz += static_cast<double>(rn) * static_cast<double>(zv);
-        arr += static_cast<double>(rn) * static_cast<double>(rn);
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * S;
+      if (i < np) {
+        Pack<T, V> zv;
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+          xv[u].v[c] = xv[u].v[c] + alpha * pv[u].v[c];
+          const T rn = rv[u].v[c] - alpha * qv[u].v[c];
+          rv[u].v[c] = rn;
+          zv.v[c] = mv[u].v[c] * rn;
+          arz += static_cast<double>(rn) * static_cast<double>(zv.v[c]);
+          arr += static_cast<double>(rn) * static_cast<double>(rn);
+        }
+        stp<T, V>(x, i, xv[u]);
+        stp<T, V>(r, i, rv[u]);
+        stp<T, V>(z, i, zv);
       }
     }
+  }
+  for (int64_t g = np * V + t0; g < ng; g += S) {
+    x[g] = x[g] + alpha * p[g];
+    const T rn = r[g] - alpha * q[g];
+    r[g] = rn;
+    const T zv = minv[g] * rn;
+    z[g] = zv;
+    arz += static_cast<double>(rn) * static_cast<double>(zv);
+    arr += static_cast<double>(rn) * static_cast<double>(rn);
   }
   double rz, rr;
   if (grid_reduce2(arz, arr, partials, &sc->ticket, &rz, &rr)) {
     sc->rz_new = rz;
     sc->beta = rz / sc->rz;
+    sc->rz_prev = sc->rz;
     sc->rz = rz;
     sc->rr = rr;
     sc->it += 1;
@@ -294,25 +388,46 @@ __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* _
   }
 }
 
-template <typename T>
+// p = z + beta p
+template <typename T, int V>
 __global__ void cg_direction(T* __restrict__ p, const T* __restrict__ z, int64_t ng, const Scalars* sc) {
   if (sc->done) return;
   const T beta = static_cast<T>(sc->beta);
-  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x)
-    p[g] = z[g] + beta * p[g];
+  const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t np = ng / V;
+  for (int64_t i = t0; i < np; i += S) {
+    Pack<T, V> pv = ldp<T, V>(p, i);
+    const Pack<T, V> zv = ldp<T, V>(z, i);
+#pragma unroll
+    for (int c = 0; c < V; ++c) pv.v[c] = zv.v[c] + beta * pv.v[c];
+    stp<T, V>(p, i, pv);
+  }
+  for (int64_t g = np * V + t0; g < ng; g += S) p[g] = z[g] + beta * p[g];
 }
 
 // Start of a PCG run from residual r (x not touched): z = minv r; p = z;
-// rz = <r,z>; ff = <b,b> (with b the right-hand side, given in r when
-// `rhs_norm_from_r`), it = 0, done unless there is work.
-template <typename T>
+// rz = <r,z>; it = 0; done unless there is work (rr > tol2 ff, maxit > 0).
+template <typename T, int V>
 __global__ void __launch_bounds__(kRedThreads) cg_start(const T* __restrict__ r, T* __restrict__ z,
                                                         T* __restrict__ p, const T* __restrict__ minv, int64_t ng,
                                                         Scalars* sc, double* partials) {
   double arz = 0.0, arr = 0.0;
-  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
-    const T rv = r[g];
-    const T zv = minv[g] * rv;
+  const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t np = ng / V;
+  for (int64_t i = t0; i < np; i += S) {
+    const Pack<T, V> rv = ldp<T, V>(r, i), mv = ldp<T, V>(minv, i);
+    Pack<T, V> zv;
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+      zv.v[c] = mv.v[c] * rv.v[c];
+      arz += static_cast<double>(rv.v[c]) * static_cast<double>(zv.v[c]);
+      arr += static_cast<double>(rv.v[c]) * static_cast<double>(rv.v[c]);
+    }
+    stp<T, V>(z, i, zv);
+    stp<T, V>(p, i, zv);
+  }
+  for (int64_t g = np * V + t0; g < ng; g += S) {
+    const T rv = r[g], zv = minv[g] * rv;
     z[g] = zv;
     p[g] = zv;
     arz += static_cast<double>(rv) * static_cast<double>(zv);
@@ -358,7 +473,43 @@ __global__ void to_f32_scaled(const double* __restrict__ r, float* __restrict__ 
   }
 }
 
-// x += ||r|| d32
+// Residual replacement of a reliable update (precision 2).  The FP32 run
+// stopped after the update of iteration i (its direction update not done);
+// the FP64 residual r64 of the corrected x replaces the recurrence residual,
+// rescaled so that ||r32|| = 1: r32 = r64 / s_new, d32 = 0, z32 = minv r32,
+// rz = <r32, z32>.  Rescaling multiplies every vector of the old scaled system
+// by c = s_old / s_new, so the direction update that follows,
+// p = z32 + beta' p, takes beta' = c * rz / (c^2 rz_prev) (rz_prev = <r_i, z_i>
+// of the old scaling).  The run then continues with tol2 / ff / maxit as set
+// by the host beforehand.
+__global__ void __launch_bounds__(kRedThreads) reliable_restart(const double* __restrict__ r64,
+                                                                float* __restrict__ r32, float* __restrict__ d32,
+                                                                float* __restrict__ z32,
+                                                                const float* __restrict__ minv, int64_t ng,
+                                                                double inv_s_new, double c, Scalars* sc,
+                                                                double* partials) {
+  double arz = 0.0, arr = 0.0;
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    const float rv = static_cast<float>(r64[g] * inv_s_new);
+    const float zv = minv[g] * rv;
+    r32[g] = rv;
+    d32[g] = 0.f;
+    z32[g] = zv;
+    arz += static_cast<double>(rv) * static_cast<double>(zv);
+    arr += static_cast<double>(rv) * static_cast<double>(rv);
+  }
+  double rz, rr;
+  if (grid_reduce2(arz, arr, partials, &sc->ticket, &rz, &rr)) {
+    sc->beta = rz / (c * sc->rz_prev);
+    sc->rz = rz;
+    sc->rr = rr;
+    sc->nonfinite = (!isfinite(rr) || !isfinite(rz) || !isfinite(sc->beta)) ? 1 : 0;
+    sc->done = (sc->nonfinite || sc->it >= sc->maxit) ? 1 : 0;
+    sc->ticket = 0;
+  }
+}
+
+// x += scale d32
 __global__ void add_correction(double* __restrict__ x, const float* __restrict__ d32, int64_t ng, double scale) {
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x)
     x[g] += scale * static_cast<double>(d32[g]);
@@ -375,7 +526,6 @@ __global__ void fill_zero(T* v, int64_t n) {
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < n; g += int64_t(gridDim.x) * blockDim.x)
     v[g] = T(0);
 }
-
 // ---------------------------------------------------------------------------
 struct Workspace {
   int32_t *row_ptr, *cols, *cursor, *totals, *grand;
@@ -468,87 +618,112 @@ spx_status build_csr(Solver& s) {
   return SPX_OK;
 }
 
+bool a16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 // y_global = A x_global in precision T (using pl / ql local buffers)
 template <typename T>
 spx_status apply_A(Solver& s, int dt, const T* xg, T* pl, T* ql, T* yg) {
   spx_status st = spx_gather(s.plan, static_cast<spx_dtype>(dt), s.l2g, s.ng, xg, pl, s.st);
   if (st != SPX_OK) return st;
-  st = spx_helmholtz(s.plan, static_cast<spx_dtype>(dt), s.lam, nullptr, nullptr, pl, ql, s.st);
+  st = helmholtz_unless(s.plan, dt, s.lam, pl, ql, nullptr, s.st);
   if (st != SPX_OK) return st;
   assemble_plain<T><<<s.grid_v, 256, 0, s.st>>>(s.w.row_ptr, s.w.cols, ql, yg, s.ng);
   SPX_CK(cudaGetLastError());
   return SPX_OK;
 }
 
+// The vectors and launches of one PCG run in precision T: x += alpha p,
+// r -= alpha A p, z = minv r, p = z + beta p.  One iteration is gather ->
+// Helmholtz (skipped once the run is done) -> assembly + <p, Ap> -> update +
+// <r, z>, <r, r> -> direction.  With use_graph, `check_every` iterations are
+// captured once in a CUDA graph that every chunk of the run replays (the
+// buffers never change); else they are launched eagerly.
 template <typename T>
-spx_status enqueue_iteration(Solver& s, int dt, T* x, T* r, T* z, T* p, T* q, const T* minv, T* pl, T* ql) {
-  Workspace& w = s.w;
-  gather_if<T><<<s.grid_v, 256, 0, s.st>>>(s.l2g, p, pl, s.nl, w.sc);
-  spx_status st = spx_helmholtz(s.plan, static_cast<spx_dtype>(dt), s.lam, nullptr, nullptr, pl, ql, s.st);
-  if (st != SPX_OK) return st;
-  assemble_dot<T><<<s.nred, kRedThreads, 0, s.st>>>(w.row_ptr, w.cols, ql, q, p, s.ng, w.sc, w.partials);
-  cg_update<T><<<s.nred, kRedThreads, 0, s.st>>>(x, r, z, p, q, minv, s.ng, w.sc, w.partials);
-  cg_direction<T><<<s.grid_v, 256, 0, s.st>>>(p, z, s.ng, w.sc);
-  SPX_CK(cudaGetLastError());
-  return SPX_OK;
-}
-
-// PCG on A x = b given the residual r of the initial x (scalars ff / tol2 /
-// maxit set by the caller).  Returns iterations done in *iters.
-template <typename T>
-spx_status pcg(Solver& s, int dt, T* x, T* r, T* z, T* p, T* q, const T* minv, T* pl, T* ql, bool use_graph,
-               int check_every, int* iters, bool* converged, bool* nonfinite) {
-  Workspace& w = s.w;
-  cg_start<T><<<s.nred, kRedThreads, 0, s.st>>>(r, z, p, minv, s.ng, w.sc, w.partials);
-  SPX_CK(cudaGetLastError());
-  // one eager apply first, so that every launch attribute of the operator
-  // kernel is set before any stream capture
-  {
-    spx_status st0 = spx_helmholtz(s.plan, static_cast<spx_dtype>(dt), s.lam, nullptr, nullptr, pl, ql, s.st);
-    if (st0 != SPX_OK) return st0;
-  }
+struct PcgRun {
+  static constexpr int V = 16 / sizeof(T);
+  Solver* s;
+  int dt;
+  T *x, *r, *z, *p, *q;
+  const T* minv;
+  T *pl, *ql;
+  int check_every = 1;
   cudaGraphExec_t exec = nullptr;
-  if (use_graph) {
+
+  ~PcgRun() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+
+  spx_status enqueue_iteration() {
+    Workspace& w = s->w;
+    cudaStream_t st = s->st;
+    if (a16(s->l2g) && a16(p) && a16(pl)) gather_if<T, V><<<s->grid_v, 256, 0, st>>>(s->l2g, p, pl, s->nl, w.sc);
+    else gather_if<T, 1><<<s->grid_v, 256, 0, st>>>(s->l2g, p, pl, s->nl, w.sc);
+    spx_status e = helmholtz_unless(s->plan, dt, s->lam, pl, ql, &w.sc->done, st);
+    if (e != SPX_OK) return e;
+    if (a16(q) && a16(p))
+      assemble_dot<T, V><<<s->nred, kRedThreads, 0, st>>>(w.row_ptr, w.cols, ql, q, p, s->ng, w.sc, w.partials);
+    else
+      assemble_dot<T, 1><<<s->nred, kRedThreads, 0, st>>>(w.row_ptr, w.cols, ql, q, p, s->ng, w.sc, w.partials);
+    if (a16(x) && a16(r) && a16(z) && a16(p) && a16(q) && a16(minv))
+      cg_update<T, V><<<s->nred, kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc, w.partials);
+    else
+      cg_update<T, 1><<<s->nred, kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc, w.partials);
+    direction();
+    SPX_CK(cudaGetLastError());
+    return SPX_OK;
+  }
+
+  void direction() {
+    if (a16(p) && a16(z)) cg_direction<T, V><<<s->grid_v, 256, 0, s->st>>>(p, z, s->ng, s->w.sc);
+    else cg_direction<T, 1><<<s->grid_v, 256, 0, s->st>>>(p, z, s->ng, s->w.sc);
+  }
+
+  // z = minv r; p = z; rz (scalars ff / tol2 / maxit set by the caller)
+  spx_status start() {
+    Workspace& w = s->w;
+    if (a16(r) && a16(z) && a16(p) && a16(minv))
+      cg_start<T, V><<<s->nred, kRedThreads, 0, s->st>>>(r, z, p, minv, s->ng, w.sc, w.partials);
+    else
+      cg_start<T, 1><<<s->nred, kRedThreads, 0, s->st>>>(r, z, p, minv, s->ng, w.sc, w.partials);
+    SPX_CK(cudaGetLastError());
+    return SPX_OK;
+  }
+
+  spx_status prepare(bool use_graph, int every) {
+    check_every = every;
+    // one eager apply first, so that every launch attribute of the operator
+    // kernel is set before any stream capture
+    spx_status e = helmholtz_unless(s->plan, dt, s->lam, pl, ql, nullptr, s->st);
+    if (e != SPX_OK || !use_graph) return e;
     cudaGraph_t graph;
-    SPX_CK(cudaStreamBeginCapture(s.st, cudaStreamCaptureModeThreadLocal));
-    spx_status st = SPX_OK;
-    for (int k = 0; k < check_every && st == SPX_OK; ++k) st = enqueue_iteration<T>(s, dt, x, r, z, p, q, minv, pl, ql);
-    cudaError_t ce = cudaStreamEndCapture(s.st, &graph);
-    if (st != SPX_OK) return st;
+    SPX_CK(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < check_every && e == SPX_OK; ++k) e = enqueue_iteration();
+    cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+    if (e != SPX_OK) return e;
     SPX_CK(ce);
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     SPX_CK(ce);
+    return SPX_OK;
   }
-  Scalars h{};
-  spx_status st = SPX_OK;
-  for (;;) {
-    if (use_graph) {
-      cudaError_t ce = cudaGraphLaunch(exec, s.st);
-      if (ce != cudaSuccess) {
-        st = cuda_fail(ce, "cudaGraphLaunch");
-        break;
+
+  // Iterates until the device sets `done`; the final scalars land in *h.
+  spx_status run(Scalars* h) {
+    for (;;) {
+      if (exec) {
+        SPX_CK(cudaGraphLaunch(exec, s->st));
+      } else {
+        for (int k = 0; k < check_every; ++k) {
+          spx_status e = enqueue_iteration();
+          if (e != SPX_OK) return e;
+        }
       }
-    } else {
-      for (int k = 0; k < check_every && st == SPX_OK; ++k)
-        st = enqueue_iteration<T>(s, dt, x, r, z, p, q, minv, pl, ql);
-      if (st != SPX_OK) break;
+      SPX_CK(cudaMemcpyAsync(h, s->w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s->st));
+      SPX_CK(cudaStreamSynchronize(s->st));
+      if (h->done) return SPX_OK;
     }
-    cudaError_t ce = cudaMemcpyAsync(&h, w.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s.st);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s.st);
-    if (ce != cudaSuccess) {
-      st = cuda_fail(ce, "cg scalars");
-      break;
-    }
-    if (h.done) break;
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (st != SPX_OK) return st;
-  *iters = h.it;
-  *nonfinite = h.nonfinite != 0;
-  *converged = !h.nonfinite && h.rr <= h.tol2 * h.ff;
-  return SPX_OK;
-}
+};
 
 spx_status set_scalars(Solver& s, double ff, double tol, int maxit) {
   Scalars h{};
@@ -589,7 +764,7 @@ using namespace spx;
 extern "C" spx_status spx_cg_workspace_bytes(const spx_plan* plan, int64_t n_global, const spx_cg_opts* o,
                                              size_t* bytes) {
   if (!plan || !o || !bytes || n_global < 0) return fail(SPX_ERR_INVALID_ARG, "cg_workspace_bytes: bad argument");
-  if (o->precision != 0 && o->precision != 1) return fail(SPX_ERR_INVALID_ARG, "cg: precision must be 0 or 1");
+  if (o->precision < 0 || o->precision > 2) return fail(SPX_ERR_INVALID_ARG, "cg: precision must be 0, 1 or 2");
   const int nred = plan->num_sms * 8;
   *bytes = carve(nullptr, n_global, plan->n_coef, nred, o->precision).bytes;
   return SPX_OK;
@@ -612,12 +787,12 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
     return fail(SPX_ERR_INVALID_ARG, "cg_solve: sizes exceed the int32 index range");
   if (n_global == 0) return SPX_OK;
   if (!l2g || !f || !x || !workspace) return fail(SPX_ERR_INVALID_ARG, "cg_solve: NULL buffer");
-  if (o->precision != 0 && o->precision != 1) return fail(SPX_ERR_INVALID_ARG, "cg_solve: precision must be 0 or 1");
+  if (o->precision < 0 || o->precision > 2) return fail(SPX_ERR_INVALID_ARG, "cg_solve: precision must be 0, 1 or 2");
   if (!(o->tol > 0) || o->maxit < 1 || o->check_every < 1)
     return fail(SPX_ERR_INVALID_ARG, "cg_solve: tol > 0, maxit >= 1, check_every >= 1 required");
-  if (o->precision == 1 && (!(o->inner_tol > 0) || o->max_outer < 1))
+  if (o->precision >= 1 && (!(o->inner_tol > 0) || o->max_outer < 1))
     return fail(SPX_ERR_INVALID_ARG, "cg_solve: inner_tol > 0 and max_outer >= 1 required");
-  if (!plan->geom[SPX_F64] || (o->precision == 1 && !plan->geom[SPX_F32]))
+  if (!plan->geom[SPX_F64] || (o->precision >= 1 && !plan->geom[SPX_F32]))
     return fail(SPX_ERR_INVALID_ARG, "cg_solve: geometry not registered for the precision(s) used");
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(SPX_ERR_INVALID_ARG, "cg_solve: workspace not 256-byte aligned");
   Solver s{};
@@ -643,7 +818,7 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
     SPX_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   } else {
     if (plan->tiles[OP_HELM][SPX_F64].dirty || plan->tiles[OP_DIAG][SPX_F64].dirty ||
-        (o->precision == 1 && plan->tiles[OP_HELM][SPX_F32].dirty))
+        (o->precision >= 1 && plan->tiles[OP_HELM][SPX_F32].dirty))
       return fail(SPX_ERR_INVALID_ARG,
                   "cg_solve_noalloc: the plan's Helmholtz / diagonal launch tiles are not built yet (run "
                   "spx_helmholtz in each precision used and spx_helmholtz_diag in FP64 once on this plan, or "
@@ -674,7 +849,7 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
   if ((st = spx_helmholtz_diag(plan, SPX_F64, lambda, w.diag64, s.st)) != SPX_OK) return finish(st);
   assemble_plain<double><<<s.grid_v, 256, 0, s.st>>>(w.row_ptr, w.cols, w.diag64, w.r64, s.ng);
   invert_diag<double><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv64, s.ng);
-  if (o->precision == 1) invert_diag<float><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv32, s.ng);
+  if (o->precision >= 1) invert_diag<float><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv32, s.ng);
   if (cudaGetLastError() != cudaSuccess) return finish(fail(SPX_ERR_CUDA, "cg setup kernels"));
 
   double rr, ff;
@@ -687,39 +862,62 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
   int total_it = 0;
   if (o->precision == 0) {
     // all-FP64 PCG; restart from the true residual if the recurrence drifted
+    PcgRun<double> run{&s, SPX_F64, x, w.r64, w.z64, w.p64, w.q64, w.minv64, w.pl64, w.ql64};
+    if ((st = run.prepare(use_graph, o->check_every)) != SPX_OK) return finish(st);
     for (int restart = 0; restart < 4; ++restart) {
       if (!std::isfinite(rr)) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite residual"));
       if (std::sqrt(rr / ff) <= tol) break;
       if ((st = set_scalars(s, ff, tol, o->maxit - total_it)) != SPX_OK) return finish(st);
-      int it = 0;
-      bool conv, nonfin;
-      st = pcg<double>(s, SPX_F64, x, w.r64, w.z64, w.p64, w.q64, w.minv64, w.pl64, w.ql64, use_graph,
-                       o->check_every, &it, &conv, &nonfin);
-      if (st != SPX_OK) return finish(st);
-      total_it += it;
-      if (nonfin) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite residual"));
+      Scalars h{};
+      if ((st = run.start()) != SPX_OK || (st = run.run(&h)) != SPX_OK) return finish(st);
+      total_it += h.it;
+      if (h.nonfinite) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite residual"));
       if ((st = residual(s, f, x, &rr, &ff)) != SPX_OK) return finish(st);
       if (total_it >= o->maxit) break;
     }
     res->iters = total_it;
     res->rel_residual = std::sqrt(rr / ff);
   } else {
+    // FP32 PCG on the scaled correction equation A d = r / ||r|| (from d = 0),
+    // x += ||r|| d and the FP64 residual r = f - A x after every FP32 run.
+    // precision 1 restarts the FP32 PCG from the new residual (p = z);
+    // precision 2 replaces the FP32 recurrence residual by the new one and
+    // continues the same run (reliable update, reliable_restart).  An FP32
+    // run stops once its residual fell by inner_tol, or by half of what the
+    // outer tolerance still asks if that is less.
+    PcgRun<float> run{&s, SPX_F32, w.d32, w.r32, w.z32, w.p32, w.q32, w.minv32, w.pl32, w.ql32};
+    if ((st = run.prepare(use_graph, o->check_every)) != SPX_OK) return finish(st);
     int outer = 0;
+    double s_old = 0.0;
     for (; outer < o->max_outer; ++outer) {
       if (!std::isfinite(rr)) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite residual"));
-      if (std::sqrt(rr / ff) <= tol) break;
-      // inner FP32 PCG on A d = r / ||r||, from d = 0
-      to_f32_scaled<<<s.grid_v, 256, 0, s.st>>>(w.r64, w.r32, w.d32, s.ng, w.sc);
-      // right-hand side norm of the scaled system is 1
-      if ((st = set_scalars(s, 1.0, o->inner_tol, o->maxit)) != SPX_OK) return finish(st);
-      int it = 0;
-      bool conv, nonfin;
-      st = pcg<float>(s, SPX_F32, w.d32, w.r32, w.z32, w.p32, w.q32, w.minv32, w.pl32, w.ql32, use_graph,
-                      o->check_every, &it, &conv, &nonfin);
-      if (st != SPX_OK) return finish(st);
-      total_it += it;
-      if (nonfin) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite inner residual"));
-      add_correction<<<s.grid_v, 256, 0, s.st>>>(x, w.d32, s.ng, std::sqrt(rr));
+      const double rel = std::sqrt(rr / ff);
+      if (rel <= tol) break;
+      if (o->precision == 2 && total_it >= o->maxit) break;
+      const double s_new = std::sqrt(rr);
+      const double itol = std::max(o->inner_tol, 0.5 * tol / rel);
+      Scalars h{};
+      if (o->precision == 1 || outer == 0) {
+        to_f32_scaled<<<s.grid_v, 256, 0, s.st>>>(w.r64, w.r32, w.d32, s.ng, w.sc);
+        // right-hand side norm of the scaled system is 1
+        if ((st = set_scalars(s, 1.0, itol, o->maxit)) != SPX_OK) return finish(st);
+        if ((st = run.start()) != SPX_OK) return finish(st);
+      } else {
+        if ((st = read_scalars(s, &h)) != SPX_OK) return finish(st);
+        h.ff = 1.0;
+        h.tol2 = itol * itol;
+        h.ticket = 0;
+        SPX_CK(cudaMemcpyAsync(w.sc, &h, sizeof(Scalars), cudaMemcpyHostToDevice, s.st));
+        reliable_restart<<<s.nred, kRedThreads, 0, s.st>>>(w.r64, w.r32, w.d32, w.z32, w.minv32, s.ng, 1.0 / s_new,
+                                                           s_old / s_new, w.sc, w.partials);
+        run.direction();
+        SPX_CK(cudaGetLastError());
+      }
+      s_old = s_new;
+      if ((st = run.run(&h)) != SPX_OK) return finish(st);
+      total_it = o->precision == 1 ? total_it + h.it : h.it;
+      if (h.nonfinite) return finish(fail(SPX_ERR_NONFINITE, "cg_solve: non-finite inner residual"));
+      add_correction<<<s.grid_v, 256, 0, s.st>>>(x, w.d32, s.ng, s_new);
       if ((st = residual(s, f, x, &rr, &ff)) != SPX_OK) return finish(st);
     }
     res->iters = total_it;

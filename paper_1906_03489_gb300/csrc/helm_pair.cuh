@@ -432,6 +432,7 @@ __global__ void __maxnreg__(REG) helm_pair_kernel(const __grid_constant__ PairPa
   const auto& p = pp.k;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
   const int tid = threadIdx.x, nthr = blockDim.x;
+  if (p.skip && *p.skip) return;   // uniform across the grid: nothing started yet
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
@@ -600,6 +601,7 @@ __global__ void __maxnreg__(REG) helm_varp_kernel(const __grid_constant__ PairPa
   const int tid = threadIdx.x;
   const int nc = blockDim.x - 32;                          // compute threads
   const int G = gridDim.x;
+  if (p.skip && *p.skip) return;   // uniform across the grid: nothing started yet
   if (tid == 0) {
     mbar_init(bar, 1);
     mbar_init(&mbar[0], 1);

@@ -139,6 +139,7 @@ struct KParams {
   T* out1;
   T* out2;
   int* status;
+  const int* skip;          // non-null and nonzero at launch time: the launch does nothing
   double lam;
   int n_tiles;
   int stages;

@@ -84,6 +84,7 @@ spx_status launch_pair(const LaunchReq& r) {
   p.kap_f = static_cast<const float*>(r.kap_f);
   p.out0 = static_cast<float*>(r.out0);
   p.status = plan->d_status;
+  p.skip = r.skip;
   p.lam = r.lam;
   p.n_tiles = tl.n;
   const int thr = pair_threshold(plan);
@@ -133,6 +134,7 @@ spx_status launch_impl(const LaunchReq& r) {
   p.out1 = static_cast<T*>(r.out1);
   p.out2 = static_cast<T*>(r.out2);
   p.status = plan->d_status;
+  p.skip = r.skip;
   p.lam = r.lam;
   p.n_tiles = tl.n;
   p.stages = cfg.stages;

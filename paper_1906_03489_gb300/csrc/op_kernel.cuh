@@ -879,6 +879,7 @@ __global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KPar
   int* tab_order = reinterpret_cast<int*>(gquad + kMaxEB);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int S = p.stages;
+  if (p.skip && *p.skip) return;   // uniform across the grid: nothing started yet
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();

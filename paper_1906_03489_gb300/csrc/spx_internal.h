@@ -79,6 +79,7 @@ struct LaunchReq {
   void* out2;
   double lam;
   cudaStream_t stream;
+  const int* skip = nullptr;  // device flag read by every CTA at launch (KParams::skip)
 };
 
 // Builds (if needed) the tile list of (op, dtype) on the device.  Synchronous.
@@ -99,6 +100,11 @@ SPX_DECL_ALL_OPS(f32, 2)
 SPX_DECL_ALL_OPS(f32, 3)
 
 spx_status launch_op(const LaunchReq& r);
+
+// Helmholtz apply for the solver: as spx_helmholtz (constant lambda, kappa =
+// 1), but the launch does nothing when *skip != 0 at the time it runs.
+spx_status helmholtz_unless(const spx_plan* p, int dtype, double lambda, const void* in, void* out,
+                            const int* skip, cudaStream_t stream);
 
 // Shared-memory footprint of (op, dtype) with the plan's current tile
 // configuration; 0 if the tile does not fit.

@@ -1,5 +1,6 @@
-"""GPU parity of the assembled solve (Jacobi-PCG, FP64 and FP32-inner with FP64
-refinement) against the oracle, plus the error paths of the solver."""
+"""GPU parity of the assembled solve (Jacobi-PCG: FP64, FP32-inner with FP64
+refinement, FP32 with reliable updates) against the oracle, plus the error
+paths of the solver."""
 import numpy as np
 import pytest
 import torch
@@ -31,7 +32,7 @@ def manufactured_rhs_gpu(c, l2g, ng, lam=1.0):
 
 
 @pytest.mark.parametrize("dim,N,P", [(3, 2, 3), (2, 3, 4), (3, 3, 2)])
-@pytest.mark.parametrize("precision", ["f64", "f32_refine"])
+@pytest.mark.parametrize("precision", ["f64", "f32_refine", "f32_reliable"])
 def test_solve_matches_dense_cholesky(dim, N, P, precision):
     c = Case(dim, N, P=P, amp=0.05)
     l2g, ng = mesh.periodic_l2g(dim, N, P)
@@ -48,7 +49,7 @@ def test_solve_matches_dense_cholesky(dim, N, P, precision):
     assert true_res <= 2e-12 and abs(true_res - info["rel_residual"]) <= 1e-13
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32_refine"])
+@pytest.mark.parametrize("precision", ["f64", "f32_refine", "f32_reliable"])
 def test_manufactured_solution_matches_oracle(precision):
     dim, N, P = 3, 4, 4
     c = Case(dim, N, P=P, amp=0.05)
@@ -75,7 +76,7 @@ def test_graph_and_eager_are_bitwise_equal():
     c = Case(dim, N, P=P, amp=0.05)
     l2g, ng = mesh.periodic_l2g(dim, N, P)
     b = torch.tensor(synth.uniform(synth.rng(32), ng), device="cuda")
-    for precision in ("f64", "f32_refine"):
+    for precision in ("f64", "f32_refine", "f32_reliable"):
         xg, ig = spx.cg_solve(c.plan, 1.0, l2g, ng, b, tol=1e-10, precision=precision, use_graph=True, check_every=7)
         xe, ie = spx.cg_solve(c.plan, 1.0, l2g, ng, b, tol=1e-10, precision=precision, use_graph=False, check_every=7)
         assert torch.equal(xg, xe)
@@ -114,3 +115,26 @@ def test_resume_from_saved_iterate():
     xr, _ = spx.cg_solve(c.plan, 1.0, l2g, ng, b, tol=1e-10, precision="f64")
     assert info2["status"] == 0
     assert rel_err(x, xr.cpu().numpy()) <= 1e-8
+
+
+@pytest.mark.parametrize("inner_tol", [1e-1, 1e-3])
+def test_reliable_updates_replace_the_residual(inner_tol):
+    """precision 2: each FP32 stretch lowers the true FP64 residual by about inner_tol, the run is
+    not restarted (fewer FP32 iterations than restarted refinement at the same inner_tol), and the
+    iteration cap is a cap on all FP32 iterations."""
+    dim, N, P = 3, 4, 4
+    c = Case(dim, N, P=P, amp=0.05)
+    l2g, ng = mesh.periodic_l2g(dim, N, P)
+    b = torch.tensor(synth.uniform(synth.rng(35), ng), device="cuda")
+    xr, ir = spx.cg_solve(c.plan, 1.0, l2g, ng, b, tol=1e-10, precision="f32_reliable", inner_tol=inner_tol)
+    xf, if_ = spx.cg_solve(c.plan, 1.0, l2g, ng, b, tol=1e-10, precision="f32_refine", inner_tol=inner_tol)
+    x64, _ = spx.cg_solve(c.plan, 1.0, l2g, ng, b, tol=1e-12, precision="f64")
+    assert ir["status"] == 0 and ir["rel_residual"] <= 1e-10
+    assert rel_err(xr, x64.cpu().numpy()) <= 1e-8
+    # ten decades in steps of inner_tol (the last step may be shorter)
+    steps = int(np.ceil(10 / -np.log10(inner_tol)))
+    assert steps <= ir["outer_iters"] <= steps + 3
+    assert ir["iters"] <= if_["iters"]
+    x, info = spx.cg_solve(c.plan, 1.0, l2g, ng, b, tol=1e-10, precision="f32_reliable", inner_tol=inner_tol,
+                           maxit=7, raise_on_fail=False)
+    assert info["status"] == 4 and info["iters"] == 7

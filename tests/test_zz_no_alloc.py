@@ -45,7 +45,7 @@ def _noalloc(plan, l2g, ng, f, x, precision):
     return st, res
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32_refine"])
+@pytest.mark.parametrize("precision", ["f64", "f32_refine", "f32_reliable"])
 def test_noalloc_solve_matches_workspace_solve_twice(precision):
     N, P = 4, 3
     plan, _ = _plan(N, P)

@@ -331,21 +331,24 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
                                "frac": round(fl / ms / 1e9 / FP64_PEAK_TFLOPS, 4),
                                "flops_per_launch": fl},
                   "hbm_frac": round(E * helm_bytes_per_elem(P, Q, 8) / ms / 1e6 / hbm_peak, 4)}
-    # PhysDeriv, BwdTrans, IProduct (FP32 and FP64)
+    # PhysDeriv, BwdTrans, IProduct (FP32 and FP64), each with its autotuned tile
     ops = {}
     for dt, sz in ((torch.float32, 4), (torch.float64, 8)):
-        f = spx.bwd_trans(plan, torch.tensor(coef, device="cuda", dtype=dt))
+        c = torch.tensor(coef, device="cuda", dtype=dt)
+        f = spx.bwd_trans(plan, c)
         outs = [torch.empty_like(f) for _ in range(3)]
-        c = torch.empty(plan.n_coef, dtype=dt, device="cuda")
         tag = "f32" if dt == torch.float32 else "f64"
-        for op, fn, nbytes in (
-                ("phys_deriv", lambda: spx.phys_deriv(plan, f, outs), E * 13 * Q ** 3 * sz),
-                ("bwd_trans", lambda: spx.bwd_trans(plan, c, f), E * (125 + Q ** 3) * sz),
-                ("iproduct", lambda: spx.iproduct(plan, f, c), E * (2 * Q ** 3 + 125) * sz)):
+        packed = torch.empty(3 * plan.n_quad, dtype=dt, device="cuda")
+        for op, fn, nbytes, tin, tout in (
+                ("phys_deriv", lambda: spx.phys_deriv(plan, f, outs), E * 13 * Q ** 3 * sz, f, packed),
+                ("bwd_trans", lambda: spx.bwd_trans(plan, c, f), E * (125 + Q ** 3) * sz, c, f),
+                ("iproduct", lambda: spx.iproduct(plan, f, c), E * (2 * Q ** 3 + 125) * sz, f, c)):
+            plan.autotune(op, dt, tin, tout, reps=5)
             fn()
             ms = timed(fn, reps, stream)
             ops[f"{op}_{tag}"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
-                                  "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4)}
+                                  "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4),
+                                  "tile_eb_threads_stages": list(plan.get_tile(op, dt, P))}
     ex["ops_hex32"] = ops
     # variable order workload
     wv, pv, gv, cv = make_workload("hex3d_24_varp", spx, mesh, synth, torch)

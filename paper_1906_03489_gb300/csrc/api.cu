@@ -184,6 +184,7 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
   }
   p->num_sms = prop.multiProcessorCount;
   p->max_smem = prop.sharedMemPerBlockOptin;
+  p->smem_per_sm = prop.sharedMemPerMultiprocessor;
   // device metadata
   auto cleanup = [&](cudaError_t err, const char* what) {
     spx_plan_destroy(p);
@@ -396,6 +397,25 @@ static float time_op(spx_plan* p, int op, spx_dtype dt, const void* in, void* ou
   return ms / std::max(1, reps);
 }
 
+// Threads (compute threads plus the producer warp of the variable-order FP32
+// Helmholtz kernel) and shared memory of a CTA whose largest tile is order
+// P's, with eb elements (every other order at one element).
+static void tile_footprint(const spx_plan* p, int op, int dt, const LaunchCfg& base, int P, int eb, int* thr,
+                           size_t* smem) {
+  LaunchCfg c = base;
+  for (int o = 1; o <= kMaxP; ++o) c.order[o].eb = 1;
+  c.order[P].eb = eb;
+  const int Q = P + p->qoff;
+  if (uses_pair_kernel(p, op, dt)) {
+    const PairShape s = pair_shape(p, c, pair_threshold(p));
+    *thr = s.nthreads + (p->uniform ? 0 : 32);
+    *smem = s.smem;
+  } else {
+    *thr = (op == OP_HELM && p->dim == 3) ? (eb * Q * Q + 31) / 32 * 32 : c.nthreads;
+    *smem = op_smem_bytes(p, op, dt, c);
+  }
+}
+
 spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, void* out, int reps, void* stream) {
   if (!p || !in || !out || op < 0 || op >= SPX_OP_COUNT || (dt != SPX_F64 && dt != SPX_F32) || reps < 1)
     return fail(SPX_ERR_INVALID_ARG, "autotune: bad argument");
@@ -408,6 +428,50 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
   const std::vector<int> nts = pair ? std::vector<int>{512, 640, 768} : std::vector<int>{64, 128, 192, 256, 384, 512};
   const std::vector<int> sts = pair ? std::vector<int>{0, 1, 2} : std::vector<int>{2, 3};
   LaunchCfg best = p->cfg[op][dt];
+  // Variable order: one launch serves every order, so its CTA is sized by the
+  // largest order's tile (threads and shared memory), and a single large tile
+  // caps the CTAs per SM for all orders.  First pass: for k = 1..4 CTAs per
+  // SM, every order takes its largest tile that lets k CTAs fit (512 / k
+  // threads, 1 / k of the SM's shared memory); the fastest k is the start of
+  // the per-order search below.
+  if (!p->uniform) {
+    float kms = 1e30f;
+    LaunchCfg kbest = best;
+    for (int k = 1; k <= 4; ++k) {
+      LaunchCfg c = best;
+      const int tmax = 512 / k;
+      const size_t smax = std::min(p->max_smem, p->smem_per_sm / k - 1024);
+      bool ok = true;
+      for (int P = 1; P <= kMaxP && ok; ++P) {
+        if (!p->present[P]) continue;
+        int pick = 0;
+        for (int eb : ebs) {
+          int thr = 0;
+          size_t sm = 0;
+          tile_footprint(p, op, dt, c, P, eb, &thr, &sm);
+          if (thr <= tmax && sm <= smax) pick = eb;
+        }
+        if (pick == 0) ok = false;
+        c.order[P].eb = pick;
+      }
+      if (!ok || op_smem_bytes(p, op, dt, c) > p->max_smem) continue;
+      p->cfg[op][dt] = c;
+      p->tiles[op][dt].dirty = true;
+      spx_status s;
+      const float ms = time_op(p, op, dt, in, out, reps, st, &s);
+      if (s != SPX_OK) {
+        p->cfg[op][dt] = best;
+        p->tiles[op][dt].dirty = true;
+        if (s == SPX_ERR_UNSUPPORTED) continue;
+        return s;
+      }
+      if (ms < kms) {
+        kms = ms;
+        kbest = c;
+      }
+    }
+    best = kbest;
+  }
   // orders one at a time (other orders keep their current tile); the same
   // thread count and depth serve the whole launch, so they are tuned last.
   float best_ms = 1e30f;

@@ -104,6 +104,37 @@ __device__ bool grid_reduce2(double a, double b, double* partials, unsigned int*
   return true;
 }
 
+// ---- dot-product accumulation ----------------------------------------------
+// Per-thread partial sums of the dot products.  FP64 vectors: plain FP64.
+// FP32 vectors: an unevaluated float pair hi + lo (double-float) that keeps
+// FP64-level accuracy without FP64 instructions (an FP32 -> FP64 conversion
+// and a DFMA per term would run on the FP64 pipe, 1/64 of the FP32 rate on
+// this part, and bound the kernels).  Each product a b is split exactly into
+// p + e (p = fl(a b), e = fma(a, b, -p)); p is added to hi by Knuth's TwoSum,
+// which also yields the exact rounding error of that addition; both errors go
+// into lo.  The pair's relative error is about (terms) x 2^-48.  The partial
+// sums are then reduced across threads in FP64 (grid_reduce2).
+template <typename T>
+struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { s = fma(static_cast<double>(a), static_cast<double>(b), s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
 // ---- CSR transpose of l2g ------------------------------------------------
 __global__ void csr_count(const int32_t* l2g, int64_t nl, int32_t* cnt) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nl; i += int64_t(gridDim.x) * blockDim.x)
@@ -211,20 +242,6 @@ __device__ __forceinline__ void stp(T* __restrict__ a, int64_t i, const Pack<T, 
   }
 }
 
-// V consecutive int32 from a V-aligned position (V * 4 bytes).
-template <int V>
-__device__ __forceinline__ void ldi(const int32_t* __restrict__ a, int64_t i, int32_t* out) {
-  if constexpr (V == 4) {
-    const int4 x = reinterpret_cast<const int4*>(a)[i];
-    out[0] = x.x; out[1] = x.y; out[2] = x.z; out[3] = x.w;
-  } else if constexpr (V == 2) {
-    const int2 x = reinterpret_cast<const int2*>(a)[i];
-    out[0] = x.x; out[1] = x.y;
-  } else {
-    out[0] = a[i];
-  }
-}
-
 template <typename T>
 __global__ void assemble_plain(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
                                const T* __restrict__ yl, T* __restrict__ yg, int64_t ng) {
@@ -235,79 +252,63 @@ __global__ void assemble_plain(const int32_t* __restrict__ row_ptr, const int32_
   }
 }
 
-// loc = g[l2g] (skipped once the solve is done)
-template <typename T, int V>
+// loc = g[l2g] (skipped once the solve is done).  One entry per thread and
+// trip: the lanes of a warp read consecutive l2g entries, whose global
+// indices run in short consecutive stretches (the modes of an element row).
+template <typename T>
 __global__ void gather_if(const int32_t* __restrict__ l2g, const T* __restrict__ g, T* __restrict__ loc, int64_t n,
                           const Scalars* sc) {
   if (sc->done) return;
-  const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int64_t np = n / V;
-  for (int64_t i = t0; i < np; i += S) {
-    int32_t k[V];
-    ldi<V>(l2g, i, k);
-    Pack<T, V> v;
-#pragma unroll
-    for (int u = 0; u < V; ++u) v.v[u] = g[k[u]];
-    stp<T, V>(loc, i, v);
-  }
-  for (int64_t i = np * V + t0; i < n; i += S) loc[i] = g[l2g[i]];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    loc[i] = g[l2g[i]];
 }
 
 // q = assemble(ql); pAp = <p, q>; alpha = rz / pAp.  A thread sums the rows
-// of kRowsA consecutive global indices in lockstep (each row in CSR order).
-constexpr int kRowsA = 8;
-template <typename T, int V>
+// g, g + S, ... (S = all threads), kRowsA of them in lockstep, each row in CSR
+// order; the lanes of a warp take consecutive rows.
+constexpr int kRowsA = 4;
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads) assemble_dot(const int32_t* __restrict__ row_ptr,
                                                             const int32_t* __restrict__ cols,
                                                             const T* __restrict__ ql, T* __restrict__ q,
                                                             const T* __restrict__ p, int64_t ng, Scalars* sc,
                                                             double* partials) {
   if (sc->done) return;
-  constexpr int NP = kRowsA / V;   // packs per trip
-  double acc = 0.0;
-  const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int64_t nt = ng / kRowsA;  // whole trips
-  for (int64_t it = t0; it < nt; it += S) {
-    const int64_t g0 = it * kRowsA;
+  DotAcc<T> acc;
+  const int64_t S = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g0 < ng; g0 += kRowsA * S) {
     int32_t k0[kRowsA], k1[kRowsA];
-#pragma unroll
-    for (int u = 0; u < kRowsA; ++u) k0[u] = row_ptr[g0 + u];
-#pragma unroll
-    for (int u = 0; u < kRowsA - 1; ++u) k1[u] = k0[u + 1];
-    k1[kRowsA - 1] = row_ptr[g0 + kRowsA];
-    Pack<T, V> pv[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) pv[j] = ldp<T, V>(p, it * NP + j);
+    T pv[kRowsA], sv[kRowsA];
     int len = 0;
 #pragma unroll
-    for (int u = 0; u < kRowsA; ++u) len = max(len, k1[u] - k0[u]);
-    T sv[kRowsA];
-#pragma unroll
-    for (int u = 0; u < kRowsA; ++u) sv[u] = T(0);
+    for (int u = 0; u < kRowsA; ++u) {
+      const int64_t g = g0 + u * S;
+      k0[u] = k1[u] = 0;
+      pv[u] = T(0);
+      sv[u] = T(0);
+      if (g < ng) {
+        k0[u] = row_ptr[g];
+        k1[u] = row_ptr[g + 1];
+        pv[u] = p[g];
+      }
+      len = max(len, k1[u] - k0[u]);
+    }
     for (int j = 0; j < len; ++j) {
 #pragma unroll
       for (int u = 0; u < kRowsA; ++u)
         if (k0[u] + j < k1[u]) sv[u] += ql[cols[k0[u] + j]];
     }
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      Pack<T, V> qv;
-#pragma unroll
-      for (int u = 0; u < V; ++u) {
-        qv.v[u] = sv[j * V + u];
-        acc += static_cast<double>(pv[j].v[u]) * static_cast<double>(qv.v[u]);
+    for (int u = 0; u < kRowsA; ++u) {
+      const int64_t g = g0 + u * S;
+      if (g < ng) {
+        q[g] = sv[u];
+        acc.add(pv[u], sv[u]);
       }
-      stp<T, V>(q, it * NP + j, qv);
     }
   }
-  for (int64_t g = nt * kRowsA + t0; g < ng; g += S) {
-    T s = T(0);
-    for (int32_t k = row_ptr[g]; k < row_ptr[g + 1]; ++k) s += ql[cols[k]];
-    q[g] = s;
-    acc += static_cast<double>(p[g]) * static_cast<double>(s);
-  }
   double pAp, unused;
-  if (grid_reduce2(acc, 0.0, partials, &sc->ticket, &pAp, &unused)) {
+  if (grid_reduce2(acc.value(), 0.0, partials, &sc->ticket, &pAp, &unused)) {
     sc->pAp = pAp;
     sc->alpha = sc->rz / pAp;
     sc->ticket = 0;
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* _
   if (sc->done) return;
   constexpr int U = V == 1 ? 4 : 1;   // packs per trip (loads in flight per thread)
   const T alpha = static_cast<T>(sc->alpha);
-  double arz = 0.0, arr = 0.0;
+  DotAcc<T> arz, arr;
   const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int64_t np = ng / V;
   for (int64_t i0 = t0; i0 < np; i0 += U * S) {
@@ -352,8 +353,8 @@ __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* _
           const T rn = rv[u].v[c] - alpha * qv[u].v[c];
           rv[u].v[c] = rn;
           zv.v[c] = mv[u].v[c] * rn;
-          arz += static_cast<double>(rn) * static_cast<double>(zv.v[c]);
-          arr += static_cast<double>(rn) * static_cast<double>(rn);
+          arz.add(rn, zv.v[c]);
+          arr.add(rn, rn);
         }
         stp<T, V>(x, i, xv[u]);
         stp<T, V>(r, i, rv[u]);
@@ -367,11 +368,11 @@ __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* _
     r[g] = rn;
     const T zv = minv[g] * rn;
     z[g] = zv;
-    arz += static_cast<double>(rn) * static_cast<double>(zv);
-    arr += static_cast<double>(rn) * static_cast<double>(rn);
+    arz.add(rn, zv);
+    arr.add(rn, rn);
   }
   double rz, rr;
-  if (grid_reduce2(arz, arr, partials, &sc->ticket, &rz, &rr)) {
+  if (grid_reduce2(arz.value(), arr.value(), partials, &sc->ticket, &rz, &rr)) {
     sc->rz_new = rz;
     sc->beta = rz / sc->rz;
     sc->rz_prev = sc->rz;
@@ -411,7 +412,7 @@ template <typename T, int V>
 __global__ void __launch_bounds__(kRedThreads) cg_start(const T* __restrict__ r, T* __restrict__ z,
                                                         T* __restrict__ p, const T* __restrict__ minv, int64_t ng,
                                                         Scalars* sc, double* partials) {
-  double arz = 0.0, arr = 0.0;
+  DotAcc<T> arz, arr;
   const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int64_t np = ng / V;
   for (int64_t i = t0; i < np; i += S) {
@@ -420,8 +421,8 @@ __global__ void __launch_bounds__(kRedThreads) cg_start(const T* __restrict__ r,
 #pragma unroll
     for (int c = 0; c < V; ++c) {
       zv.v[c] = mv.v[c] * rv.v[c];
-      arz += static_cast<double>(rv.v[c]) * static_cast<double>(zv.v[c]);
-      arr += static_cast<double>(rv.v[c]) * static_cast<double>(rv.v[c]);
+      arz.add(rv.v[c], zv.v[c]);
+      arr.add(rv.v[c], rv.v[c]);
     }
     stp<T, V>(z, i, zv);
     stp<T, V>(p, i, zv);
@@ -430,11 +431,11 @@ __global__ void __launch_bounds__(kRedThreads) cg_start(const T* __restrict__ r,
     const T rv = r[g], zv = minv[g] * rv;
     z[g] = zv;
     p[g] = zv;
-    arz += static_cast<double>(rv) * static_cast<double>(zv);
-    arr += static_cast<double>(rv) * static_cast<double>(rv);
+    arz.add(rv, zv);
+    arr.add(rv, rv);
   }
   double rz, rr;
-  if (grid_reduce2(arz, arr, partials, &sc->ticket, &rz, &rr)) {
+  if (grid_reduce2(arz.value(), arr.value(), partials, &sc->ticket, &rz, &rr)) {
     sc->rz = rz;
     sc->rr = rr;
     sc->it = 0;
@@ -488,18 +489,18 @@ __global__ void __launch_bounds__(kRedThreads) reliable_restart(const double* __
                                                                 const float* __restrict__ minv, int64_t ng,
                                                                 double inv_s_new, double c, Scalars* sc,
                                                                 double* partials) {
-  double arz = 0.0, arr = 0.0;
+  DotAcc<float> arz, arr;
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
     const float rv = static_cast<float>(r64[g] * inv_s_new);
     const float zv = minv[g] * rv;
     r32[g] = rv;
     d32[g] = 0.f;
     z32[g] = zv;
-    arz += static_cast<double>(rv) * static_cast<double>(zv);
-    arr += static_cast<double>(rv) * static_cast<double>(rv);
+    arz.add(rv, zv);
+    arr.add(rv, rv);
   }
   double rz, rr;
-  if (grid_reduce2(arz, arr, partials, &sc->ticket, &rz, &rr)) {
+  if (grid_reduce2(arz.value(), arr.value(), partials, &sc->ticket, &rz, &rr)) {
     sc->beta = rz / (c * sc->rz_prev);
     sc->rz = rz;
     sc->rr = rr;
@@ -586,6 +587,7 @@ struct Solver {
   cudaStream_t st;
   int grid_v;    // grid of element-wise kernels
   int nred;      // grid of reduction kernels (fixed => deterministic)
+  int grid_dir;  // grid of the direction update
   Workspace w;
   double lam;
 };
@@ -656,14 +658,10 @@ struct PcgRun {
   spx_status enqueue_iteration() {
     Workspace& w = s->w;
     cudaStream_t st = s->st;
-    if (a16(s->l2g) && a16(p) && a16(pl)) gather_if<T, V><<<s->grid_v, 256, 0, st>>>(s->l2g, p, pl, s->nl, w.sc);
-    else gather_if<T, 1><<<s->grid_v, 256, 0, st>>>(s->l2g, p, pl, s->nl, w.sc);
+    gather_if<T><<<s->grid_v, 256, 0, st>>>(s->l2g, p, pl, s->nl, w.sc);
     spx_status e = helmholtz_unless(s->plan, dt, s->lam, pl, ql, &w.sc->done, st);
     if (e != SPX_OK) return e;
-    if (a16(q) && a16(p))
-      assemble_dot<T, V><<<s->nred, kRedThreads, 0, st>>>(w.row_ptr, w.cols, ql, q, p, s->ng, w.sc, w.partials);
-    else
-      assemble_dot<T, 1><<<s->nred, kRedThreads, 0, st>>>(w.row_ptr, w.cols, ql, q, p, s->ng, w.sc, w.partials);
+    assemble_dot<T><<<s->nred, kRedThreads, 0, st>>>(w.row_ptr, w.cols, ql, q, p, s->ng, w.sc, w.partials);
     if (a16(x) && a16(r) && a16(z) && a16(p) && a16(q) && a16(minv))
       cg_update<T, V><<<s->nred, kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc, w.partials);
     else
@@ -674,8 +672,8 @@ struct PcgRun {
   }
 
   void direction() {
-    if (a16(p) && a16(z)) cg_direction<T, V><<<s->grid_v, 256, 0, s->st>>>(p, z, s->ng, s->w.sc);
-    else cg_direction<T, 1><<<s->grid_v, 256, 0, s->st>>>(p, z, s->ng, s->w.sc);
+    if (a16(p) && a16(z)) cg_direction<T, V><<<s->grid_dir, 256, 0, s->st>>>(p, z, s->ng, s->w.sc);
+    else cg_direction<T, 1><<<s->grid_dir, 256, 0, s->st>>>(p, z, s->ng, s->w.sc);
   }
 
   // z = minv r; p = z; rz (scalars ff / tol2 / maxit set by the caller)
@@ -801,7 +799,34 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
   s.ng = n_global;
   s.nl = plan->n_coef;
   s.lam = lambda;
-  s.nred = plan->num_sms * 8;
+  // Grids of one wave: every block of a reduction kernel is resident at once
+  // (blocks per SM = the smallest occupancy of the reduction kernels, so the
+  // grid, and with it the order of every sum, is the same for all of them).
+  {
+    int bmin = 8;
+    auto occ = [&](const void* k) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kRedThreads, 0) == cudaSuccess && nb > 0)
+        bmin = std::min(bmin, nb);
+    };
+    occ(reinterpret_cast<const void*>(assemble_dot<float>));
+    occ(reinterpret_cast<const void*>(assemble_dot<double>));
+    occ(reinterpret_cast<const void*>(cg_update<float, 4>));
+    occ(reinterpret_cast<const void*>(cg_update<float, 1>));
+    occ(reinterpret_cast<const void*>(cg_update<double, 2>));
+    occ(reinterpret_cast<const void*>(cg_update<double, 1>));
+    occ(reinterpret_cast<const void*>(cg_start<float, 4>));
+    occ(reinterpret_cast<const void*>(cg_start<float, 1>));
+    occ(reinterpret_cast<const void*>(cg_start<double, 2>));
+    occ(reinterpret_cast<const void*>(cg_start<double, 1>));
+    occ(reinterpret_cast<const void*>(residual64));
+    occ(reinterpret_cast<const void*>(reliable_restart));
+    s.nred = plan->num_sms * bmin;
+    int nd = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd, cg_direction<float, 4>, 256, 0) != cudaSuccess || nd < 1)
+      nd = 4;
+    s.grid_dir = plan->num_sms * std::min(8, nd);
+  }
   s.grid_v = plan->num_sms * 8;
   s.w = carve(static_cast<char*>(workspace), n_global, plan->n_coef, s.nred, o->precision);
   if (ws_bytes < s.w.bytes) return fail(SPX_ERR_NO_MEMORY, "cg_solve: workspace smaller than cg_workspace_bytes");

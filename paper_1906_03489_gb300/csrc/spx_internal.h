@@ -46,7 +46,8 @@ struct spx_plan {
   std::vector<int64_t> bucket_start;     // host: start of each order's bucket in ids
   int device = 0;
   int num_sms = 0;
-  size_t max_smem = 0;
+  size_t max_smem = 0;                   // shared memory per block (opt-in limit)
+  size_t smem_per_sm = 0;                // shared memory per SM
   // device metadata (owned)
   int64_t* d_coef_off = nullptr;
   int64_t* d_quad_off = nullptr;

@@ -260,21 +260,51 @@ def run_ours(a):
     achieved = bytes_launch / (ms * 1e-3) / 1e9
     traffic = profiled_traffic("helmholtz_f32_hex32.txt")
 
-    # end to end through the C ABI with host buffers: H2D of u, apply, D2H of y
+    # end to end through the C ABI with host buffers: every step copies its
+    # input u from pinned host memory, applies the operator and copies the
+    # result y back.  Served as a pipeline on three streams with two device
+    # buffers each: the upload of step i+1 and the download of step i-1 run on
+    # the copy engines while step i computes.
     uh = torch.tensor(coef, dtype=dt).pin_memory()
-    yh = torch.empty(plans[0].n_coef, dtype=dt).pin_memory()
-    ud, yd = torch.empty_like(u[0]), torch.empty_like(u[0])
+    yh = [torch.empty(plans[0].n_coef, dtype=dt).pin_memory() for _ in range(2)]
+    ud = [torch.empty_like(u[0]) for _ in range(2)]
+    yd = [torch.empty_like(u[0]) for _ in range(2)]
+    s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_comp = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    for k in range(2):   # every buffer starts free
+        ev_comp[k].record(s_comp)
+        ev_out[k].record(s_out)
 
-    def e2e_step():
-        ud.copy_(uh, non_blocking=True)
-        spx.helmholtz(plans[0], ud, lam=1.0, out=yd)
-        yh.copy_(yd, non_blocking=True)
+    def e2e_step(i):
+        k = i & 1
+        with torch.cuda.stream(s_in):
+            s_in.wait_event(ev_comp[k])          # ud[k] no longer read by step i-2
+            ud[k].copy_(uh, non_blocking=True)
+            ev_in[k].record(s_in)
+        with torch.cuda.stream(s_comp):
+            s_comp.wait_event(ev_in[k])
+            s_comp.wait_event(ev_out[k])         # yd[k] downloaded by step i-2
+            spx.helmholtz(plans[0], ud[k], lam=1.0, out=yd[k])
+            ev_comp[k].record(s_comp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_comp[k])
+            yh[k].copy_(yd[k], non_blocking=True)
+            ev_out[k].record(s_out)
 
-    for _ in range(3):
-        e2e_step()
+    for i in range(4):
+        e2e_step(i)
     torch.cuda.synchronize()
     k_e2e = max(10, a.steps // 10)
-    ms_e2e = max_over_ranks(timed(e2e_step, k_e2e, stream), world)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record(s_in)
+    for i in range(k_e2e):
+        e2e_step(i)
+    t1e.record(s_out)          # after the last download, which follows every earlier step
+    t1e.synchronize()
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(t0e.elapsed_time(t1e) / k_e2e, world)
     e2e_value = world * dofs / (ms_e2e * 1e-3) / 1e9
 
     extras = {}
@@ -301,7 +331,10 @@ def run_ours(a):
                          "algorithmic_bytes_per_launch": bytes_launch,
                          "bytes_model": "per element (2 (P+1)^3 coefficients + 7 Q^3 geometric factors) x 4 B"},
             "e2e": {"value": round(e2e_value, 3), "unit": "GDOF/s", "h2d_bytes_per_step": int(uh.numel() * 4),
-                    "d2h_bytes_per_step": int(yh.numel() * 4), "ms_per_step": round(ms_e2e, 4)},
+                    "d2h_bytes_per_step": int(yh[0].numel() * 4), "ms_per_step": round(ms_e2e, 4),
+                    "steps": k_e2e,
+                    "pipeline": "pinned host buffers; 3 streams, 2 device buffers each: the upload of step i+1 "
+                                "and the download of step i-1 overlap the apply of step i"},
             "gpu_launches": a.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -432,6 +465,46 @@ def measure_cg(spx, mesh, synth, torch):
     return res
 
 
+def run_case(a):
+    """Single-purpose runs for profiling (ncu launch lists and captures): one
+    workload, one operation, a short JSON line; not the benchmark contract."""
+    import torch
+    import paper_1906_03489_gb300 as spx
+    from paper_1906_03489_gb300 import mesh, synth
+    dist_setup()
+    spx.lib()
+    stream = torch.cuda.current_stream()
+    if a.case == "cg":
+        w = synth.WORKLOADS["hex3d_48_p4"]
+        N, P = w["N"], w["P"]
+        plan = spx.Plan(3, N ** 3, order=P)
+        g = spx.geom_factors(plan, mesh.structured_nodes(3, N, P, w["amp"]))
+        plan.set_geometry(torch.float64, g["geom"], g["dxi"])
+        plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])
+        l2g, ng = mesh.periodic_l2g(3, N, P)
+        f = torch.tensor(synth.uniform(synth.rng(w["seed"]), ng), device="cuda")
+        spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision=a.precision, maxit=5, max_outer=1,
+                     raise_on_fail=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision=a.precision, maxit=a.cg_maxit,
+                               max_outer=1, raise_on_fail=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "cg", "workload": "hex3d_48_p4", "precision": a.precision,
+                          "iters": info["iters"], "s": round(time.perf_counter() - t0, 4)}), flush=True)
+    elif a.case == "varp":
+        w, plans, _, coef = make_workload("hex3d_24_varp", spx, mesh, synth, torch)
+        plan = plans[0]
+        dt = torch.float32 if a.precision != "f64" else torch.float64
+        u = torch.tensor(coef, device="cuda", dtype=dt)
+        y = torch.empty_like(u)
+        plan.autotune("helmholtz", dt, u, y, reps=2)
+        ms = timed(lambda: spx.helmholtz(plan, u, out=y), max(1, a.steps), stream)
+        print(json.dumps({"case": "varp", "workload": "hex3d_24_varp", "dtype": str(dt), "ms": round(ms, 4),
+                          "tiles": {int(P): plan.get_tile("helmholtz", dt, int(P))[0]
+                                    for P in sorted(set(plan.orders.tolist()))}}), flush=True)
+
+
 def oracle_sample_rate(name, n_elem_sample, seconds, repeat=None):
     """Times the oracle's dense Helmholtz on a sample of the workload's elements."""
     import numpy as np
@@ -497,9 +570,15 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--case", default="bench", choices=["bench", "cg", "varp"],
+                    help="bench: the benchmark line; cg / varp: one short run for profiling")
+    ap.add_argument("--precision", default="f32_reliable", help="cg: f64 | f32_refine | f32_reliable; varp: f32 | f64")
+    ap.add_argument("--cg-maxit", type=int, default=30)
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
-    if a.impl == "reference":
+    if a.case != "bench":
+        run_case(a)
+    elif a.impl == "reference":
         os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
         os.environ.setdefault("OPENBLAS_NUM_THREADS", os.environ["OMP_NUM_THREADS"])
         run_reference(a)

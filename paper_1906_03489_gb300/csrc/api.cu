@@ -429,45 +429,52 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
   const std::vector<int> sts = pair ? std::vector<int>{0, 1, 2} : std::vector<int>{2, 3};
   LaunchCfg best = p->cfg[op][dt];
   // Variable order: one launch serves every order, so its CTA is sized by the
-  // largest order's tile (threads and shared memory), and a single large tile
-  // caps the CTAs per SM for all orders.  First pass: for k = 1..4 CTAs per
-  // SM, every order takes its largest tile that lets k CTAs fit (512 / k
-  // threads, 1 / k of the SM's shared memory); the fastest k is the start of
-  // the per-order search below.
+  // largest order's tile (threads and shared memory); an order whose tile
+  // uses fewer threads leaves them idle at every phase barrier, and one large
+  // tile caps the CTAs per SM for all orders.  First pass: for a target of T
+  // threads per CTA and k CTAs per SM, every order takes the largest tile
+  // (any size up to kMaxEB) that stays within T threads and 1 / k of the SM's
+  // shared memory, which evens out the orders' thread counts; the fastest
+  // (T, k) is the start of the per-order search below.
   if (!p->uniform) {
     float kms = 1e30f;
     LaunchCfg kbest = best;
-    for (int k = 1; k <= 4; ++k) {
-      LaunchCfg c = best;
-      const int tmax = 512 / k;
-      const size_t smax = std::min(p->max_smem, p->smem_per_sm / k - 1024);
-      bool ok = true;
-      for (int P = 1; P <= kMaxP && ok; ++P) {
-        if (!p->present[P]) continue;
-        int pick = 0;
-        for (int eb : ebs) {
-          int thr = 0;
-          size_t sm = 0;
-          tile_footprint(p, op, dt, c, P, eb, &thr, &sm);
-          if (thr <= tmax && sm <= smax) pick = eb;
+    std::vector<std::vector<int>> seen;
+    for (int T : {64, 96, 128, 160, 192, 224, 256, 320, 384, 448, 512}) {
+      for (int k = 1; k <= 3; ++k) {
+        LaunchCfg c = best;
+        const size_t smax = std::min(p->max_smem, p->smem_per_sm / k - 1024);
+        std::vector<int> key;
+        for (int P = 1; P <= kMaxP; ++P) {
+          if (!p->present[P]) continue;
+          int pick = 1;
+          for (int eb = 1; eb <= kMaxEB; ++eb) {
+            int thr = 0;
+            size_t sm = 0;
+            tile_footprint(p, op, dt, c, P, eb, &thr, &sm);
+            if (thr > T + (pair ? 32 : 0) || sm > smax) break;
+            pick = eb;
+          }
+          c.order[P].eb = pick;
+          key.push_back(pick);
         }
-        if (pick == 0) ok = false;
-        c.order[P].eb = pick;
-      }
-      if (!ok || op_smem_bytes(p, op, dt, c) > p->max_smem) continue;
-      p->cfg[op][dt] = c;
-      p->tiles[op][dt].dirty = true;
-      spx_status s;
-      const float ms = time_op(p, op, dt, in, out, reps, st, &s);
-      if (s != SPX_OK) {
-        p->cfg[op][dt] = best;
+        if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+        seen.push_back(key);
+        if (op_smem_bytes(p, op, dt, c) > p->max_smem) continue;
+        p->cfg[op][dt] = c;
         p->tiles[op][dt].dirty = true;
-        if (s == SPX_ERR_UNSUPPORTED) continue;
-        return s;
-      }
-      if (ms < kms) {
-        kms = ms;
-        kbest = c;
+        spx_status s;
+        const float ms = time_op(p, op, dt, in, out, reps, st, &s);
+        if (s != SPX_OK) {
+          p->cfg[op][dt] = best;
+          p->tiles[op][dt].dirty = true;
+          if (s == SPX_ERR_UNSUPPORTED) continue;
+          return s;
+        }
+        if (ms < kms) {
+          kms = ms;
+          kbest = c;
+        }
       }
     }
     best = kbest;

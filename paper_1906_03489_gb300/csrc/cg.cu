@@ -586,7 +586,7 @@ struct Solver {
   int64_t ng, nl;
   cudaStream_t st;
   int grid_v;    // grid of element-wise kernels
-  int nred;      // grid of reduction kernels (fixed => deterministic)
+  int nred;      // upper bound of the reduction kernels' grids (partials buffer)
   int grid_dir;  // grid of the direction update
   Workspace w;
   double lam;
@@ -597,6 +597,17 @@ struct Solver {
     cudaError_t e_ = (expr);                                  \
     if (e_ != cudaSuccess) return cuda_fail(e_, #expr);       \
   } while (0)
+
+// Grid of a reduction kernel: one wave, every block resident at once (SMs x
+// the kernel's occupancy, at most s.nred).  It is a property of the compiled
+// kernel and the GPU, so each kernel's grid, and with it the order of every
+// sum, is the same at every launch.
+template <class K>
+int one_wave(const Solver& s, K kern) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kRedThreads, 0) != cudaSuccess || nb < 1) nb = 1;
+  return std::min(s.nred, s.plan->num_sms * nb);
+}
 
 spx_status build_csr(Solver& s) {
   Workspace& w = s.w;
@@ -661,11 +672,14 @@ struct PcgRun {
     gather_if<T><<<s->grid_v, 256, 0, st>>>(s->l2g, p, pl, s->nl, w.sc);
     spx_status e = helmholtz_unless(s->plan, dt, s->lam, pl, ql, &w.sc->done, st);
     if (e != SPX_OK) return e;
-    assemble_dot<T><<<s->nred, kRedThreads, 0, st>>>(w.row_ptr, w.cols, ql, q, p, s->ng, w.sc, w.partials);
+    assemble_dot<T><<<one_wave(*s, assemble_dot<T>), kRedThreads, 0, st>>>(w.row_ptr, w.cols, ql, q, p, s->ng, w.sc,
+                                                                          w.partials);
     if (a16(x) && a16(r) && a16(z) && a16(p) && a16(q) && a16(minv))
-      cg_update<T, V><<<s->nred, kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc, w.partials);
+      cg_update<T, V><<<one_wave(*s, cg_update<T, V>), kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc,
+                                                                               w.partials);
     else
-      cg_update<T, 1><<<s->nred, kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc, w.partials);
+      cg_update<T, 1><<<one_wave(*s, cg_update<T, 1>), kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc,
+                                                                               w.partials);
     direction();
     SPX_CK(cudaGetLastError());
     return SPX_OK;
@@ -680,9 +694,11 @@ struct PcgRun {
   spx_status start() {
     Workspace& w = s->w;
     if (a16(r) && a16(z) && a16(p) && a16(minv))
-      cg_start<T, V><<<s->nred, kRedThreads, 0, s->st>>>(r, z, p, minv, s->ng, w.sc, w.partials);
+      cg_start<T, V><<<one_wave(*s, cg_start<T, V>), kRedThreads, 0, s->st>>>(r, z, p, minv, s->ng, w.sc,
+                                                                                w.partials);
     else
-      cg_start<T, 1><<<s->nred, kRedThreads, 0, s->st>>>(r, z, p, minv, s->ng, w.sc, w.partials);
+      cg_start<T, 1><<<one_wave(*s, cg_start<T, 1>), kRedThreads, 0, s->st>>>(r, z, p, minv, s->ng, w.sc,
+                                                                                w.partials);
     SPX_CK(cudaGetLastError());
     return SPX_OK;
   }
@@ -744,7 +760,7 @@ spx_status residual(Solver& s, const double* f, const double* x, double* rr, dou
   Workspace& w = s.w;
   spx_status st = apply_A<double>(s, SPX_F64, x, w.pl64, w.ql64, w.q64);
   if (st != SPX_OK) return st;
-  residual64<<<s.nred, kRedThreads, 0, s.st>>>(f, w.q64, w.r64, s.ng, w.sc, w.partials);
+  residual64<<<one_wave(s, residual64), kRedThreads, 0, s.st>>>(f, w.q64, w.r64, s.ng, w.sc, w.partials);
   SPX_CK(cudaGetLastError());
   Scalars h;
   st = read_scalars(s, &h);
@@ -799,29 +815,8 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
   s.ng = n_global;
   s.nl = plan->n_coef;
   s.lam = lambda;
-  // Grids of one wave: every block of a reduction kernel is resident at once
-  // (blocks per SM = the smallest occupancy of the reduction kernels, so the
-  // grid, and with it the order of every sum, is the same for all of them).
+  s.nred = plan->num_sms * 8;   // 256-thread blocks: at most 8 per SM
   {
-    int bmin = 8;
-    auto occ = [&](const void* k) {
-      int nb = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kRedThreads, 0) == cudaSuccess && nb > 0)
-        bmin = std::min(bmin, nb);
-    };
-    occ(reinterpret_cast<const void*>(assemble_dot<float>));
-    occ(reinterpret_cast<const void*>(assemble_dot<double>));
-    occ(reinterpret_cast<const void*>(cg_update<float, 4>));
-    occ(reinterpret_cast<const void*>(cg_update<float, 1>));
-    occ(reinterpret_cast<const void*>(cg_update<double, 2>));
-    occ(reinterpret_cast<const void*>(cg_update<double, 1>));
-    occ(reinterpret_cast<const void*>(cg_start<float, 4>));
-    occ(reinterpret_cast<const void*>(cg_start<float, 1>));
-    occ(reinterpret_cast<const void*>(cg_start<double, 2>));
-    occ(reinterpret_cast<const void*>(cg_start<double, 1>));
-    occ(reinterpret_cast<const void*>(residual64));
-    occ(reinterpret_cast<const void*>(reliable_restart));
-    s.nred = plan->num_sms * bmin;
     int nd = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd, cg_direction<float, 4>, 256, 0) != cudaSuccess || nd < 1)
       nd = 4;
@@ -873,8 +868,8 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
   // Jacobi diagonal: assembled diag(H_e)
   if ((st = spx_helmholtz_diag(plan, SPX_F64, lambda, w.diag64, s.st)) != SPX_OK) return finish(st);
   assemble_plain<double><<<s.grid_v, 256, 0, s.st>>>(w.row_ptr, w.cols, w.diag64, w.r64, s.ng);
-  invert_diag<double><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv64, s.ng);
-  if (o->precision >= 1) invert_diag<float><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv32, s.ng);
+  if (o->precision == 0) invert_diag<double><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv64, s.ng);
+  else invert_diag<float><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv32, s.ng);
   if (cudaGetLastError() != cudaSuccess) return finish(fail(SPX_ERR_CUDA, "cg setup kernels"));
 
   double rr, ff;
@@ -933,8 +928,8 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
         h.tol2 = itol * itol;
         h.ticket = 0;
         SPX_CK(cudaMemcpyAsync(w.sc, &h, sizeof(Scalars), cudaMemcpyHostToDevice, s.st));
-        reliable_restart<<<s.nred, kRedThreads, 0, s.st>>>(w.r64, w.r32, w.d32, w.z32, w.minv32, s.ng, 1.0 / s_new,
-                                                           s_old / s_new, w.sc, w.partials);
+        reliable_restart<<<one_wave(s, reliable_restart), kRedThreads, 0, s.st>>>(
+            w.r64, w.r32, w.d32, w.z32, w.minv32, s.ng, 1.0 / s_new, s_old / s_new, w.sc, w.partials);
         run.direction();
         SPX_CK(cudaGetLastError());
       }

@@ -445,13 +445,13 @@ __global__ void __launch_bounds__(kRedThreads) cg_start(const T* __restrict__ r,
   }
 }
 
-// r = f - y (FP64); rr = <r,r>; ff = <f,f>
+// r = f - y (FP64; y = nullptr: y = 0); rr = <r,r>; ff = <f,f>
 __global__ void __launch_bounds__(kRedThreads) residual64(const double* __restrict__ f, const double* __restrict__ y,
                                                           double* __restrict__ r, int64_t ng, Scalars* sc,
                                                           double* partials) {
   double arr = 0.0, aff = 0.0;
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
-    const double rv = f[g] - y[g];
+    const double rv = y ? f[g] - y[g] : f[g];
     r[g] = rv;
     arr += rv * rv;
     aff += f[g] * f[g];
@@ -460,6 +460,19 @@ __global__ void __launch_bounds__(kRedThreads) residual64(const double* __restri
   if (grid_reduce2(arr, aff, partials, &sc->ticket, &rr, &ff)) {
     sc->rr = rr;
     sc->ff = ff;
+    sc->ticket = 0;
+  }
+}
+
+// scale = <x, x> (FP64): tells whether the initial guess is zero
+__global__ void __launch_bounds__(kRedThreads) sumsq64(const double* __restrict__ x, int64_t ng, Scalars* sc,
+                                                       double* partials) {
+  double a = 0.0;
+  for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x)
+    a += x[g] * x[g];
+  double xx, unused;
+  if (grid_reduce2(a, 0.0, partials, &sc->ticket, &xx, &unused)) {
+    sc->scale = xx;
     sc->ticket = 0;
   }
 }
@@ -755,12 +768,17 @@ spx_status read_scalars(Solver& s, Scalars* h) {
   return SPX_OK;
 }
 
-// FP64 residual r = f - A x; returns ||r||^2 and ||f||^2 (sets rr, ff)
-spx_status residual(Solver& s, const double* f, const double* x, double* rr, double* ff) {
+// FP64 residual r = f - A x; returns ||r||^2 and ||f||^2 (sets rr, ff).
+// x_zero: x is known to be zero, so r = f without an apply.
+spx_status residual(Solver& s, const double* f, const double* x, double* rr, double* ff, bool x_zero = false) {
   Workspace& w = s.w;
-  spx_status st = apply_A<double>(s, SPX_F64, x, w.pl64, w.ql64, w.q64);
-  if (st != SPX_OK) return st;
-  residual64<<<one_wave(s, residual64), kRedThreads, 0, s.st>>>(f, w.q64, w.r64, s.ng, w.sc, w.partials);
+  if (!x_zero) {
+    spx_status st = apply_A<double>(s, SPX_F64, x, w.pl64, w.ql64, w.q64);
+    if (st != SPX_OK) return st;
+  }
+  residual64<<<one_wave(s, residual64), kRedThreads, 0, s.st>>>(f, x_zero ? nullptr : w.q64, w.r64, s.ng, w.sc,
+                                                                 w.partials);
+  spx_status st;
   SPX_CK(cudaGetLastError());
   Scalars h;
   st = read_scalars(s, &h);
@@ -872,8 +890,13 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
   else invert_diag<float><<<s.grid_v, 256, 0, s.st>>>(w.r64, w.minv32, s.ng);
   if (cudaGetLastError() != cudaSuccess) return finish(fail(SPX_ERR_CUDA, "cg setup kernels"));
 
+  // initial residual; a zero initial guess needs no apply
+  sumsq64<<<one_wave(s, sumsq64), kRedThreads, 0, s.st>>>(x, s.ng, w.sc, w.partials);
+  if (cudaGetLastError() != cudaSuccess) return finish(fail(SPX_ERR_CUDA, "cg initial guess norm"));
+  Scalars h0{};
+  if ((st = read_scalars(s, &h0)) != SPX_OK) return finish(st);
   double rr, ff;
-  if ((st = residual(s, f, x, &rr, &ff)) != SPX_OK) return finish(st);
+  if ((st = residual(s, f, x, &rr, &ff, h0.scale == 0.0)) != SPX_OK) return finish(st);
   if (ff == 0.0) {
     fill_zero<double><<<s.grid_v, 256, 0, s.st>>>(x, s.ng);
     return finish(SPX_OK);

@@ -23,6 +23,10 @@ What it computes, and the passage each part follows:
                  matrix (or dense mat-vec) built from the definitions.
 * ``solve``      periodic C0 assembly (§2.1 assembly paragraph), Jacobi PCG
                  and a dense Cholesky solve for tiny meshes.
+* ``adapt``      the element error sensor S_e = ||u_P - u_{P-1}||^2 / ||u_P||^2
+                 of the adaptive polynomial order procedure and its order
+                 update (§4.2), with u_{P-1} the dense L^2 projection onto the
+                 order P - 1 basis.
 * ``adjoint``    gradients of 0.5*||H(lambda,kappa)u - f||^2 with respect to
                  u, lambda(x) and kappa(x), by differentiating the dense
                  forms of eq. e:bilinear.

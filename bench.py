@@ -63,12 +63,22 @@ def helm_flops_per_elem(P, Q):
     return 2 * (2 * bwd + 6 * Q ** 4) + 20 * Q ** 3
 
 
-def kernel_digest():
+# Sources of the FP32 Helmholtz kernel and its launcher (what its ncu counters depend on).
+HELM_SOURCES = ("helm_pair.cuh", "op_kernel.cuh", "lanes.cuh", "kernel_params.h", "device_common.cuh",
+                "launch_ops.cuh", "smem_layout.h")
+
+
+def kernel_digest(names=None):
+    """Digest of the library sources (all of them, or the named files of csrc/)."""
     h = hashlib.sha256()
-    for d in (os.path.join(ROOT, "paper_1906_03489_gb300", "csrc"), os.path.join(ROOT, "include")):
-        for name in sorted(os.listdir(d)):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    csrc = os.path.join(ROOT, "paper_1906_03489_gb300", "csrc")
+    if names is None:
+        files = [(d, n) for d in (csrc, os.path.join(ROOT, "include")) for n in sorted(os.listdir(d))]
+    else:
+        files = [(csrc, n) for n in names]
+    for d, name in files:
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -81,7 +91,7 @@ def profiled_traffic(name):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_digest") == kernel_digest():
+        if kv.get("kernel_digest") == kernel_digest(HELM_SOURCES):
             return float(kv["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -382,6 +392,23 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
             ops[f"{op}_{tag}"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
                                   "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4),
                                   "tile_eb_threads_stages": list(plan.get_tile(op, dt, P))}
+        # FwdTrans (elemental preconditioned CG in one launch; reads f and JW, writes the coefficients)
+        # and Integral (reads f and JW)
+        f = spx.bwd_trans(plan, torch.tensor(coef, device="cuda", dtype=dt))
+        cf = torch.empty(plan.n_coef, dtype=dt, device="cuda")
+        plan.autotune("fwd_trans", dt, f, cf, reps=3)
+        ms = timed(lambda: spx.fwd_trans(plan, f, cf), reps, stream)
+        nbytes = E * (2 * Q ** 3 + 125) * sz
+        ops[f"fwd_trans_{tag}"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+                                   "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4),
+                                   "tile_eb_threads_stages": list(plan.get_tile("fwd_trans", dt, P)),
+                                   "max_err_vs_input_coefficients": (cf.double() - torch.tensor(coef, device="cuda")
+                                                                     ).abs().max().item()}
+        res = torch.empty((), dtype=torch.float64, device="cuda")
+        ms = timed(lambda: spx.integral(plan, f, res), reps, stream)
+        nbytes = E * 2 * Q ** 3 * sz
+        ops[f"integral_{tag}"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+                                  "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4)}
     ex["ops_hex32"] = ops
     # variable order workload
     wv, pv, gv, cv = make_workload("hex3d_24_varp", spx, mesh, synth, torch)

@@ -75,7 +75,10 @@ typedef enum {
   SPX_OP_IPRODUCT = 1,
   SPX_OP_PHYS_DERIV = 2,
   SPX_OP_HELMHOLTZ = 3,
-  SPX_OP_COUNT = 4
+  SPX_OP_HELMHOLTZ_ADJOINT = 4,
+  SPX_OP_HELMHOLTZ_DIAG = 5,
+  SPX_OP_FWD_TRANS = 6,
+  SPX_OP_COUNT = 7
 } spx_op;
 
 typedef struct spx_plan spx_plan;
@@ -220,6 +223,30 @@ spx_status spx_helmholtz(const spx_plan *plan, spx_dtype dtype, double lambda, c
  * forward call.  Needs FP64 geom. */
 spx_status spx_helmholtz_adjoint(const spx_plan *plan, const double *u, const double *g, double *grad_lambda,
                                  double *grad_kappa, void *stream);
+
+/* FwdTrans: Galerkin projection of quadrature-point values onto the
+ * expansion (§3.5, Listing lst:python, the FwdTrans call), per element
+ *   c_e = M_e^{-1} IProductWRTBase(f)_e,  M_e = Phi^T diag(JW) Phi.
+ * Solved in one launch by a preconditioned CG per element (matrix-free, in
+ * shared memory), preconditioned by (1 / Jbar_e) (M1^{-1})^{(x)d} with M1 the
+ * 1D mass matrix B^T diag(w) B and Jbar_e the element's mean Jacobian: exact,
+ * so one step, when det J is constant on the element.  Each element stops at
+ * ||M_e c - b||_2 <= tol ||b||_2 (tol 1e-14 FP64, 1e-6 FP32) or after 64 steps.
+ * The coefficients are as ill-conditioned as M_e (cond about 4e7 at P = 4 in
+ * 3D in this basis); the projected function BwdTrans(c) only by the square
+ * root: about sqrt(cond) x unit roundoff, i.e. ~1e-12 in FP64 but ~1e-4 in
+ * FP32 (use FP64 where the projection must be accurate).
+ * phys: device in [n_quad]; coef: device out [n_coef] (must not alias phys).
+ * Needs geom. */
+spx_status spx_fwd_trans(const spx_plan *plan, spx_dtype dtype, const void *phys, void *coef, void *stream);
+
+/* Integral over the mesh (§3.5, Listing lst:python, the Integral call):
+ * sum over elements and quadrature points of JW_q f_q, i.e. of w det J f.
+ * phys: device in [n_quad] of the call's dtype; result: device, one FP64
+ * value, written by the stream's work (read it after synchronising).  Sums in
+ * FP64 in a fixed order (reproducible).  Calls on one plan that overlap on the
+ * GPU race on the plan's partial-sum buffer: serialise them.  Needs geom. */
+spx_status spx_integral(const spx_plan *plan, spx_dtype dtype, const void *phys, double *result, void *stream);
 
 /* Diagonal of the elemental Helmholtz matrices, diag(H_e)_l for every local
  * mode (the Jacobi preconditioner before assembly).  out: device [n_coef]. */

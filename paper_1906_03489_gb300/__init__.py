@@ -2,11 +2,12 @@
 
 BwdTrans, IProductWRTBase, PhysDeriv and the Helmholtz operator H = lambda M + L
 evaluated over all elements of quad/hex meshes by sum-factorised CUDA kernels
-behind a C ABI (include/spx.h); adjoint of H with respect to its coefficient
-fields behind ``torch.autograd``; periodic C0 assembly and a mixed-precision
-Jacobi-PCG solver.
+behind a C ABI (include/spx.h); FwdTrans (Galerkin projection) and Integral;
+adjoint of H with respect to its coefficient fields behind ``torch.autograd``;
+periodic C0 assembly and a mixed-precision Jacobi-PCG solver.
 """
 from ._lib import SpxError, lib  # noqa: F401
 from .binding import (Plan, assemble, basis_tables, bwd_trans, cg_solve, cg_workspace_bytes,  # noqa: F401
-                      gather, geom_factors, helmholtz, helmholtz_adjoint, helmholtz_diag, iproduct, phys_deriv)
+                      fwd_trans, gather, geom_factors, helmholtz, helmholtz_adjoint, helmholtz_diag, integral,
+                      iproduct, phys_deriv)
 from .autograd import HelmholtzFn, helmholtz_ad  # noqa: F401

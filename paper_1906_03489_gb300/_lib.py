@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libspx.so")
 
 SPX_F64, SPX_F32 = 0, 1
-OPS = {"bwd_trans": 0, "iproduct": 1, "phys_deriv": 2, "helmholtz": 3}
+OPS = {"bwd_trans": 0, "iproduct": 1, "phys_deriv": 2, "helmholtz": 3, "helmholtz_adjoint": 4,
+       "helmholtz_diag": 5, "fwd_trans": 6}
 
 STATUS = {
     0: "SPX_OK", 1: "SPX_ERR_INVALID_ARG", 2: "SPX_ERR_UNSUPPORTED", 3: "SPX_ERR_CUDA",
@@ -62,6 +63,8 @@ SIGNATURES = {
     "spx_helmholtz": (I32, [P, I32, D, P, P, P, P, P]),
     "spx_helmholtz_adjoint": (I32, [P, P, P, P, P, P]),
     "spx_helmholtz_diag": (I32, [P, I32, D, P, P]),
+    "spx_fwd_trans": (I32, [P, I32, P, P, P]),
+    "spx_integral": (I32, [P, I32, P, P, P]),
     "spx_gather": (I32, [P, I32, P, I64, P, P, P]),
     "spx_assemble": (I32, [P, I32, P, I64, P, P, P]),
     "spx_cg_workspace_bytes": (I32, [P, I64, C.POINTER(CgOpts), C.POINTER(C.c_size_t)]),

@@ -11,7 +11,8 @@ import torch
 
 from ._lib import SPX_F32, SPX_F64, OPS, CgOpts, CgResult, PlanDesc, SpxError, check, lib
 
-__all__ = ["Plan", "basis_tables", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz",
+__all__ = ["Plan", "basis_tables", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz", "fwd_trans",
+           "integral",
            "helmholtz_adjoint", "helmholtz_diag", "gather", "assemble", "cg_workspace_bytes", "cg_solve", "SpxError"]
 
 
@@ -142,6 +143,22 @@ def iproduct(plan, f, out=None):
     _dev(f, "f")
     out = torch.empty(plan.n_coef, dtype=f.dtype, device=f.device) if out is None else out
     check(lib().spx_iproduct(plan.handle, _code(f.dtype), _p(f), _p(out), _stream()))
+    return out
+
+
+def fwd_trans(plan, f, out=None):
+    """Galerkin projection of quadrature-point values onto the expansion (per element)."""
+    _dev(f, "f")
+    out = torch.empty(plan.n_coef, dtype=f.dtype, device=f.device) if out is None else out
+    check(lib().spx_fwd_trans(plan.handle, _code(f.dtype), _p(f), _p(out), _stream()))
+    return out
+
+
+def integral(plan, f, out=None):
+    """Sum of JW f over the mesh as a device FP64 scalar tensor (``float(...)`` synchronises)."""
+    _dev(f, "f")
+    out = torch.empty((), dtype=torch.float64, device=f.device) if out is None else out
+    check(lib().spx_integral(plan.handle, _code(f.dtype), _p(f), _p(out), _stream()))
     return out
 
 

@@ -82,7 +82,7 @@ spx_status launch_op(const LaunchReq& r) {
   case DT * 100 + DIM * 10 + OP: return launch_##TN##_##DIM##_##OP(r);
 #define SPX_CASES(DT, TN, DIM) \
   SPX_CASE(DT, TN, DIM, 0) SPX_CASE(DT, TN, DIM, 1) SPX_CASE(DT, TN, DIM, 2) \
-  SPX_CASE(DT, TN, DIM, 3) SPX_CASE(DT, TN, DIM, 4) SPX_CASE(DT, TN, DIM, 5)
+  SPX_CASE(DT, TN, DIM, 3) SPX_CASE(DT, TN, DIM, 4) SPX_CASE(DT, TN, DIM, 5) SPX_CASE(DT, TN, DIM, 6)
     SPX_CASES(0, f64, 2)
     SPX_CASES(0, f64, 3)
     SPX_CASES(1, f32, 2)
@@ -192,6 +192,26 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
   };
   if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup(e, "cudaMalloc(status)");
   if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup(e, "cudaMemset(status)");
+  {  // inverse 1D mass matrices of every order (FwdTrans preconditioner)
+    std::vector<double> a64;
+    for (int P = 1; P <= kMaxP; ++P) {
+      p->aux_off[P] = static_cast<int>(a64.size());
+      const int n = P + 1;
+      a64.resize(a64.size() + n * n);
+      mass1d_inverse(P, P + qoff, a64.data() + p->aux_off[P]);
+    }
+    p->aux_off[kMaxP + 1] = static_cast<int>(a64.size());
+    std::vector<float> a32(a64.begin(), a64.end());
+    if ((e = cudaMalloc(&p->d_aux64, a64.size() * sizeof(double))) != cudaSuccess) return cleanup(e, "cudaMalloc(aux)");
+    if ((e = cudaMalloc(&p->d_aux32, a32.size() * sizeof(float))) != cudaSuccess) return cleanup(e, "cudaMalloc(aux)");
+    if ((e = cudaMemcpy(p->d_aux64, a64.data(), a64.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_aux32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cleanup(e, "cudaMemcpy(aux)");
+    if ((e = cudaMalloc(&p->d_partials, size_t(p->num_sms) * kIntegralBlocksPerSM * sizeof(double))) != cudaSuccess)
+      return cleanup(e, "cudaMalloc(partials)");
+    if ((e = cudaMalloc(&p->d_ticket, sizeof(unsigned int))) != cudaSuccess) return cleanup(e, "cudaMalloc(ticket)");
+    if ((e = cudaMemset(p->d_ticket, 0, sizeof(unsigned int))) != cudaSuccess) return cleanup(e, "cudaMemset(ticket)");
+  }
   if (!p->uniform) {
     p->bucket_start.assign(kMaxP + 2, 0);
     for (int64_t i = 0; i < p->E; ++i) p->bucket_start[p->orders[i] + 1]++;
@@ -237,6 +257,10 @@ spx_status spx_plan_destroy(spx_plan* p) {
   if (p->d_coef_off) cudaFree(p->d_coef_off);
   if (p->d_quad_off) cudaFree(p->d_quad_off);
   if (p->d_status) cudaFree(p->d_status);
+  if (p->d_aux64) cudaFree(p->d_aux64);
+  if (p->d_aux32) cudaFree(p->d_aux32);
+  if (p->d_partials) cudaFree(p->d_partials);
+  if (p->d_ticket) cudaFree(p->d_ticket);
   delete p;
   return SPX_OK;
 }
@@ -359,6 +383,13 @@ spx_status spx_helmholtz_adjoint(const spx_plan* p, const double* u, const doubl
   return run_op(p, OP_ADJ, SPX_F64, u, g, nullptr, nullptr, glam, gkap, nullptr, 0.0, stream);
 }
 
+spx_status spx_fwd_trans(const spx_plan* p, spx_dtype dt, const void* phys, void* coef, void* stream) {
+  if (p && p->E && (!coef || !phys)) return fail(SPX_ERR_INVALID_ARG, "fwd_trans: NULL buffer");
+  if (p && phys && phys == coef) return fail(SPX_ERR_INVALID_ARG, "fwd_trans: coef must not alias phys");
+  const void* aux = !p ? nullptr : (dt == SPX_F64 ? static_cast<const void*>(p->d_aux64) : p->d_aux32);
+  return run_op(p, OP_FWD, dt, phys, aux, nullptr, nullptr, coef, nullptr, nullptr, 0.0, stream);
+}
+
 spx_status spx_helmholtz_diag(const spx_plan* p, spx_dtype dt, double lambda, void* out, void* stream) {
   if (p && p->E && !out) return fail(SPX_ERR_INVALID_ARG, "helmholtz_diag: NULL buffer");
   return run_op(p, OP_DIAG, dt, nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, lambda, stream);
@@ -376,6 +407,7 @@ static float time_op(spx_plan* p, int op, spx_dtype dt, const void* in, void* ou
     o[1] = static_cast<char*>(out) + qbytes;
     o[2] = p->dim == 3 ? static_cast<char*>(out) + 2 * qbytes : nullptr;
   }
+  if (op == OP_FWD) in1 = dt == SPX_F64 ? static_cast<const void*>(p->d_aux64) : p->d_aux32;
   if (op == OP_ADJ) {
     in1 = in;
     o[1] = static_cast<char*>(out) + qbytes;

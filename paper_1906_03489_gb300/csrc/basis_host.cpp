@@ -203,4 +203,43 @@ void eo_tables(int P, int Q, double* tab) {
     }
 }
 
+// Inverse of the 1D mass matrix M1 = B^T diag(w) B (n x n, SPD) of order P on
+// Q GLL points, by Cholesky factorisation and two triangular solves per
+// column.  Row-major [n][n] into minv.
+void mass1d_inverse(int P, int Q, double* minv) {
+  const int n = P + 1;
+  std::vector<double> xi(Q), w(Q), B(Q * n), dB(Q * n), D(Q * Q);
+  basis_tables(P, Q, xi.data(), w.data(), B.data(), dB.data(), D.data());
+  std::vector<double> M(n * n, 0.0), L(n * n, 0.0);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double s = 0.0;
+      for (int i = 0; i < Q; ++i) s += B[i * n + a] * w[i] * B[i * n + b];
+      M[a * n + b] = s;
+    }
+  for (int j = 0; j < n; ++j) {
+    double d = M[j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+    L[j * n + j] = std::sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double s = M[i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = s / L[j * n + j];
+    }
+  }
+  std::vector<double> y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {  // L y = e_c
+      double s = i == c ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+      double s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * minv[k * n + c];
+      minv[i * n + c] = s / L[i * n + i];
+    }
+  }
+}
+
 }  // namespace spx

@@ -312,9 +312,79 @@ __global__ void assemble_atomic(const int32_t* __restrict__ l2g, const T* __rest
   }
 }
 
+// ---- integral: sum over elements and quadrature points of JW f -----------
+// One warp per element (elements warp, warp + all warps, ...), lanes over the
+// element's points; FP64 sums in a fixed order (per-thread partials, warp
+// shuffles, per-warp then per-block sums, and the last block to finish sums
+// the block partials), so the result is reproducible for a given GPU.
+constexpr int kIntThreads = 256;
+template <typename T>
+__global__ void __launch_bounds__(kIntThreads) integral_kernel(const T* __restrict__ f, const T* __restrict__ geom,
+                                                               const int64_t* __restrict__ quad_off, int64_t qd_uniform,
+                                                               int nf, int64_t E, double* partials,
+                                                               unsigned int* ticket, double* out) {
+  __shared__ double ws[kIntThreads / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  double acc = 0.0;
+  for (int64_t e = gw; e < E; e += nw) {
+    const int64_t q0 = quad_off ? quad_off[e] : e * qd_uniform;
+    const int64_t qd = quad_off ? quad_off[e + 1] - q0 : qd_uniform;
+    const T* jw = geom + int64_t(nf) * q0 + int64_t(nf - 1) * qd;
+    const T* fe = f + q0;
+    for (int64_t q = lane; q < qd; q += 32) acc = fma(static_cast<double>(jw[q]), static_cast<double>(fe[q]), acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) ws[w] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int i = 0; i < kIntThreads / 32; ++i) b += ws[i];
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double t = 0.0;
+  for (unsigned i = 0; i < gridDim.x; ++i) t += static_cast<volatile const double*>(partials)[i];
+  *out = t;
+  *ticket = 0;
+}
+
 }  // namespace spx
 
 using namespace spx;
+
+extern "C" spx_status spx_integral(const spx_plan* plan, spx_dtype dt, const void* phys, double* result,
+                                   void* stream) {
+  if (!plan || !result || (plan->n_quad && !phys)) return fail(SPX_ERR_INVALID_ARG, "integral: NULL argument");
+  if (dt != SPX_F64 && dt != SPX_F32) return fail(SPX_ERR_INVALID_ARG, "integral: bad dtype");
+  const void* geom = plan->geom[dt];
+  if (plan->E && !geom) return fail(SPX_ERR_INVALID_ARG, "integral: geometry not registered for this dtype");
+  const size_t a = dt == SPX_F64 ? 8 : 4;
+  if ((reinterpret_cast<uintptr_t>(phys) % a) || (reinterpret_cast<uintptr_t>(result) % 8))
+    return fail(SPX_ERR_INVALID_ARG, "integral: buffer not aligned to its element size");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nf = plan->dim == 3 ? 7 : 4;
+  const int Q = plan->uP + plan->qoff;
+  const int64_t qd = plan->uniform ? (plan->dim == 3 ? int64_t(Q) * Q * Q : int64_t(Q) * Q) : 0;
+  const int64_t* qoff = plan->uniform ? nullptr : plan->d_quad_off;
+  const int grid = plan->num_sms * kIntegralBlocksPerSM;
+  if (dt == SPX_F64)
+    integral_kernel<double><<<grid, kIntThreads, 0, st>>>(static_cast<const double*>(phys),
+                                                           static_cast<const double*>(geom), qoff, qd, nf, plan->E,
+                                                           plan->d_partials, plan->d_ticket, result);
+  else
+    integral_kernel<float><<<grid, kIntThreads, 0, st>>>(static_cast<const float*>(phys),
+                                                          static_cast<const float*>(geom), qoff, qd, nf, plan->E,
+                                                          plan->d_partials, plan->d_ticket, result);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e, "integral kernel launch");
+}
 
 extern "C" spx_status spx_geom_factors(const spx_plan* plan, const double* nodes, double* geom, double* dxi,
                                        double* xq, float* geom32, float* dxi32, void* stream) {

@@ -61,6 +61,10 @@ __device__ __forceinline__ int op_streams(const Prm& p, int P, int Q, StreamDesc
       s[k++] = {p.lam_f, qd, 1, 0, true, true};
       s[k++] = {p.kap_f, qd, 1, 0, true, true};
       break;
+    case OP_FWD:
+      s[k++] = {p.in0, qd, 1, 0, true, true};
+      s[k++] = {p.geom, qd, nf, (nf - 1) * qd, true, false};
+      break;
     case OP_DIAG:
       s[k++] = {p.geom, nf * qd, nf, 0, true, true};
       s[k++] = {p.lam_f, qd, 1, 0, true, true};
@@ -135,6 +139,7 @@ struct Ctx {
   const int64_t* gquad;   // [kMaxEB] quadrature offsets
   int ne, tid, nthr;
   int* tab_order;         // order whose tables are in work buffer 4 (shared)
+  T* extra;               // kFwdExtra values after the tile metadata (FwdTrans)
   bool has_lam, has_kap;
   T lam;
   __device__ const T* staged(int s, int j) const { return reinterpret_cast<const T*>(sm) + soff[s * kMaxEB + j]; }
@@ -849,6 +854,189 @@ __device__ void body_diag(const T* tab, const Ctx<T>& c, T* out, Rel release) {
 // ===========================================================================
 // The kernel.
 // ===========================================================================
+// ---- FwdTrans ---------------------------------------------------------------
+// Galerkin projection of quadrature-point values f onto the expansion (the
+// FwdTrans of §3.5, Listing lst:python): u_e = M_e^{-1} b_e with
+// b_e = IProduct(f)_e and M_e = Phi^T diag(JW) Phi the elemental mass matrix.
+// Solved per element by preconditioned CG, all elements of the tile in
+// lockstep with their own step lengths, matrix-free (M_e p = IProduct(JW
+// BwdTrans(p)) by sum-factorisation through shared memory).  Preconditioner:
+// K_e^{-1} = (1 / Jbar_e) (M1^{-1} (x) M1^{-1} (x) M1^{-1}), with M1 = B^T
+// diag(w) B the 1D mass matrix (host-inverted table `mi`) and Jbar_e =
+// sum_q JW_q / 2^d the element's mean Jacobian, since M_e = Jbar_e M1^{(x)d}
+// whenever det J is constant on the element: then one step solves it, and a
+// varying det J only adds steps.  An element stops at ||r|| <= tol ||b||
+// (1e-14 FP64, 1e-6 FP32) or after 64 steps.  Per-element dot products:
+// one warp per element, lanes in a fixed order (reproducible).
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// <a, b> over element e's ND modes (buffers [ne][WS], compact modal layout)
+template <typename T, int ND, int WS>
+__device__ __forceinline__ T elem_dot(const T* a, const T* b, int e, int lane) {
+  T s = T(0);
+  for (int m = lane; m < ND; m += 32) s = fma(a[e * WS + m], b[e * WS + m], s);
+  return warp_sum_t(s);
+}
+
+template <typename T, int DIM, int P, int Q>
+__device__ void body_fwd(const T* tab, const Ctx<T>& c, const T* __restrict__ mi_g, T* out) {
+  using S = Shape<T, DIM, P, Q>;
+  constexpr int n = S::n, S1 = S::S1, S2 = S::S2, WS = S::WS, ND = S::ND, QD = S::QD;
+  constexpr T kTol2 = sizeof(T) == 8 ? T(1e-28) : T(1e-12);
+  constexpr int kMaxIt = 64;
+  const T* B = tab;
+  T *W0 = c.work[0], *W1 = c.work[1], *X = c.work[2], *R = c.work[3], *Pd = c.work[4], *AP = c.work[5],
+    *Z = c.work[6];
+  T* jb = c.extra;          // 1 / Jbar_e
+  T* rz = jb + kMaxEB;      // <r, K^{-1} r>
+  T* bb = rz + kMaxEB;      // <b, b>
+  T* al = bb + kMaxEB;      // step length (0 once converged)
+  T* be = al + kMaxEB;      // direction update (< 0: converged)
+  T* mi = be + kMaxEB;      // [n][n]
+  const int ne = c.ne, tid = c.tid, nthr = c.nthr;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
+  BaseTable32 f{c.soff}, jw{c.soff + kMaxEB};
+  const T* sm = reinterpret_cast<const T*>(c.sm);
+  const T* nul = nullptr;
+  for (int t = tid; t < n * n; t += nthr) mi[t] = mi_g[t];
+  // b = IProduct(f) -> R
+  if constexpr (DIM == 3) {
+    contract_g<2, Q, Q, Q, n, true, 0, true, Q, Q * Q, S1, S2>(sm, f, sm, jw, W0, BaseStride{WS}, B, ne, tid, nthr);
+    SPX_SYNC();
+    contract_g<1, Q, Q, n, n, true, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
+                                                               BaseStride{WS}, B, ne, tid, nthr);
+    SPX_SYNC();
+    contract_g<0, Q, n, n, n, true, 0, false, S1, S2, n, n * n>(W1, BaseStride{WS}, nul, BaseStride{0}, R,
+                                                                 BaseStride{WS}, B, ne, tid, nthr);
+  } else {
+    contract_g<1, Q, Q, 1, n, true, 0, true, Q, 0, S1, 0>(sm, f, sm, jw, W0, BaseStride{WS}, B, ne, tid, nthr);
+    SPX_SYNC();
+    contract_g<0, Q, n, 1, n, true, 0, false, S1, 0, n, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, R,
+                                                           BaseStride{WS}, B, ne, tid, nthr);
+  }
+  for (int e = warp; e < ne; e += nwarp) {  // 1 / Jbar_e = 2^d / sum_q JW_q
+    const T* J = c.staged(1, e);
+    T s = T(0);
+    for (int q = lane; q < QD; q += 32) s += J[q];
+    s = warp_sum_t(s);
+    if (lane == 0) jb[e] = T(1 << DIM) / s;
+  }
+  SPX_SYNC();
+  // Z = (M1^{-1})^{(x)d} R (unscaled; the 1 / Jbar_e factor is applied by the callers)
+  auto precond = [&]() {
+    if constexpr (DIM == 3) {
+      contract_g<0, n, n, n, n, false, 0, false, n, n * n, n, n * n>(R, BaseStride{WS}, nul, BaseStride{0}, W0,
+                                                                     BaseStride{WS}, mi, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, n, n, n, n, false, 0, false, n, n * n, n, n * n>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
+                                                                     BaseStride{WS}, mi, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<2, n, n, n, n, false, 0, false, n, n * n, n, n * n>(W1, BaseStride{WS}, nul, BaseStride{0}, Z,
+                                                                     BaseStride{WS}, mi, ne, tid, nthr);
+    } else {
+      contract_g<0, n, n, 1, n, false, 0, false, n, 0, n, 0>(R, BaseStride{WS}, nul, BaseStride{0}, W0,
+                                                             BaseStride{WS}, mi, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, n, n, 1, n, false, 0, false, n, 0, n, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, Z,
+                                                             BaseStride{WS}, mi, ne, tid, nthr);
+    }
+    SPX_SYNC();
+  };
+  precond();
+  // X = 0, Z = K^{-1} R, Pd = Z; rz = <R, Z>, bb = <R, R>
+  for (int t = tid; t < ne * ND; t += nthr) {
+    const int e = t / ND, m = t - e * ND;
+    const T z = jb[e] * Z[e * WS + m];
+    X[e * WS + m] = T(0);
+    Z[e * WS + m] = z;
+    Pd[e * WS + m] = z;
+  }
+  SPX_SYNC();
+  for (int e = warp; e < ne; e += nwarp) {
+    const T a = elem_dot<T, ND, WS>(R, Z, e, lane), b2 = elem_dot<T, ND, WS>(R, R, e, lane);
+    if (lane == 0) {
+      rz[e] = a;
+      bb[e] = b2;
+      be[e] = b2 > T(0) ? T(0) : T(-1);   // a zero right-hand side is converged at x = 0
+    }
+  }
+  SPX_SYNC();
+  for (int it = 0; it < kMaxIt; ++it) {
+    // AP = M_e Pd: BwdTrans to the quadrature points (compact layout in W0), then IProduct of JW * u
+    if constexpr (DIM == 3) {
+      contract_g<0, n, n, n, Q, false, 0, false, n, n * n, S1, S2>(Pd, BaseStride{WS}, nul, BaseStride{0}, W0,
+                                                                    BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, Q, n, n, Q, false, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
+                                                                  BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<2, Q, Q, n, Q, false, 0, false, S1, S2, Q, Q * Q>(W1, BaseStride{WS}, nul, BaseStride{0}, W0,
+                                                                    BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<2, Q, Q, Q, n, true, 0, true, Q, Q * Q, S1, S2>(W0, BaseStride{WS}, sm, jw, W1, BaseStride{WS}, B,
+                                                                  ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, Q, Q, n, n, true, 0, false, S1, S2, S1, S2>(W1, BaseStride{WS}, nul, BaseStride{0}, W0,
+                                                                 BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<0, Q, n, n, n, true, 0, false, S1, S2, n, n * n>(W0, BaseStride{WS}, nul, BaseStride{0}, AP,
+                                                                   BaseStride{WS}, B, ne, tid, nthr);
+    } else {
+      contract_g<0, n, n, 1, Q, false, 0, false, n, 0, S1, 0>(Pd, BaseStride{WS}, nul, BaseStride{0}, W0,
+                                                              BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, Q, n, 1, Q, false, 0, false, S1, 0, Q, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
+                                                              BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, Q, Q, 1, n, true, 0, true, Q, 0, S1, 0>(W1, BaseStride{WS}, sm, jw, W0, BaseStride{WS}, B, ne,
+                                                            tid, nthr);
+      SPX_SYNC();
+      contract_g<0, Q, n, 1, n, true, 0, false, S1, 0, n, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, AP,
+                                                             BaseStride{WS}, B, ne, tid, nthr);
+    }
+    SPX_SYNC();
+    for (int e = warp; e < ne; e += nwarp) {
+      const T pap = elem_dot<T, ND, WS>(Pd, AP, e, lane);
+      if (lane == 0) al[e] = be[e] < T(0) ? T(0) : rz[e] / pap;
+    }
+    SPX_SYNC();
+    for (int t = tid; t < ne * ND; t += nthr) {
+      const int e = t / ND, m = t - e * ND;
+      X[e * WS + m] = fma(al[e], Pd[e * WS + m], X[e * WS + m]);
+      R[e * WS + m] = fma(-al[e], AP[e * WS + m], R[e * WS + m]);
+    }
+    SPX_SYNC();
+    precond();
+    bool active = false;
+    for (int e = warp; e < ne; e += nwarp) {
+      const T rr = elem_dot<T, ND, WS>(R, R, e, lane);
+      const T rzn = jb[e] * elem_dot<T, ND, WS>(R, Z, e, lane);
+      if (lane == 0) {
+        if (be[e] >= T(0) && rr <= kTol2 * bb[e]) be[e] = T(-1);
+        if (be[e] >= T(0)) {
+          be[e] = rzn / rz[e];
+          rz[e] = rzn;
+          active = true;
+        }
+      }
+    }
+    if (!__syncthreads_or(active)) break;
+    for (int t = tid; t < ne * ND; t += nthr) {
+      const int e = t / ND, m = t - e * ND;
+      if (be[e] >= T(0)) Pd[e * WS + m] = fma(be[e], Pd[e * WS + m], jb[e] * Z[e * WS + m]);
+    }
+    SPX_SYNC();
+  }
+  for (int t = tid; t < ne * ND; t += nthr) {
+    const int e = t / ND, m = t - e * ND;
+    out[c.gcoef[e] + m] = X[e * WS + m];
+  }
+}
+
 template <typename T, int DIM, int OP, int P, int Q, class Prm, class Rel>
 __device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel) {
   const T* tab = p.tab + Prm::Layout::off(P);
@@ -858,6 +1046,7 @@ __device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel)
   else if constexpr (OP == OP_HELM && DIM == 3) body_helm_role<T, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_HELM) body_helm<T, DIM, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_ADJ) body_adj<T, DIM, P, Q>(tab, c, p.out0, p.out1, rel);
+  else if constexpr (OP == OP_FWD) body_fwd<T, DIM, P, Q>(tab, c, p.in1 + mass1d_off(P), p.out0);
   else body_diag<T, DIM, P, Q>(tab, c, p.out0, rel);
 }
 
@@ -897,6 +1086,7 @@ __global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KPar
   for (int w = 0; w < 8; ++w) c.work[w] = reinterpret_cast<T*>(sm + p.work_base + size_t(w) * p.work_bytes);
   c.soff = soff;
   c.tab_order = tab_order;
+  c.extra = reinterpret_cast<T*>(sm + p.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8 + 16);
   c.gcoef = gcoef;
   c.gquad = gquad;
   c.tid = tid;

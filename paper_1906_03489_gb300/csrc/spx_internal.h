@@ -53,6 +53,14 @@ struct spx_plan {
   int64_t* d_quad_off = nullptr;
   int32_t* d_ids = nullptr;
   int* d_status = nullptr;
+  // small device buffers (owned): per-order inverse 1D mass matrices (FP64 at
+  // aux64, FP32 at aux32, order P at offset aux_off[P]) for FwdTrans, and the
+  // partial sums of spx_integral
+  double* d_aux64 = nullptr;
+  float* d_aux32 = nullptr;
+  int aux_off[spx::kMaxP1 + 1] = {};
+  double* d_partials = nullptr;
+  unsigned int* d_ticket = nullptr;
   // per operator and precision
   spx::LaunchCfg cfg[spx::OP_KINDS][2];
   spx::TileList tiles[spx::OP_KINDS][2];
@@ -94,7 +102,8 @@ spx_status ensure_tiles(spx_plan* plan, int op, int dtype);
   SPX_DECL_LAUNCH(TN, DIM, 2)     \
   SPX_DECL_LAUNCH(TN, DIM, 3)     \
   SPX_DECL_LAUNCH(TN, DIM, 4)     \
-  SPX_DECL_LAUNCH(TN, DIM, 5)
+  SPX_DECL_LAUNCH(TN, DIM, 5)     \
+  SPX_DECL_LAUNCH(TN, DIM, 6)
 SPX_DECL_ALL_OPS(f64, 2)
 SPX_DECL_ALL_OPS(f64, 3)
 SPX_DECL_ALL_OPS(f32, 2)
@@ -116,5 +125,12 @@ spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* 
 
 // Even-odd coefficients appended to a per-order table (EOLayout).
 void eo_tables(int P, int Q, double* tab);
+
+// Blocks per SM of the spx_integral reduction (fixed: its sums are
+// reproducible); the plan's partials buffer holds one FP64 value per block.
+constexpr int kIntegralBlocksPerSM = 4;
+
+// Inverse of the 1D mass matrix B^T diag(w) B of order P on Q points, [n][n].
+void mass1d_inverse(int P, int Q, double* minv);
 
 }  // namespace spx

@@ -404,6 +404,15 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
                                    "tile_eb_threads_stages": list(plan.get_tile("fwd_trans", dt, P)),
                                    "max_err_vs_input_coefficients": (cf.double() - torch.tensor(coef, device="cuda")
                                                                      ).abs().max().item()}
+        if dt == torch.float64:   # adaptive-order sensor (FP64): reads the coefficients and JW, writes one value per element
+            cc = torch.tensor(coef, device="cuda")
+            so = torch.empty(plan.E, dtype=torch.float64, device="cuda")
+            plan.autotune("sensor", dt, cc, so, reps=3)
+            ms = timed(lambda: spx.sensor(plan, cc, so), reps, stream)
+            nbytes = E * (125 + Q ** 3 + 1) * sz
+            ops["sensor_f64"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+                                 "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4),
+                                 "tile_eb_threads_stages": list(plan.get_tile("sensor", dt, P))}
         res = torch.empty((), dtype=torch.float64, device="cuda")
         ms = timed(lambda: spx.integral(plan, f, res), reps, stream)
         nbytes = E * 2 * Q ** 3 * sz
@@ -525,7 +534,11 @@ def run_case(a):
         dt = torch.float32 if a.precision != "f64" else torch.float64
         u = torch.tensor(coef, device="cuda", dtype=dt)
         y = torch.empty_like(u)
-        plan.autotune("helmholtz", dt, u, y, reps=2)
+        if a.varp_tiles:   # elements per tile of orders 2..8 (no autotuning: a reproducible launch)
+            for P, eb in zip(range(2, 9), (int(x) for x in a.varp_tiles.split(","))):
+                plan.set_tile("helmholtz", dt, eb, 512, 0 if dt == torch.float32 else 2, order=P)
+        else:
+            plan.autotune("helmholtz", dt, u, y, reps=2)
         ms = timed(lambda: spx.helmholtz(plan, u, out=y), max(1, a.steps), stream)
         print(json.dumps({"case": "varp", "workload": "hex3d_24_varp", "dtype": str(dt), "ms": round(ms, 4),
                           "tiles": {int(P): plan.get_tile("helmholtz", dt, int(P))[0]
@@ -601,6 +614,7 @@ def main():
                     help="bench: the benchmark line; cg / varp: one short run for profiling")
     ap.add_argument("--precision", default="f32_reliable", help="cg: f64 | f32_refine | f32_reliable; varp: f32 | f64")
     ap.add_argument("--cg-maxit", type=int, default=30)
+    ap.add_argument("--varp-tiles", default=None, help="varp: elements per tile of orders 2..8, e.g. 24,16,8,4,3,2,2")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
     if a.case != "bench":

@@ -78,7 +78,8 @@ typedef enum {
   SPX_OP_HELMHOLTZ_ADJOINT = 4,
   SPX_OP_HELMHOLTZ_DIAG = 5,
   SPX_OP_FWD_TRANS = 6,
-  SPX_OP_COUNT = 7
+  SPX_OP_SENSOR = 7,
+  SPX_OP_COUNT = 8
 } spx_op;
 
 typedef struct spx_plan spx_plan;
@@ -247,6 +248,28 @@ spx_status spx_fwd_trans(const spx_plan *plan, spx_dtype dtype, const void *phys
  * FP64 in a fixed order (reproducible).  Calls on one plan that overlap on the
  * GPU race on the plan's partial-sum buffer: serialise them.  Needs geom. */
 spx_status spx_integral(const spx_plan *plan, spx_dtype dtype, const void *phys, double *result, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Adaptive polynomial order (§4.2, adaptive polynomial order paragraph).
+ * ------------------------------------------------------------------------- */
+
+/* Element error sensor S_e = ||u_P - u_{P-1}||^2 / ||u_P||^2 of §4.2, for every
+ * element of order P: u_P the expansion with coefficients `coef`, u_{P-1}
+ * its L2 projection onto polynomials of degree <= P-1 per direction, norms
+ * L2 on the element (quadrature with w det J).  u_{P-1} is computed in the
+ * span of the order-P modes that avoid the degree-P bubble in every
+ * direction (the same space), by preconditioned CG per element in one launch;
+ * S_e = 0 where u_P = 0.  FP64 only.  coef: device [n_coef]; S: device out
+ * [n_elem], indexed by element.  Orders >= 2 (SPX_ERR_UNSUPPORTED if an
+ * element has order 1).  Needs FP64 geom. */
+spx_status spx_sensor(const spx_plan *plan, const double *coef, double *S, void *stream);
+
+/* Order update of §4.2 (host): new_orders[e] = orders[e] + 1 where S[e] >
+ * upper, orders[e] - 1 where S[e] < lower, else unchanged, then clamped to
+ * [p_min, p_max] (2 <= p_min <= p_max <= 8).  All arrays host, n_elem
+ * entries.  The new orders define the next variable-order plan. */
+spx_status spx_adapt_orders(int64_t n_elem, const double *S, const int32_t *orders, double lower, double upper,
+                            int p_min, int p_max, int32_t *new_orders);
 
 /* Diagonal of the elemental Helmholtz matrices, diag(H_e)_l for every local
  * mode (the Jacobi preconditioner before assembly).  out: device [n_coef]. */

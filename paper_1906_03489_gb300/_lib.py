@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libspx.so")
 
 SPX_F64, SPX_F32 = 0, 1
 OPS = {"bwd_trans": 0, "iproduct": 1, "phys_deriv": 2, "helmholtz": 3, "helmholtz_adjoint": 4,
-       "helmholtz_diag": 5, "fwd_trans": 6}
+       "helmholtz_diag": 5, "fwd_trans": 6, "sensor": 7}
 
 STATUS = {
     0: "SPX_OK", 1: "SPX_ERR_INVALID_ARG", 2: "SPX_ERR_UNSUPPORTED", 3: "SPX_ERR_CUDA",
@@ -65,6 +65,8 @@ SIGNATURES = {
     "spx_helmholtz_diag": (I32, [P, I32, D, P, P]),
     "spx_fwd_trans": (I32, [P, I32, P, P, P]),
     "spx_integral": (I32, [P, I32, P, P, P]),
+    "spx_sensor": (I32, [P, P, P, P]),
+    "spx_adapt_orders": (I32, [I64, P, P, D, D, I32, I32, P]),
     "spx_gather": (I32, [P, I32, P, I64, P, P, P]),
     "spx_assemble": (I32, [P, I32, P, I64, P, P, P]),
     "spx_cg_workspace_bytes": (I32, [P, I64, C.POINTER(CgOpts), C.POINTER(C.c_size_t)]),

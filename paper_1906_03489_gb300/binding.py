@@ -12,7 +12,7 @@ import torch
 from ._lib import SPX_F32, SPX_F64, OPS, CgOpts, CgResult, PlanDesc, SpxError, check, lib
 
 __all__ = ["Plan", "basis_tables", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz", "fwd_trans",
-           "integral",
+           "integral", "sensor", "adapt_orders",
            "helmholtz_adjoint", "helmholtz_diag", "gather", "assemble", "cg_workspace_bytes", "cg_solve", "SpxError"]
 
 
@@ -160,6 +160,26 @@ def integral(plan, f, out=None):
     out = torch.empty((), dtype=torch.float64, device=f.device) if out is None else out
     check(lib().spx_integral(plan.handle, _code(f.dtype), _p(f), _p(out), _stream()))
     return out
+
+
+def sensor(plan, coef, out=None):
+    """Adaptive-order error sensor S_e per element (FP64 device tensor [n_elem])."""
+    _dev(coef, "coef")
+    if coef.dtype != torch.float64:
+        raise TypeError("the sensor is FP64 only")
+    out = torch.empty(plan.E, dtype=torch.float64, device=coef.device) if out is None else out
+    check(lib().spx_sensor(plan.handle, _p(coef), _p(out), _stream()))
+    return out
+
+
+def adapt_orders(S, orders, lower, upper, p_min=2, p_max=8):
+    """New per-element orders from the sensor values (host int32 numpy array)."""
+    S = np.ascontiguousarray(S.detach().cpu().numpy() if isinstance(S, torch.Tensor) else S, dtype=np.float64)
+    orders = np.ascontiguousarray(orders, dtype=np.int32)
+    new = np.empty_like(orders)
+    check(lib().spx_adapt_orders(S.size, S.ctypes.data_as(C.c_void_p), orders.ctypes.data_as(C.c_void_p),
+                                 float(lower), float(upper), int(p_min), int(p_max), new.ctypes.data_as(C.c_void_p)))
+    return new
 
 
 def phys_deriv(plan, f, outs=None):

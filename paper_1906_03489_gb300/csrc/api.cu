@@ -82,7 +82,8 @@ spx_status launch_op(const LaunchReq& r) {
   case DT * 100 + DIM * 10 + OP: return launch_##TN##_##DIM##_##OP(r);
 #define SPX_CASES(DT, TN, DIM) \
   SPX_CASE(DT, TN, DIM, 0) SPX_CASE(DT, TN, DIM, 1) SPX_CASE(DT, TN, DIM, 2) \
-  SPX_CASE(DT, TN, DIM, 3) SPX_CASE(DT, TN, DIM, 4) SPX_CASE(DT, TN, DIM, 5) SPX_CASE(DT, TN, DIM, 6)
+  SPX_CASE(DT, TN, DIM, 3) SPX_CASE(DT, TN, DIM, 4) SPX_CASE(DT, TN, DIM, 5) SPX_CASE(DT, TN, DIM, 6) \
+  SPX_CASE(DT, TN, DIM, 7)
     SPX_CASES(0, f64, 2)
     SPX_CASES(0, f64, 3)
     SPX_CASES(1, f32, 2)
@@ -193,14 +194,12 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
   if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return cleanup(e, "cudaMalloc(status)");
   if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return cleanup(e, "cudaMemset(status)");
   {  // inverse 1D mass matrices of every order (FwdTrans preconditioner)
-    std::vector<double> a64;
+    // full inverses of orders 1..8, then the sensor's restricted ones (order 1: unused zeros)
+    std::vector<double> a64(2 * mass1d_off(kMaxP + 1), 0.0);
     for (int P = 1; P <= kMaxP; ++P) {
-      p->aux_off[P] = static_cast<int>(a64.size());
-      const int n = P + 1;
-      a64.resize(a64.size() + n * n);
-      mass1d_inverse(P, P + qoff, a64.data() + p->aux_off[P]);
+      mass1d_inverse(P, P + qoff, a64.data() + mass1d_off(P));
+      if (P >= 2) mass1d_inverse(P, P + qoff, a64.data() + mass1d_off(kMaxP + 1) + mass1d_off(P), true);
     }
-    p->aux_off[kMaxP + 1] = static_cast<int>(a64.size());
     std::vector<float> a32(a64.begin(), a64.end());
     if ((e = cudaMalloc(&p->d_aux64, a64.size() * sizeof(double))) != cudaSuccess) return cleanup(e, "cudaMalloc(aux)");
     if ((e = cudaMalloc(&p->d_aux32, a32.size() * sizeof(float))) != cudaSuccess) return cleanup(e, "cudaMalloc(aux)");
@@ -390,6 +389,28 @@ spx_status spx_fwd_trans(const spx_plan* p, spx_dtype dt, const void* phys, void
   return run_op(p, OP_FWD, dt, phys, aux, nullptr, nullptr, coef, nullptr, nullptr, 0.0, stream);
 }
 
+spx_status spx_sensor(const spx_plan* p, const double* coef, double* S, void* stream) {
+  if (p && p->E && (!coef || !S)) return fail(SPX_ERR_INVALID_ARG, "sensor: NULL buffer");
+  if (p && p->present[1]) return fail(SPX_ERR_UNSUPPORTED, "sensor: elements of order 1 (the sensor needs P >= 2)");
+  return run_op(p, OP_SENSOR, SPX_F64, coef, p ? p->d_aux64 : nullptr, nullptr, nullptr, S, nullptr, nullptr, 0.0,
+                stream);
+}
+
+spx_status spx_adapt_orders(int64_t n_elem, const double* S, const int32_t* orders, double lower, double upper,
+                            int p_min, int p_max, int32_t* new_orders) {
+  if (n_elem < 0 || (n_elem && (!S || !orders || !new_orders)))
+    return fail(SPX_ERR_INVALID_ARG, "adapt_orders: bad argument");
+  if (p_min < 2 || p_max > kMaxP || p_min > p_max || !(lower <= upper))
+    return fail(SPX_ERR_INVALID_ARG, "adapt_orders: need 2 <= p_min <= p_max <= 8 and lower <= upper");
+  for (int64_t e = 0; e < n_elem; ++e) {
+    int P = orders[e];
+    if (S[e] > upper) ++P;
+    else if (S[e] < lower) --P;
+    new_orders[e] = std::min(p_max, std::max(p_min, P));
+  }
+  return SPX_OK;
+}
+
 spx_status spx_helmholtz_diag(const spx_plan* p, spx_dtype dt, double lambda, void* out, void* stream) {
   if (p && p->E && !out) return fail(SPX_ERR_INVALID_ARG, "helmholtz_diag: NULL buffer");
   return run_op(p, OP_DIAG, dt, nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, lambda, stream);
@@ -407,7 +428,7 @@ static float time_op(spx_plan* p, int op, spx_dtype dt, const void* in, void* ou
     o[1] = static_cast<char*>(out) + qbytes;
     o[2] = p->dim == 3 ? static_cast<char*>(out) + 2 * qbytes : nullptr;
   }
-  if (op == OP_FWD) in1 = dt == SPX_F64 ? static_cast<const void*>(p->d_aux64) : p->d_aux32;
+  if (op == OP_FWD || op == OP_SENSOR) in1 = dt == SPX_F64 ? static_cast<const void*>(p->d_aux64) : p->d_aux32;
   if (op == OP_ADJ) {
     in1 = in;
     o[1] = static_cast<char*>(out) + qbytes;

@@ -206,15 +206,21 @@ void eo_tables(int P, int Q, double* tab) {
 // Inverse of the 1D mass matrix M1 = B^T diag(w) B (n x n, SPD) of order P on
 // Q GLL points, by Cholesky factorisation and two triangular solves per
 // column.  Row-major [n][n] into minv.
-void mass1d_inverse(int P, int Q, double* minv) {
-  const int n = P + 1;
-  std::vector<double> xi(Q), w(Q), B(Q * n), dB(Q * n), D(Q * Q);
+void mass1d_inverse(int P, int Q, double* minv, bool restricted) {
+  const int nf = P + 1;
+  std::vector<double> xi(Q), w(Q), B(Q * nf), dB(Q * nf), D(Q * Q);
   basis_tables(P, Q, xi.data(), w.data(), B.data(), dB.data(), D.data());
-  std::vector<double> M(n * n, 0.0), L(n * n, 0.0);
+  std::fill(minv, minv + nf * nf, 0.0);
+  // kept modes: all, or all but the degree-P bubble (index P - 1)
+  std::vector<int> keep;
+  for (int a = 0; a < nf; ++a)
+    if (!restricted || a != P - 1) keep.push_back(a);
+  const int n = static_cast<int>(keep.size());
+  std::vector<double> M(n * n, 0.0), L(n * n, 0.0), Mi(n * n, 0.0);
   for (int a = 0; a < n; ++a)
     for (int b = 0; b < n; ++b) {
       double s = 0.0;
-      for (int i = 0; i < Q; ++i) s += B[i * n + a] * w[i] * B[i * n + b];
+      for (int i = 0; i < Q; ++i) s += B[i * nf + keep[a]] * w[i] * B[i * nf + keep[b]];
       M[a * n + b] = s;
     }
   for (int j = 0; j < n; ++j) {
@@ -236,10 +242,12 @@ void mass1d_inverse(int P, int Q, double* minv) {
     }
     for (int i = n - 1; i >= 0; --i) {  // L^T x = y
       double s = y[i];
-      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * minv[k * n + c];
-      minv[i * n + c] = s / L[i * n + i];
+      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * Mi[k * n + c];
+      Mi[i * n + c] = s / L[i * n + i];
     }
   }
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) minv[keep[a] * nf + keep[b]] = Mi[a * n + b];
 }
 
 }  // namespace spx

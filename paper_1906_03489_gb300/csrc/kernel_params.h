@@ -8,18 +8,21 @@ constexpr int kMaxEB = 64;  // elements per tile (upper bound)
 constexpr int kMaxP = 8;    // highest supported order
 constexpr int kMaxP1 = 9;   // orders 0..8 index per-order tables
 
-enum OpKind { OP_BWD = 0, OP_IPROD = 1, OP_DERIV = 2, OP_HELM = 3, OP_ADJ = 4, OP_DIAG = 5, OP_FWD = 6, OP_KINDS = 7 };
+enum OpKind {
+  OP_BWD = 0, OP_IPROD = 1, OP_DERIV = 2, OP_HELM = 3, OP_ADJ = 4, OP_DIAG = 5, OP_FWD = 6, OP_SENSOR = 7, OP_KINDS = 8
+};
 
 // Offset of order P's [n][n] inverse 1D mass matrix in the per-order table
-// array (orders 1, 2, ... stored one after the other).
+// array (orders 1, 2, ... stored one after the other; the sensor's restricted
+// inverses follow at mass1d_off(kMaxP + 1)).
 __host__ __device__ constexpr int mass1d_off(int P) {
   int o = 0;
   for (int p = 1; p < P; ++p) o += (p + 1) * (p + 1);
   return o;
 }
-// Values of the FwdTrans body's scratch region after the tile metadata:
-// five per-element scalars and one order's [n][n] table.
-constexpr int kFwdExtra = 5 * kMaxEB + 81;
+// Values of the FwdTrans / sensor body's scratch region after the tile
+// metadata: six per-element scalars and one order's [n][n] table.
+constexpr int kFwdExtra = 6 * kMaxEB + 81;
 
 // A tile: `count` elements of order P.  contig != 0: the elements are
 // id(first), id(first)+1, ...; else ids[first + j].  Without an id array

@@ -65,6 +65,10 @@ __device__ __forceinline__ int op_streams(const Prm& p, int P, int Q, StreamDesc
       s[k++] = {p.in0, qd, 1, 0, true, true};
       s[k++] = {p.geom, qd, nf, (nf - 1) * qd, true, false};
       break;
+    case OP_SENSOR:
+      s[k++] = {p.in0, nd, 1, 0, false, true};
+      s[k++] = {p.geom, qd, nf, (nf - 1) * qd, true, false};
+      break;
     case OP_DIAG:
       s[k++] = {p.geom, nf * qd, nf, 0, true, true};
       s[k++] = {p.lam_f, qd, 1, 0, true, true};
@@ -882,7 +886,16 @@ __device__ __forceinline__ T elem_dot(const T* a, const T* b, int e, int lane) {
   return warp_sum_t(s);
 }
 
-template <typename T, int DIM, int P, int Q>
+// SENSOR = false: FwdTrans (above).  SENSOR = true: the adaptive-order sensor
+// of §4.2, S_e = ||u_P - u_{P-1}||^2 / ||u_P||^2 (L2 norms by the element's
+// quadrature, w det J): the input is the coefficients u_P, u_{P-1} is the L2
+// projection onto degree <= P-1, i.e. onto the order-P modes that avoid the
+// top bubble index P-1 in every direction (which span that space), computed
+// by the same PCG restricted to those modes (the table `mi` is then the
+// inverse of the restricted 1D mass matrix, zero on row and column P-1); then
+// S_e = d^T M_e d / u^T M_e u with d = u_P - u_{P-1} (0 where u_P = 0),
+// written to out[e] (the metadata slot gquad holds element ids for this op).
+template <typename T, int DIM, int P, int Q, bool SENSOR = false>
 __device__ void body_fwd(const T* tab, const Ctx<T>& c, const T* __restrict__ mi_g, T* out) {
   using S = Shape<T, DIM, P, Q>;
   constexpr int n = S::n, S1 = S::S1, S2 = S::S2, WS = S::WS, ND = S::ND, QD = S::QD;
@@ -893,39 +906,58 @@ __device__ void body_fwd(const T* tab, const Ctx<T>& c, const T* __restrict__ mi
     *Z = c.work[6];
   T* jb = c.extra;          // 1 / Jbar_e
   T* rz = jb + kMaxEB;      // <r, K^{-1} r>
-  T* bb = rz + kMaxEB;      // <b, b>
+  T* bb = rz + kMaxEB;      // <b, b>  (sensor: later u^T M u)
   T* al = bb + kMaxEB;      // step length (0 once converged)
   T* be = al + kMaxEB;      // direction update (< 0: converged)
-  T* mi = be + kMaxEB;      // [n][n]
+  T* uMu = be + kMaxEB;     // (sensor) u^T M u
+  T* mi = uMu + kMaxEB;     // [n][n]
   const int ne = c.ne, tid = c.tid, nthr = c.nthr;
   const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
-  BaseTable32 f{c.soff}, jw{c.soff + kMaxEB};
+  BaseTable32 in0{c.soff}, jw{c.soff + kMaxEB};
   const T* sm = reinterpret_cast<const T*>(c.sm);
   const T* nul = nullptr;
+  // mode m kept in the restricted space (sensor): no index equal to P - 1
+  auto kept = [](int m) {
+    const int a = m % n, b = (m / n) % n, q = DIM == 3 ? m / (n * n) : 0;
+    return !(a == P - 1 || b == P - 1 || (DIM == 3 && q == P - 1));
+  };
   for (int t = tid; t < n * n; t += nthr) mi[t] = mi_g[t];
-  // b = IProduct(f) -> R
-  if constexpr (DIM == 3) {
-    contract_g<2, Q, Q, Q, n, true, 0, true, Q, Q * Q, S1, S2>(sm, f, sm, jw, W0, BaseStride{WS}, B, ne, tid, nthr);
-    SPX_SYNC();
-    contract_g<1, Q, Q, n, n, true, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
-                                                               BaseStride{WS}, B, ne, tid, nthr);
-    SPX_SYNC();
-    contract_g<0, Q, n, n, n, true, 0, false, S1, S2, n, n * n>(W1, BaseStride{WS}, nul, BaseStride{0}, R,
+  // AP = M_e v for a modal vector v (element base vb(e)): BwdTrans to the
+  // quadrature points (compact layout in W0), then IProduct of JW * u
+  auto mass_apply = [&](const T* v, auto vb) {
+    if constexpr (DIM == 3) {
+      contract_g<0, n, n, n, Q, false, 0, false, n, n * n, S1, S2>(v, vb, nul, BaseStride{0}, W0, BaseStride{WS}, B,
+                                                                    ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, Q, n, n, Q, false, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
+                                                                  BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<2, Q, Q, n, Q, false, 0, false, S1, S2, Q, Q * Q>(W1, BaseStride{WS}, nul, BaseStride{0}, W0,
+                                                                    BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<2, Q, Q, Q, n, true, 0, true, Q, Q * Q, S1, S2>(W0, BaseStride{WS}, sm, jw, W1, BaseStride{WS}, B,
+                                                                  ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, Q, Q, n, n, true, 0, false, S1, S2, S1, S2>(W1, BaseStride{WS}, nul, BaseStride{0}, W0,
                                                                  BaseStride{WS}, B, ne, tid, nthr);
-  } else {
-    contract_g<1, Q, Q, 1, n, true, 0, true, Q, 0, S1, 0>(sm, f, sm, jw, W0, BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<0, Q, n, n, n, true, 0, false, S1, S2, n, n * n>(W0, BaseStride{WS}, nul, BaseStride{0}, AP,
+                                                                   BaseStride{WS}, B, ne, tid, nthr);
+    } else {
+      contract_g<0, n, n, 1, Q, false, 0, false, n, 0, S1, 0>(v, vb, nul, BaseStride{0}, W0, BaseStride{WS}, B, ne,
+                                                              tid, nthr);
+      SPX_SYNC();
+      contract_g<1, Q, n, 1, Q, false, 0, false, S1, 0, Q, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
+                                                              BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<1, Q, Q, 1, n, true, 0, true, Q, 0, S1, 0>(W1, BaseStride{WS}, sm, jw, W0, BaseStride{WS}, B, ne,
+                                                            tid, nthr);
+      SPX_SYNC();
+      contract_g<0, Q, n, 1, n, true, 0, false, S1, 0, n, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, AP,
+                                                             BaseStride{WS}, B, ne, tid, nthr);
+    }
     SPX_SYNC();
-    contract_g<0, Q, n, 1, n, true, 0, false, S1, 0, n, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, R,
-                                                           BaseStride{WS}, B, ne, tid, nthr);
-  }
-  for (int e = warp; e < ne; e += nwarp) {  // 1 / Jbar_e = 2^d / sum_q JW_q
-    const T* J = c.staged(1, e);
-    T s = T(0);
-    for (int q = lane; q < QD; q += 32) s += J[q];
-    s = warp_sum_t(s);
-    if (lane == 0) jb[e] = T(1 << DIM) / s;
-  }
-  SPX_SYNC();
+  };
   // Z = (M1^{-1})^{(x)d} R (unscaled; the 1 / Jbar_e factor is applied by the callers)
   auto precond = [&]() {
     if constexpr (DIM == 3) {
@@ -946,6 +978,46 @@ __device__ void body_fwd(const T* tab, const Ctx<T>& c, const T* __restrict__ mi
     }
     SPX_SYNC();
   };
+  if constexpr (SENSOR) {
+    // b = restriction of M_e u_P; u^T M u for the denominator
+    mass_apply(sm, in0);
+    for (int e = warp; e < ne; e += nwarp) {
+      const T* u = c.staged(0, e);
+      T s = T(0);
+      for (int m = lane; m < ND; m += 32) s = fma(u[m], AP[e * WS + m], s);
+      s = warp_sum_t(s);
+      if (lane == 0) uMu[e] = s;
+    }
+    for (int t = tid; t < ne * ND; t += nthr) {
+      const int e = t / ND, m = t - e * ND;
+      R[e * WS + m] = kept(m) ? AP[e * WS + m] : T(0);
+    }
+  } else {
+    // b = IProduct(f) -> R
+    if constexpr (DIM == 3) {
+      contract_g<2, Q, Q, Q, n, true, 0, true, Q, Q * Q, S1, S2>(sm, in0, sm, jw, W0, BaseStride{WS}, B, ne, tid,
+                                                                  nthr);
+      SPX_SYNC();
+      contract_g<1, Q, Q, n, n, true, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
+                                                                 BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<0, Q, n, n, n, true, 0, false, S1, S2, n, n * n>(W1, BaseStride{WS}, nul, BaseStride{0}, R,
+                                                                   BaseStride{WS}, B, ne, tid, nthr);
+    } else {
+      contract_g<1, Q, Q, 1, n, true, 0, true, Q, 0, S1, 0>(sm, in0, sm, jw, W0, BaseStride{WS}, B, ne, tid, nthr);
+      SPX_SYNC();
+      contract_g<0, Q, n, 1, n, true, 0, false, S1, 0, n, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, R,
+                                                             BaseStride{WS}, B, ne, tid, nthr);
+    }
+  }
+  for (int e = warp; e < ne; e += nwarp) {  // 1 / Jbar_e = 2^d / sum_q JW_q
+    const T* J = c.staged(1, e);
+    T s = T(0);
+    for (int q = lane; q < QD; q += 32) s += J[q];
+    s = warp_sum_t(s);
+    if (lane == 0) jb[e] = T(1 << DIM) / s;
+  }
+  SPX_SYNC();
   precond();
   // X = 0, Z = K^{-1} R, Pd = Z; rz = <R, Z>, bb = <R, R>
   for (int t = tid; t < ne * ND; t += nthr) {
@@ -966,39 +1038,14 @@ __device__ void body_fwd(const T* tab, const Ctx<T>& c, const T* __restrict__ mi
   }
   SPX_SYNC();
   for (int it = 0; it < kMaxIt; ++it) {
-    // AP = M_e Pd: BwdTrans to the quadrature points (compact layout in W0), then IProduct of JW * u
-    if constexpr (DIM == 3) {
-      contract_g<0, n, n, n, Q, false, 0, false, n, n * n, S1, S2>(Pd, BaseStride{WS}, nul, BaseStride{0}, W0,
-                                                                    BaseStride{WS}, B, ne, tid, nthr);
+    mass_apply(Pd, BaseStride{WS});
+    if constexpr (SENSOR) {   // restrict to the kept modes
+      for (int t = tid; t < ne * ND; t += nthr) {
+        const int e = t / ND, m = t - e * ND;
+        if (!kept(m)) AP[e * WS + m] = T(0);
+      }
       SPX_SYNC();
-      contract_g<1, Q, n, n, Q, false, 0, false, S1, S2, S1, S2>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
-                                                                  BaseStride{WS}, B, ne, tid, nthr);
-      SPX_SYNC();
-      contract_g<2, Q, Q, n, Q, false, 0, false, S1, S2, Q, Q * Q>(W1, BaseStride{WS}, nul, BaseStride{0}, W0,
-                                                                    BaseStride{WS}, B, ne, tid, nthr);
-      SPX_SYNC();
-      contract_g<2, Q, Q, Q, n, true, 0, true, Q, Q * Q, S1, S2>(W0, BaseStride{WS}, sm, jw, W1, BaseStride{WS}, B,
-                                                                  ne, tid, nthr);
-      SPX_SYNC();
-      contract_g<1, Q, Q, n, n, true, 0, false, S1, S2, S1, S2>(W1, BaseStride{WS}, nul, BaseStride{0}, W0,
-                                                                 BaseStride{WS}, B, ne, tid, nthr);
-      SPX_SYNC();
-      contract_g<0, Q, n, n, n, true, 0, false, S1, S2, n, n * n>(W0, BaseStride{WS}, nul, BaseStride{0}, AP,
-                                                                   BaseStride{WS}, B, ne, tid, nthr);
-    } else {
-      contract_g<0, n, n, 1, Q, false, 0, false, n, 0, S1, 0>(Pd, BaseStride{WS}, nul, BaseStride{0}, W0,
-                                                              BaseStride{WS}, B, ne, tid, nthr);
-      SPX_SYNC();
-      contract_g<1, Q, n, 1, Q, false, 0, false, S1, 0, Q, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, W1,
-                                                              BaseStride{WS}, B, ne, tid, nthr);
-      SPX_SYNC();
-      contract_g<1, Q, Q, 1, n, true, 0, true, Q, 0, S1, 0>(W1, BaseStride{WS}, sm, jw, W0, BaseStride{WS}, B, ne,
-                                                            tid, nthr);
-      SPX_SYNC();
-      contract_g<0, Q, n, 1, n, true, 0, false, S1, 0, n, 0>(W0, BaseStride{WS}, nul, BaseStride{0}, AP,
-                                                             BaseStride{WS}, B, ne, tid, nthr);
     }
-    SPX_SYNC();
     for (int e = warp; e < ne; e += nwarp) {
       const T pap = elem_dot<T, ND, WS>(Pd, AP, e, lane);
       if (lane == 0) al[e] = be[e] < T(0) ? T(0) : rz[e] / pap;
@@ -1031,9 +1078,23 @@ __device__ void body_fwd(const T* tab, const Ctx<T>& c, const T* __restrict__ mi
     }
     SPX_SYNC();
   }
-  for (int t = tid; t < ne * ND; t += nthr) {
-    const int e = t / ND, m = t - e * ND;
-    out[c.gcoef[e] + m] = X[e * WS + m];
+  if constexpr (SENSOR) {
+    // d = u_P - u_{P-1}; S_e = d^T M d / u^T M u
+    for (int t = tid; t < ne * ND; t += nthr) {
+      const int e = t / ND, m = t - e * ND;
+      Pd[e * WS + m] = c.staged(0, e)[m] - X[e * WS + m];
+    }
+    SPX_SYNC();
+    mass_apply(Pd, BaseStride{WS});
+    for (int e = warp; e < ne; e += nwarp) {
+      const T dmd = elem_dot<T, ND, WS>(Pd, AP, e, lane);
+      if (lane == 0) out[c.gquad[e]] = uMu[e] > T(0) ? dmd / uMu[e] : T(0);
+    }
+  } else {
+    for (int t = tid; t < ne * ND; t += nthr) {
+      const int e = t / ND, m = t - e * ND;
+      out[c.gcoef[e] + m] = X[e * WS + m];
+    }
   }
 }
 
@@ -1047,6 +1108,8 @@ __device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel)
   else if constexpr (OP == OP_HELM) body_helm<T, DIM, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_ADJ) body_adj<T, DIM, P, Q>(tab, c, p.out0, p.out1, rel);
   else if constexpr (OP == OP_FWD) body_fwd<T, DIM, P, Q>(tab, c, p.in1 + mass1d_off(P), p.out0);
+  else if constexpr (OP == OP_SENSOR)
+    body_fwd<T, DIM, P, Q, true>(tab, c, p.in1 + mass1d_off(kMaxP + 1) + mass1d_off(P), p.out0);
   else body_diag<T, DIM, P, Q>(tab, c, p.out0, rel);
 }
 
@@ -1136,6 +1199,7 @@ __global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KPar
         }
         soff[s * kMaxEB + j] = static_cast<uint32_t>((at - sm) / sizeof(T));
       }
+      if constexpr (OP == OP_SENSOR) gquad[j] = e;   // its output is one value per element
     }
     __syncthreads();
     bool released = false;

@@ -15,6 +15,7 @@ inline int n_work_buffers(int op) {
     case OP_HELM: return 5;
     case OP_ADJ: return 8;
     case OP_FWD: return 7;
+    case OP_SENSOR: return 7;
     default: return 5;
   }
 }
@@ -30,6 +31,7 @@ inline void stream_lens(int op, int dim, int P, int Q, bool lam_f, bool kap_f, i
     case OP_BWD: lens[0] = nd; break;
     case OP_IPROD: lens[0] = qd; lens[1] = qd; break;
     case OP_FWD: lens[0] = qd; lens[1] = qd; break;
+    case OP_SENSOR: lens[0] = nd; lens[1] = qd; break;
     case OP_DERIV: lens[0] = qd; lens[1] = dim * dim * qd; break;
     case OP_HELM:
       lens[0] = nd; lens[1] = nf * qd; lens[2] = lam_f ? qd : 0; lens[3] = kap_f ? qd : 0;
@@ -78,7 +80,7 @@ inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const Launch
   L.work_base = L.slot_base + cfg.stages * L.slot_bytes;
   L.work_bytes = up128(work);
   L.meta_base = L.work_base + n_work_buffers(op) * L.work_bytes;
-  L.total = L.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8 + 16 + (op == OP_FWD ? kFwdExtra * sz : 0);
+  L.total = L.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8 + 16 + (op == OP_FWD || op == OP_SENSOR ? kFwdExtra * sz : 0);
   return L;
 }
 

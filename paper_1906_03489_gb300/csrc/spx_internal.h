@@ -53,12 +53,11 @@ struct spx_plan {
   int64_t* d_quad_off = nullptr;
   int32_t* d_ids = nullptr;
   int* d_status = nullptr;
-  // small device buffers (owned): per-order inverse 1D mass matrices (FP64 at
-  // aux64, FP32 at aux32, order P at offset aux_off[P]) for FwdTrans, and the
-  // partial sums of spx_integral
+  // small device buffers (owned): per-order inverse 1D mass matrices for
+  // FwdTrans and the sensor (FP64 at aux64, FP32 at aux32; layout
+  // mass1d_off in kernel_params.h), and the partial sums of spx_integral
   double* d_aux64 = nullptr;
   float* d_aux32 = nullptr;
-  int aux_off[spx::kMaxP1 + 1] = {};
   double* d_partials = nullptr;
   unsigned int* d_ticket = nullptr;
   // per operator and precision
@@ -103,7 +102,8 @@ spx_status ensure_tiles(spx_plan* plan, int op, int dtype);
   SPX_DECL_LAUNCH(TN, DIM, 3)     \
   SPX_DECL_LAUNCH(TN, DIM, 4)     \
   SPX_DECL_LAUNCH(TN, DIM, 5)     \
-  SPX_DECL_LAUNCH(TN, DIM, 6)
+  SPX_DECL_LAUNCH(TN, DIM, 6)     \
+  SPX_DECL_LAUNCH(TN, DIM, 7)
 SPX_DECL_ALL_OPS(f64, 2)
 SPX_DECL_ALL_OPS(f64, 3)
 SPX_DECL_ALL_OPS(f32, 2)
@@ -131,6 +131,8 @@ void eo_tables(int P, int Q, double* tab);
 constexpr int kIntegralBlocksPerSM = 4;
 
 // Inverse of the 1D mass matrix B^T diag(w) B of order P on Q points, [n][n].
-void mass1d_inverse(int P, int Q, double* minv);
+// restricted: the matrix without row and column P - 1 (the degree-P bubble),
+// inverted, with zeros in that row and column (P >= 2).
+void mass1d_inverse(int P, int Q, double* minv, bool restricted = false);
 
 }  // namespace spx

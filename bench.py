@@ -487,12 +487,14 @@ def measure_cg(spx, mesh, synth, torch):
         spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision=prec, workspace=ws, maxit=5,
                      raise_on_fail=False)  # warm-up (graphs, tiles)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, info = spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision=prec, inner_tol=itol, workspace=ws)
-        torch.cuda.synchronize()
-        t = time.perf_counter() - t0
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            t0 = time.perf_counter()
+            x, info = spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision=prec, inner_tol=itol, workspace=ws)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
         uh = spx.bwd_trans(plan, spx.gather(plan, l2g, x))
         res[prec] = {"time_s": round(t, 4), "iters": info["iters"], "outer_iters": info["outer_iters"],
+                     "clocks": clk.summary(),
                      "inner_tol": itol if prec != "f64" else None,
                      "rel_residual": info["rel_residual"], "status": info["status"],
                      "max_err_vs_exact": (uh - u_star).abs().max().item()}

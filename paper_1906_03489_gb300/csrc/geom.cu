@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "op_kernel.cuh"
+#include "dot_acc.cuh"
 #include "spx_internal.h"
 
 namespace spx {
@@ -314,7 +315,8 @@ __global__ void assemble_atomic(const int32_t* __restrict__ l2g, const T* __rest
 
 // ---- integral: sum over elements and quadrature points of JW f -----------
 // One warp per element (elements warp, warp + all warps, ...), lanes over the
-// element's points; FP64 sums in a fixed order (per-thread partials, warp
+// element's points; sums at FP64 accuracy in a fixed order (per-thread
+// partials as in dot_acc.cuh, then FP64: warp
 // shuffles, per-warp then per-block sums, and the last block to finish sums
 // the block partials), so the result is reproducible for a given GPU.
 constexpr int kIntThreads = 256;
@@ -328,14 +330,15 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(const T* __restri
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  double acc = 0.0;
+  DotAcc<T> part;   // FP64, or a compensated float pair for FP32 data (no FP64 instruction per term)
   for (int64_t e = gw; e < E; e += nw) {
     const int64_t q0 = quad_off ? quad_off[e] : e * qd_uniform;
     const int64_t qd = quad_off ? quad_off[e + 1] - q0 : qd_uniform;
     const T* jw = geom + int64_t(nf) * q0 + int64_t(nf - 1) * qd;
     const T* fe = f + q0;
-    for (int64_t q = lane; q < qd; q += 32) acc = fma(static_cast<double>(jw[q]), static_cast<double>(fe[q]), acc);
+    for (int64_t q = lane; q < qd; q += 32) part.add(jw[q], fe[q]);
   }
+  double acc = part.value();
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) ws[w] = acc;
   __syncthreads();

@@ -130,7 +130,8 @@ spx_status spx_plan_offsets(const spx_plan *plan, int64_t *coef_off, int64_t *qu
 /* Reads the plan's device status word (synchronises the device): bit 0 set
  * means a kernel of this plan gave up a bounded wait for its input copies and
  * left its outputs incomplete; bit 1 means an index argument was out of
- * range.  reset != 0 clears the word afterwards. */
+ * range; bit 2 means an elemental solve (FwdTrans, sensor) stopped at its
+ * step cap above its tolerance.  reset != 0 clears the word afterwards. */
 spx_status spx_plan_device_status(spx_plan *plan, int *status, int reset);
 
 /* Registers caller-owned geometry buffers (device, layout above) for one
@@ -232,7 +233,8 @@ spx_status spx_helmholtz_adjoint(const spx_plan *plan, const double *u, const do
  * shared memory), preconditioned by (1 / Jbar_e) (M1^{-1})^{(x)d} with M1 the
  * 1D mass matrix B^T diag(w) B and Jbar_e the element's mean Jacobian: exact,
  * so one step, when det J is constant on the element.  Each element stops at
- * ||M_e c - b||_2 <= tol ||b||_2 (tol 1e-14 FP64, 1e-6 FP32) or after 64 steps.
+ * ||M_e c - b||_2 <= tol ||b||_2 (tol 1e-14 FP64, 1e-6 FP32) or after 64 steps
+ * (then bit 2 of the plan's device status word is set).
  * The coefficients are as ill-conditioned as M_e (cond about 4e7 at P = 4 in
  * 3D in this basis); the projected function BwdTrans(c) only by the square
  * root: about sqrt(cond) x unit roundoff, i.e. ~1e-12 in FP64 but ~1e-4 in

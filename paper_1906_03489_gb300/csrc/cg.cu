@@ -222,12 +222,22 @@ __global__ void assemble_plain(const int32_t* __restrict__ row_ptr, const int32_
   }
 }
 
+// Programmatic dependent launch (sm_90+): the iteration's vector kernels are
+// launched with programmatic stream serialisation, so a kernel's blocks may be
+// scheduled while its predecessor drains.  Each of them first waits for the
+// predecessor grid to complete with its memory visible (griddep_wait: a no-op
+// without a programmatic predecessor), and lets its own successor launch once
+// its main loop is done (griddep_launch).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // loc = g[l2g] (skipped once the solve is done).  One entry per thread and
 // trip: the lanes of a warp read consecutive l2g entries, whose global
 // indices run in short consecutive stretches (the modes of an element row).
 template <typename T>
 __global__ void gather_if(const int32_t* __restrict__ l2g, const T* __restrict__ g, T* __restrict__ loc, int64_t n,
                           const Scalars* sc) {
+  griddep_wait();
   if (sc->done) return;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     loc[i] = g[l2g[i]];
@@ -243,6 +253,7 @@ __global__ void __launch_bounds__(kRedThreads) assemble_dot(const int32_t* __res
                                                             const T* __restrict__ ql, T* __restrict__ q,
                                                             const T* __restrict__ p, int64_t ng, Scalars* sc,
                                                             double* partials) {
+  griddep_wait();
   if (sc->done) return;
   DotAcc<T> acc;
   const int64_t S = int64_t(gridDim.x) * blockDim.x;
@@ -277,6 +288,7 @@ __global__ void __launch_bounds__(kRedThreads) assemble_dot(const int32_t* __res
       }
     }
   }
+  griddep_launch();
   double pAp, unused;
   if (grid_reduce2(acc.value(), 0.0, partials, &sc->ticket, &pAp, &unused)) {
     sc->pAp = pAp;
@@ -293,6 +305,7 @@ __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* _
                                                          const T* __restrict__ p, const T* __restrict__ q,
                                                          const T* __restrict__ minv, int64_t ng, Scalars* sc,
                                                          double* partials) {
+  griddep_wait();
   if (sc->done) return;
   constexpr int U = V == 1 ? 4 : 1;   // packs per trip (loads in flight per thread)
   const T alpha = static_cast<T>(sc->alpha);
@@ -341,6 +354,7 @@ __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* _
     arz.add(rn, zv);
     arr.add(rn, rn);
   }
+  griddep_launch();
   double rz, rr;
   if (grid_reduce2(arz.value(), arr.value(), partials, &sc->ticket, &rz, &rr)) {
     sc->rz_new = rz;
@@ -362,6 +376,7 @@ __global__ void __launch_bounds__(kRedThreads) cg_update(T* __restrict__ x, T* _
 // p = z + beta p
 template <typename T, int V>
 __global__ void cg_direction(T* __restrict__ p, const T* __restrict__ z, int64_t ng, const Scalars* sc) {
+  griddep_wait();
   if (sc->done) return;
   const T beta = static_cast<T>(sc->beta);
   const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -616,6 +631,22 @@ spx_status build_csr(Solver& s) {
 
 bool a16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// Launch with programmatic stream serialisation (see griddep_wait).
+template <typename... KArgs, typename... Args>
+void pdl_launch(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // y_global = A x_global in precision T (using pl / ql local buffers)
 template <typename T>
 spx_status apply_A(Solver& s, int dt, const T* xg, T* pl, T* ql, T* yg) {
@@ -652,25 +683,27 @@ struct PcgRun {
   spx_status enqueue_iteration() {
     Workspace& w = s->w;
     cudaStream_t st = s->st;
-    gather_if<T><<<s->grid_v, 256, 0, st>>>(s->l2g, p, pl, s->nl, w.sc);
+    pdl_launch(gather_if<T>, s->grid_v, 256, st, s->l2g, p, pl, s->nl, w.sc);
     spx_status e = helmholtz_unless(s->plan, dt, s->lam, pl, ql, &w.sc->done, st);
     if (e != SPX_OK) return e;
-    assemble_dot<T><<<one_wave(*s, assemble_dot<T>), kRedThreads, 0, st>>>(w.row_ptr, w.cols, ql, q, p, s->ng, w.sc,
-                                                                          w.partials);
+    pdl_launch(assemble_dot<T>, one_wave(*s, assemble_dot<T>), kRedThreads, st, w.row_ptr, w.cols, ql, q, p, s->ng,
+               w.sc, w.partials);
     if (a16(x) && a16(r) && a16(z) && a16(p) && a16(q) && a16(minv))
-      cg_update<T, V><<<one_wave(*s, cg_update<T, V>), kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc,
-                                                                               w.partials);
+      pdl_launch(cg_update<T, V>, one_wave(*s, cg_update<T, V>), kRedThreads, st, x, r, z, p, q, minv, s->ng, w.sc,
+                 w.partials);
     else
-      cg_update<T, 1><<<one_wave(*s, cg_update<T, 1>), kRedThreads, 0, st>>>(x, r, z, p, q, minv, s->ng, w.sc,
-                                                                               w.partials);
+      pdl_launch(cg_update<T, 1>, one_wave(*s, cg_update<T, 1>), kRedThreads, st, x, r, z, p, q, minv, s->ng, w.sc,
+                 w.partials);
     direction();
     SPX_CK(cudaGetLastError());
     return SPX_OK;
   }
 
   void direction() {
-    if (a16(p) && a16(z)) cg_direction<T, V><<<s->grid_dir, 256, 0, s->st>>>(p, z, s->ng, s->w.sc);
-    else cg_direction<T, 1><<<s->grid_dir, 256, 0, s->st>>>(p, z, s->ng, s->w.sc);
+    if (a16(p) && a16(z)) pdl_launch(cg_direction<T, V>, s->grid_dir, 256, s->st, p, static_cast<const T*>(z), s->ng,
+                                     static_cast<const Scalars*>(s->w.sc));
+    else pdl_launch(cg_direction<T, 1>, s->grid_dir, 256, s->st, p, static_cast<const T*>(z), s->ng,
+                    static_cast<const Scalars*>(s->w.sc));
   }
 
   // z = minv r; p = z; rz (scalars ff / tol2 / maxit set by the caller)

@@ -13,6 +13,7 @@ namespace spx {
 constexpr unsigned long long kWaitNs = 4000000000ull;  // a staged copy not landed after 4 s is abandoned
 constexpr int kStatusTimeout = 1;     // bit set in the plan's device status word
 constexpr int kStatusBadIndex = 2;    // bit set when an index argument is out of range
+constexpr int kStatusNotConverged = 4;  // bit set when an elemental iteration hit its step cap
 
 // ---------------------------------------------------------------------------
 // PTX helpers

@@ -144,6 +144,7 @@ struct Ctx {
   int ne, tid, nthr;
   int* tab_order;         // order whose tables are in work buffer 4 (shared)
   T* extra;               // kFwdExtra values after the tile metadata (FwdTrans)
+  int* status;            // the plan's device status word
   bool has_lam, has_kap;
   T lam;
   __device__ const T* staged(int s, int j) const { return reinterpret_cast<const T*>(sm) + soff[s * kMaxEB + j]; }
@@ -870,8 +871,10 @@ __device__ void body_diag(const T* tab, const Ctx<T>& c, T* out, Rel release) {
 // sum_q JW_q / 2^d the element's mean Jacobian, since M_e = Jbar_e M1^{(x)d}
 // whenever det J is constant on the element: then one step solves it, and a
 // varying det J only adds steps.  An element stops at ||r|| <= tol ||b||
-// (1e-14 FP64, 1e-6 FP32) or after 64 steps.  Per-element dot products:
-// one warp per element, lanes in a fixed order (reproducible).
+// (1e-14 FP64, 1e-6 FP32); a tile whose elements have not all converged
+// after 64 steps stops there and sets bit 2 of the plan's status word.
+// Per-element dot products: one warp per element, lanes in a fixed order
+// (reproducible).
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -1072,6 +1075,10 @@ __device__ void body_fwd(const T* tab, const Ctx<T>& c, const T* __restrict__ mi
       }
     }
     if (!__syncthreads_or(active)) break;
+    if (it == kMaxIt - 1) {   // step cap reached with elements still above the tolerance
+      if (tid == 0) atomicOr(c.status, kStatusNotConverged);
+      break;
+    }
     for (int t = tid; t < ne * ND; t += nthr) {
       const int e = t / ND, m = t - e * ND;
       if (be[e] >= T(0)) Pd[e * WS + m] = fma(be[e], Pd[e * WS + m], jb[e] * Z[e * WS + m]);
@@ -1150,6 +1157,7 @@ __global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KPar
   c.soff = soff;
   c.tab_order = tab_order;
   c.extra = reinterpret_cast<T*>(sm + p.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8 + 16);
+  c.status = p.status;
   c.gcoef = gcoef;
   c.gquad = gquad;
   c.tid = tid;

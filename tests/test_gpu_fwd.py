@@ -111,6 +111,18 @@ def test_fwd_trans_variable_order():
     assert rel_err(operators.bwd_trans(c.om, cg), operators.bwd_trans(c.om, ref)) <= 100 * np.sqrt(kappa) * EPS
 
 
+def test_fwd_trans_q_offset_one():
+    """Q = P + 1 points (the mass matrix is no longer integrated exactly, but it is
+    still SPD and the same projection is solved): parity with the oracle."""
+    c = Case(3, 3, P=4, amp=0.05, q_offset=1)
+    f, ft = c.quad(26)
+    cg = spx.fwd_trans(c.plan, ft).cpu().numpy()
+    ref = operators.fwd_trans(c.om, f)
+    kappa = _elem_checks(c, f, cg, 1e-13)
+    assert rel_err(cg, ref) <= 100 * kappa * EPS
+    assert rel_err(operators.bwd_trans(c.om, cg), operators.bwd_trans(c.om, ref)) <= 100 * np.sqrt(kappa) * EPS
+
+
 @pytest.mark.parametrize("dim,P", [(3, 4), (2, 6)])
 def test_projection_reproduces_expansions(dim, P):
     """FwdTrans(BwdTrans(u)) = u: the projection of a function in the space is itself."""

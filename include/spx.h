@@ -6,9 +6,11 @@
  * element method of arXiv 1906.03489 (Nektar++ 5.0): BwdTrans,
  * IProductWRTBase, PhysDeriv and the Helmholtz operator H = lambda M + L,
  * with the modified C0 basis (§2.1) on Gauss-Lobatto-Legendre points, by
- * sum-factorisation (§3.3) in hand-written CUDA kernels; plus the adjoint of H
- * with respect to its coefficient fields, periodic C0 assembly and a
- * Jacobi-preconditioned CG solver (§2.1, implicit-type methods).
+ * sum-factorisation (§3.3) in hand-written CUDA kernels; FwdTrans (Galerkin
+ * projection) and Integral (§3.5 worked example); the adjoint of H with
+ * respect to its coefficient fields; the adaptive-order error sensor (§4.2);
+ * periodic C0 assembly and a Jacobi-preconditioned CG solver (§2.1,
+ * implicit-type methods).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -16,7 +18,8 @@
  *   memory of the current device; "host" pointers are ordinary host memory.
  * - Ownership: the caller owns every data buffer.  The library never frees a
  *   caller pointer and allocates no buffer of the size of a field; a plan owns
- *   only small metadata (per-element offsets and a work list, O(E) words).
+ *   only small metadata (per-element offsets and a work list, O(E) words;
+ *   per-order 1D tables and a few kilobytes of reduction partials).
  * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream).  All device work is enqueued on it and the call returns without
  *   synchronising, unless stated otherwise.

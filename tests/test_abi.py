@@ -68,3 +68,19 @@ def test_periodic_map_matches_oracle(dim, N, P):
     om = geometry.StructuredMesh(dim, N, P)
     np.testing.assert_array_equal(l2g.numpy(), solve.local_to_global(om))
     assert ng == solve.n_global(om)
+
+
+def test_adapt_orders_host_entry_point_matches_oracle(lib):
+    """spx_adapt_orders is host code: the §4.2 order update, checked on the CPU."""
+    from oracle import adapt
+    import paper_1906_03489_gb300 as spx
+    rng = np.random.default_rng(9)
+    S = 10.0 ** rng.uniform(-12, 0, 200)
+    P = rng.integers(2, 9, 200).astype(np.int32)
+    for lo, hi, pmin, pmax in ((1e-8, 1e-3, 2, 8), (1e-6, 1e-6, 3, 6), (0.0, 1.0, 2, 2)):
+        np.testing.assert_array_equal(spx.adapt_orders(S, P, lo, hi, pmin, pmax),
+                                      adapt.adapt_orders(S, P, lo, hi, pmin, pmax))
+    with pytest.raises(spx.SpxError):
+        spx.adapt_orders(S, P, 1e-3, 1e-8, 2, 8)        # lower > upper
+    with pytest.raises(spx.SpxError):
+        spx.adapt_orders(S, P, 1e-8, 1e-3, 1, 8)        # P_min < 2

@@ -456,11 +456,11 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
     ex["adjoint_hex16_p6"] = {"fwd_bwd_ms": round(ms, 3)}
     del pa, ga
     # periodic solve of the 48^3 workload
-    ex["cg_hex48"] = measure_cg(spx, mesh, synth, torch)
+    ex["cg_hex48"] = measure_cg(spx, mesh, synth, torch, hbm_peak)
     return ex
 
 
-def measure_cg(spx, mesh, synth, torch):
+def measure_cg(spx, mesh, synth, torch, hbm_peak):
     import numpy as np
     w = synth.WORKLOADS["hex3d_48_p4"]
     N, P = w["N"], w["P"]
@@ -498,6 +498,27 @@ def measure_cg(spx, mesh, synth, torch):
                      "inner_tol": itol if prec != "f64" else None,
                      "rel_residual": info["rel_residual"], "status": info["status"],
                      "max_err_vs_exact": (uh - u_star).abs().max().item()}
+    # one FP32 iteration: time from two iteration caps of one FP32 run, and the
+    # algorithmic bytes it moves (Helmholtz apply + gather + assembly + vector updates)
+    ts = {}
+    for m in (50, 250):
+        spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-14, precision="f32_reliable", maxit=5, max_outer=1, workspace=ws,
+                     raise_on_fail=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, inf = spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-14, precision="f32_reliable", maxit=m, max_outer=1,
+                              workspace=ws, raise_on_fail=False)
+        torch.cuda.synchronize()
+        ts[m] = (time.perf_counter() - t0, inf["iters"])
+    per = (ts[250][0] - ts[50][0]) / max(1, ts[250][1] - ts[50][1])
+    nl, E = plan.n_coef, plan.E
+    it_bytes = (E * helm_bytes_per_elem(P, P + 2, 4)            # Helmholtz apply
+                + nl * 4 * 2 + ng * 4                           # gather: l2g, local copy, p
+                + (ng + 1) * 4 + nl * 4 * 2 + ng * 4 * 2        # assembly: row_ptr, cols, ql, p, q
+                + ng * 4 * 8 + ng * 4 * 3)                      # update (5 reads, 3 writes), direction
+    res["f32_iteration"] = {"us": round(per * 1e6, 1), "algorithmic_bytes": it_bytes,
+                            "gbs": round(it_bytes / per / 1e9, 1), "hbm_frac": round(it_bytes / per / 1e9 / hbm_peak, 4),
+                            "timing": "difference of 250- and 50-iteration FP32 runs (wall clock, synchronised)"}
     res["speedup_f32_refine_vs_f64"] = round(res["f64"]["time_s"] / res["f32_refine"]["time_s"], 3)
     res["speedup_f32_reliable_vs_f64"] = round(res["f64"]["time_s"] / res["f32_reliable"]["time_s"], 3)
     return res

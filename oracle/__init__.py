@@ -27,6 +27,9 @@ What it computes, and the passage each part follows:
                  of the adaptive polynomial order procedure and its order
                  update (§4.2), with u_{P-1} the dense L^2 projection onto the
                  order P - 1 basis.
+* ``nodal``      the GLL nodal (Lagrange, classical spectral element) basis
+                 variant of the elemental Helmholtz matrix (§2.1 names the
+                 Lagrange interpolant basis beside the modified one).
 * ``adjoint``    gradients of 0.5*||H(lambda,kappa)u - f||^2 with respect to
                  u, lambda(x) and kappa(x), by differentiating the dense
                  forms of eq. e:bilinear.

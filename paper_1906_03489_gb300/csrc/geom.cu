@@ -318,7 +318,8 @@ __global__ void assemble_atomic(const int32_t* __restrict__ l2g, const T* __rest
 // element's points; sums at FP64 accuracy in a fixed order (per-thread
 // partials as in dot_acc.cuh, then FP64: warp
 // shuffles, per-warp then per-block sums, and the last block to finish sums
-// the block partials), so the result is reproducible for a given GPU.
+// the block partials with all its threads), so the result is reproducible
+// for a given GPU.
 constexpr int kIntThreads = 256;
 template <typename T>
 __global__ void __launch_bounds__(kIntThreads) integral_kernel(const T* __restrict__ f, const T* __restrict__ geom,
@@ -350,12 +351,22 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(const T* __restri
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;   // uniform across the block
   __threadfence();
+  // the block sums the partials: thread t takes t, t + blockDim, ... in order,
+  // then warp shuffles and the warp sums in warp order (a fixed order)
   double t = 0.0;
-  for (unsigned i = 0; i < gridDim.x; ++i) t += static_cast<volatile const double*>(partials)[i];
-  *out = t;
-  *ticket = 0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) t += static_cast<volatile const double*>(partials)[i];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  __syncthreads();
+  if (lane == 0) ws[w] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int i = 0; i < kIntThreads / 32; ++i) b += ws[i];
+    *out = b;
+    *ticket = 0;
+  }
 }
 
 }  // namespace spx

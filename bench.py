@@ -455,9 +455,33 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
     ms = timed(fwd_bwd, 10, stream)
     ex["adjoint_hex16_p6"] = {"fwd_bwd_ms": round(ms, 3)}
     del pa, ga
+    # 2D correctness workload (16 x 16 affine quads, P = 4, Q = 6, FP64): BwdTrans,
+    # IProduct and Helmholtz once each after warm-up; latency-sized (6400 DOFs),
+    # so times only, no roofline
+    try:
+        ex["quad2d_16x16_p4"] = measure_quad2d(spx, mesh, synth, torch, stream)
+    except Exception as err:   # an extra: never lose the benchmark line over it
+        ex["quad2d_16x16_p4"] = {"error": str(err)[:200]}
     # periodic solve of the 48^3 workload
     ex["cg_hex48"] = measure_cg(spx, mesh, synth, torch, hbm_peak)
     return ex
+
+
+def measure_quad2d(spx, mesh, synth, torch, stream):
+    w, plans, _, coef = make_workload("quad2d_16x16_p4", spx, mesh, synth, torch)
+    plan = plans[0]
+    u = torch.tensor(coef, device="cuda")
+    f = spx.bwd_trans(plan, u)
+    y, c = torch.empty_like(u), torch.empty_like(u)
+    out = {}
+    for op, fn in (("bwd_trans_us", lambda: spx.bwd_trans(plan, u, f)),
+                   ("iproduct_us", lambda: spx.iproduct(plan, f, c)),
+                   ("helmholtz_us", lambda: spx.helmholtz(plan, u, lam=1.0, out=y))):
+        fn()
+        out[op] = round(timed(fn, 50, stream) * 1e3, 2)
+    out["elements"] = plan.E
+    out["local_dofs"] = plan.n_coef
+    return out
 
 
 def measure_cg(spx, mesh, synth, torch, hbm_peak):

@@ -84,3 +84,27 @@ def test_adapt_orders_host_entry_point_matches_oracle(lib):
         spx.adapt_orders(S, P, 1e-3, 1e-8, 2, 8)        # lower > upper
     with pytest.raises(spx.SpxError):
         spx.adapt_orders(S, P, 1e-8, 1e-3, 1, 8)        # P_min < 2
+
+
+@pytest.mark.parametrize("dim,n_elem,order,orders,qoff,status", [
+    (4, 8, 3, None, 2, 1),              # dimension outside {2, 3}
+    (3, -1, 3, None, 2, 1),             # negative element count
+    (3, 8, 9, None, 2, 1),              # uniform order above 8
+    (3, 8, 0, None, 2, 1),              # uniform order below 1
+    (3, 3, 0, [2, 9, 4], 2, 1),         # a per-element order above 8
+    (3, 8, 3, None, 3, 2),              # q_offset outside {1, 2}
+])
+def test_plan_create_validates_before_touching_the_device(lib, dim, n_elem, order, orders, qoff, status):
+    """Invalid plan descriptions are refused with a status and a message, before any CUDA call."""
+    import ctypes as C
+    from paper_1906_03489_gb300 import _lib
+    d = _lib.PlanDesc()
+    d.dim, d.n_elem, d.uniform_order, d.q_offset = dim, n_elem, order, qoff
+    keep = None
+    if orders is not None:
+        keep = np.asarray(orders, dtype=np.int32)
+        d.elem_order = keep.ctypes.data_as(C.POINTER(C.c_int32))
+    h = C.c_void_p()
+    assert lib.spx_plan_create(C.byref(h), C.byref(d)) == status
+    assert not h.value
+    assert lib.spx_last_error().decode().startswith("plan_create")

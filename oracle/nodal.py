@@ -2,11 +2,14 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-§2.1 names, beside the modified C0 basis, the classical Lagrange interpolant
-basis; both admit the boundary-interior decomposition that C0 assembly uses.
-Nodal basis of order P, read here as: the Lagrange polynomials l_m through the
-P+1 Gauss-Lobatto-Legendre points, in the library's tensor-product index order
-(m along xi_1 fastest).  On Q = P+1 GLL quadrature points (collocation) the
+§2.1, right after the display of the modified basis phi_p: the same 1D
+functions may instead be taken as the Lagrange polynomials through the
+Gauss-Lobatto-Legendre points, which gives the traditional spectral element
+method, with tensor products of either basis on quadrilaterals and
+hexahedra (the p-adaptivity paragraph of §4.2 notes that both admit the
+boundary-interior decomposition C0 assembly uses).  Nodal basis of order P,
+read here as: the Lagrange polynomials l_m through the P+1 GLL points, in the
+library's tensor-product index order (m along xi_1 fastest).  On Q = P+1 GLL quadrature points (collocation) the
 basis matrix is the identity, its reference gradient the collocation
 derivative, and the mass matrix diag(w det J); with more points the same
 definitions apply with the Lagrange values at those points.  The elemental

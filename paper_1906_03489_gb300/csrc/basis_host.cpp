@@ -190,9 +190,14 @@ void eo_tables(int P, int Q, double* tab) {
   double* Dm = Dp + H * H;
   double* Tp = Dm + H * H;
   double* Tm = Tp + H * H;
+  double* Gs = Tm + H * H;
+  double* Gd = Gs + Hc;
+  const double* dB = tab + Q * n;
   for (int i = 0; i < Hc; ++i) {
     Bs[i] = 0.5 * (B[i * n] + B[i * n + P]);
     Bd[i] = 0.5 * (B[i * n] - B[i * n + P]);
+    Gs[i] = 0.5 * (dB[i * n] + dB[i * n + P]);
+    Gd[i] = 0.5 * (dB[i * n] - dB[i * n + P]);
   }
   for (int i = 0; i < H; ++i)
     for (int j = 0; j < H; ++j) {

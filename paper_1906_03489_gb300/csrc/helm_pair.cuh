@@ -216,7 +216,7 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
     for (int j = 0; j < Q; ++j) C[a + Q * b + YS * j] = y[j];
   }
   ctl.sync();
-  // S3: column (i, j) = (a, b): u = B y along xi_3 -> U in A and U' in F; d2 = D u in registers
+  // S3: column (i, j) = (a, b): u = B y along xi_3 -> U in A and U' in F; d2 = dB y in registers
   V u[Q], g2[Q];
   if (act) {
     V y[n];
@@ -228,7 +228,7 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
       A[a + Q * b + US * k] = u[k];
       F[a + Q * b + GS * k] = u[k];
     }
-    eo_d<P, Q, false>(tab, u, g2);
+    eo_db<P, Q>(tab, y, g2);
   }
   ctl.sync();
   // S4: gradient pencils, in place: along xi_1 at (j, k) = (b, a) in A (U -> d0),
@@ -251,12 +251,13 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
   // the tile's geometry: wait for it to land (ends the phase with a barrier)
   if (!ctl.geo_wait(p, t, Q)) return false;
   // S5: column (i, j) = (a, b): pointwise geometric factors; g0 -> A, g1 -> F, g2 and
-  // lambda JW u in registers; then z = lambda JW u + D^T g2 along xi_3
+  // lambda JW in registers; then z = D^T g2 + lambda JW u along xi_3
   V z[Q];
   if (act) {
     const float* G0 = geo_staged(p.geom, dsm + ctl.offs[3], t, j0, q0, Q) + b * Q + a;
     const float* G1 = geo_staged(p.geom, dsm + ctl.offs[3], t, two ? j1 : j0, two ? q1 : q0, Q) + b * Q + a;
     const float lam = static_cast<float>(p.lam);
+    V ljk[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int w0 = a + Q * b + US * k, w1 = a + Q * b + GS * k;
@@ -288,11 +289,11 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
       A[w0] = r0;
       F[w1] = r1;
       g2[k] = r2;
-      u[k] = Vt::mul(lj, u[k]);
+      ljk[k] = lj;
     }
     eo_d<P, Q, true>(tab, g2, z);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) z[k] = Vt::add(z[k], u[k]);
+    for (int k = 0; k < Q; ++k) z[k] = Vt::fmav(ljk[k], u[k], z[k]);
   }
   ctl.sync();
   // every thread is done with the geometry slot

@@ -36,8 +36,8 @@ struct Tile {
 
 // Per-order table: B[Q][n], dB[Q][n], D[Q][Q], then the even-odd
 // coefficients (EOLayout): Bs[Hc], Bd[Hc], Dp[H][H], Dm[H][H], Tp[H][H],
-// Tm[H][H] with H = Q / 2, Hc = (Q + 1) / 2.
-__host__ __device__ constexpr int eo_len(int Q) { return 2 * ((Q + 1) / 2) + 4 * (Q / 2) * (Q / 2); }
+// Tm[H][H], Gs[Hc], Gd[Hc] with H = Q / 2, Hc = (Q + 1) / 2.
+__host__ __device__ constexpr int eo_len(int Q) { return 4 * ((Q + 1) / 2) + 4 * (Q / 2) * (Q / 2); }
 __host__ __device__ constexpr int tab_len(int P, int QOFF) {
   return 2 * (P + QOFF) * (P + 1) + (P + QOFF) * (P + QOFF) + eo_len(P + QOFF);
 }
@@ -54,11 +54,16 @@ __host__ __device__ constexpr int tab_len(int P, int QOFF) {
 // with Bs_i = (B_i0 + B_iP) / 2, Bd_i = (B_i0 - B_iP) / 2,
 // Dp_ij = (D_ij + D_i,Q-1-j) / 2, Dm_ij = (D_ij - D_i,Q-1-j) / 2 and Tp, Tm the
 // same for D^T; the transposed contractions follow by the same symmetry.
+// The derivatives of the basis have the opposite parity, phi_0'(-x) =
+// -phi_P'(x) and phi_b'(-x) = (-1)^b phi_b'(x), so
+//   (dB v)_i, (dB v)_{Q-1-i} = S'_i +- A'_i,  S'_i = Gd_i o + sum_{b even} dB_ib v_b,
+//                                               A'_i = Gs_i e + sum_{b odd} dB_ib v_b
+// with Gs_i = (dB_i0 + dB_iP) / 2, Gd_i = (dB_i0 - dB_iP) / 2.
 template <int P, int Q>
 struct EOLayout {
   static constexpr int n = P + 1, H = Q / 2, Hc = (Q + 1) / 2;
   static constexpr int Bs = 2 * Q * n + Q * Q, Bd = Bs + Hc, Dp = Bd + Hc, Dm = Dp + H * H, Tp = Dm + H * H,
-                       Tm = Tp + H * H;
+                       Tm = Tp + H * H, Gs = Tm + H * H, Gd = Gs + Hc;
 };
 
 // Shared-memory layout of the FP32 3D Helmholtz kernel (helm_pair.cuh), in

@@ -98,6 +98,33 @@ __device__ __forceinline__ void eo_b(const S* tab, const V* v, V* u) {
   }
 }
 
+// u[Q] = dB v[n]   (derivative of the expansion at the quadrature points along
+// one direction; the opposite parity of B, EOLayout)
+template <int P, int Q, class V, class S>
+__device__ __forceinline__ void eo_db(const S* tab, const V* v, V* u) {
+  using E = EOLayout<P, Q>;
+  using Vt = Lane<V>;
+  constexpr int n = P + 1, H = Q / 2;
+  const S* dB = tab + Q * n;
+  const V e = Vt::add(v[0], v[P]);
+  const V o = vsub(v[0], v[P]);
+#pragma unroll
+  for (int i = 0; i < E::Hc; ++i) {
+    V s = vscale(tab[E::Gd + i], o);
+#pragma unroll
+    for (int b = 2; b < P; b += 2) s = Vt::fma(dB[i * n + b], v[b], s);
+    if (i == H) {  // middle point of an odd Q: the antisymmetric part vanishes
+      u[i] = s;
+    } else {
+      V a = vscale(tab[E::Gs + i], e);
+#pragma unroll
+      for (int b = 1; b < P; b += 2) a = Vt::fma(dB[i * n + b], v[b], a);
+      u[i] = Vt::add(s, a);
+      u[Q - 1 - i] = vsub(s, a);
+    }
+  }
+}
+
 // y[n] = B^T w[Q]   (quadrature -> modal, the inner product along one direction)
 template <int P, int Q, class V, class S>
 __device__ __forceinline__ void eo_bt(const S* tab, const V* w, V* y) {

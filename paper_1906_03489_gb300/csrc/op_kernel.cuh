@@ -571,7 +571,7 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
     for (int j = 0; j < Q; ++j) W1[(j * Q + a) * SN + b] = y[j];
   }
   SPX_SYNC();
-  // S3: column (i, j) = (a, b): u = B y (xi_3), d2 = D u; U[k][j][i] = u
+  // S3: column (i, j) = (a, b): u = B y (xi_3), d2 = dB y; U[k][j][i] = u
   T u[Q], g2[Q];
   if (act) {
     T y[n];
@@ -580,7 +580,7 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
     eo_b<P, Q>(tab, y, u);
 #pragma unroll
     for (int k = 0; k < Q; ++k) W2[k * PL + b * S + a] = u[k];
-    eo_d<P, Q, false>(tab, u, g2);
+    eo_db<P, Q>(tab, y, g2);
   }
   SPX_SYNC();
   // S4: gradient pencils: along xi_1 at (j, k) = (a, b) -> W3, along xi_2 at (i, k) = (a, b) -> W4
@@ -598,12 +598,14 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
     for (int j = 0; j < Q; ++j) W4[b * PL + j * S + a] = d[j];
   }
   SPX_SYNC();
-  // S5: column (i, j) = (a, b): pointwise; g0 -> W3, g1 -> W4, g2 and v in registers
+  // S5: column (i, j) = (a, b): pointwise; g0 -> W3, g1 -> W4, g2 and lambda JW in
+  // registers; then z = D^T g2 + lambda JW u along xi_3
   T z[Q];
   if (act) {
     const T* G = c.staged(1, el) + b * Q + a;
     const T* lf = c.has_lam ? c.staged(2, el) + b * Q + a : nullptr;
     const T* kf = c.has_kap ? c.staged(3, el) + b * Q + a : nullptr;
+    T lj[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int w = k * PL + b * S + a;
@@ -611,16 +613,23 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
       const T* g = G + k * Q2;
       const T g00 = g[0], g01 = g[Q3], g02 = g[2 * Q3], g11 = g[3 * Q3], g12 = g[4 * Q3], g22 = g[5 * Q3];
       const T jw = g[6 * Q3];
-      const T kk = kf ? kf[k * Q2] : T(1);
-      const T ll = lf ? lf[k * Q2] : c.lam;
-      W3[w] = kk * (g00 * d0 + g01 * d1 + g02 * d2);
-      W4[w] = kk * (g01 * d0 + g11 * d1 + g12 * d2);
-      g2[k] = kk * (g02 * d0 + g12 * d1 + g22 * d2);
-      u[k] = ll * jw * u[k];
+      T r0 = fma(g02, d2, fma(g01, d1, g00 * d0));
+      T r1 = fma(g12, d2, fma(g11, d1, g01 * d0));
+      T r2 = fma(g22, d2, fma(g12, d1, g02 * d0));
+      if (kf) {
+        const T kk = kf[k * Q2];
+        r0 *= kk;
+        r1 *= kk;
+        r2 *= kk;
+      }
+      W3[w] = r0;
+      W4[w] = r1;
+      g2[k] = r2;
+      lj[k] = (lf ? lf[k * Q2] : c.lam) * jw;
     }
     eo_d<P, Q, true>(tab, g2, z);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) z[k] += u[k];
+    for (int k = 0; k < Q; ++k) z[k] = fma(lj[k], u[k], z[k]);
   }
   SPX_SYNC();
   release();

@@ -134,7 +134,9 @@ spx_status spx_plan_offsets(const spx_plan *plan, int64_t *coef_off, int64_t *qu
  * means a kernel of this plan gave up a bounded wait for its input copies and
  * left its outputs incomplete; bit 1 means an index argument was out of
  * range; bit 2 means an elemental solve (FwdTrans, sensor) stopped at its
- * step cap above its tolerance.  reset != 0 clears the word afterwards. */
+ * step cap above its tolerance.  reset != 0 clears the word afterwards.
+ * (The paper has no device-side status; this reports on the collective
+ * operations of §3.3 and the elemental projections of §3.5 / §4.2.) */
 spx_status spx_plan_device_status(spx_plan *plan, int *status, int reset);
 
 /* Registers caller-owned geometry buffers (device, layout above) for one
@@ -144,7 +146,12 @@ spx_status spx_plan_device_status(spx_plan *plan, int *status, int reset);
  * and unchanged while operators run. */
 spx_status spx_plan_set_geometry(spx_plan *plan, spx_dtype dtype, const void *geom, const void *dxi_dx);
 
-/* Overrides the launch tile of one operator/precision/order: elements per
+/* Launch tiles: the GPU counterpart of the Collections strategy choice that
+ * §3.3 makes at start-up (autotuning, COLLECTIONS DEFAULT="auto"): here the
+ * strategy is fixed (sum-factorisation over element tiles) and its tile
+ * shape per operator, precision and order is what is chosen.
+ *
+ * Overrides the launch tile of one operator/precision/order: elements per
  * batch `eb` (1..64), threads per block `nthreads` (32..512, multiple of
  * 32) and pipeline depth `stages` (1..4).  order = -1 sets every order.
  * Two operators derive their block size from eb instead:
@@ -164,7 +171,8 @@ spx_status spx_plan_set_tile(spx_plan *plan, spx_op op, spx_dtype dtype, int ord
 spx_status spx_autotune(spx_plan *plan, spx_op op, spx_dtype dtype, const void *in, void *out, int reps,
                         void *stream);
 
-/* Reads back the tile chosen for (op, dtype, order). */
+/* Reads back the tile chosen for (op, dtype, order) (§3.3 autotuning, as
+ * above). */
 spx_status spx_plan_get_tile(const spx_plan *plan, spx_op op, spx_dtype dtype, int order, int *eb,
                              int *nthreads, int *stages);
 
@@ -277,7 +285,12 @@ spx_status spx_adapt_orders(int64_t n_elem, const double *S, const int32_t *orde
                             int p_min, int p_max, int32_t *new_orders);
 
 /* Diagonal of the elemental Helmholtz matrices, diag(H_e)_l for every local
- * mode (the Jacobi preconditioner before assembly).  out: device [n_coef]. */
+ * mode: the diagonal of the elemental Galerkin matrix of the bilinear form
+ * a(u, v) of §2.1 (eq. e:bilinear with the Helmholtz integrand), summed over
+ * shared modes by spx_assemble it is the Jacobi preconditioner of the
+ * assembled system (§2.1, implicit-type methods).  dtype selects FP64 or
+ * FP32 output and geometry; lambda as in spx_helmholtz (kappa = 1).
+ * out: device [n_coef].  Needs geom. */
 spx_status spx_helmholtz_diag(const spx_plan *plan, spx_dtype dtype, double lambda, void *out, void *stream);
 
 /* ---------------------------------------------------------------------------
@@ -298,6 +311,20 @@ spx_status spx_gather(const spx_plan *plan, spx_dtype dtype, const int32_t *l2g,
  * are skipped and set bit 1 of the plan's device status word. */
 spx_status spx_assemble(const spx_plan *plan, spx_dtype dtype, const int32_t *l2g, int64_t n_global,
                         const void *local, void *global, void *stream);
+
+/* Inner product <a, b> = sum_i a_i b_i of two device vectors of n values of
+ * the call's dtype, at FP64 accuracy: the reductions of the conjugate-
+ * gradient method for the assembled system (§2.1, implicit-type methods),
+ * computed the way the solver computes them: per-thread partials (FP64 for
+ * FP64 data; an unevaluated float pair, hi + lo, for FP32 data, so that no
+ * FP64 instruction is spent per term), then FP64 sums across threads in a
+ * fixed order, so the result is reproducible bit for bit.  For FP32 data the
+ * error is about (terms per thread)^2 2^-48 + (tree depth) 2^-53 times
+ * sum |a_i b_i|.  result: device, one FP64 value written by the stream's
+ * work.  Uses the plan's reduction buffers: calls on one plan that overlap
+ * on the GPU (this and spx_integral) race on them; serialise them. */
+spx_status spx_dot(const spx_plan *plan, spx_dtype dtype, int64_t n, const void *a, const void *b, double *result,
+                   void *stream);
 
 /* Options of spx_cg_solve. */
 typedef struct {
@@ -354,9 +381,14 @@ spx_status spx_cg_solve(const spx_plan *plan, double lambda, const int32_t *l2g,
  *     ignored) and the call synchronises that stream.
  *   - The plan's launch tiles must already exist: run spx_cg_solve once, or
  *     spx_helmholtz in each precision used and spx_helmholtz_diag in FP64,
- *     on the plan first; otherwise SPX_ERR_INVALID_ARG.
- *   - The first call on a device looks up the array's device address (once
- *     per device); make that first call before any stream capture.
+ *     on the plan first; otherwise SPX_ERR_INVALID_ARG, x untouched.
+ *   - The array is reserved on a device when this library's solver code is
+ *     loaded there.  spx_plan_create loads it and looks up the array's
+ *     device address with that device current (once per device and CUDA
+ *     context), so a solve on a plan's device finds everything in place.
+ *     Only a first call in a context where no plan was created does that
+ *     set-up itself (and may reserve the array then); make such a first
+ *     call before any stream capture.
  *   - Every call on a device shares the one array and it keeps the previous
  *     call's contents (the solver re-initialises what it needs); calls that
  *     overlap on the GPU (other threads or streams) race on it and must be

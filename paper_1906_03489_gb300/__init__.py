@@ -8,7 +8,7 @@ adjoint of H with respect to its coefficient fields behind ``torch.autograd``;
 periodic C0 assembly and a mixed-precision Jacobi-PCG solver.
 """
 from ._lib import SpxError, lib  # noqa: F401
-from .binding import (Plan, assemble, basis_tables, bwd_trans, cg_solve, cg_workspace_bytes,  # noqa: F401
+from .binding import (Plan, assemble, basis_tables, bwd_trans, cg_solve, cg_workspace_bytes, dot,  # noqa: F401
                       fwd_trans, gather, geom_factors, helmholtz, helmholtz_adjoint, helmholtz_diag, integral,
                       iproduct, phys_deriv, sensor, adapt_orders)
 from .autograd import HelmholtzFn, helmholtz_ad  # noqa: F401

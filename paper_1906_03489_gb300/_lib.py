@@ -69,6 +69,7 @@ SIGNATURES = {
     "spx_adapt_orders": (I32, [I64, P, P, D, D, I32, I32, P]),
     "spx_gather": (I32, [P, I32, P, I64, P, P, P]),
     "spx_assemble": (I32, [P, I32, P, I64, P, P, P]),
+    "spx_dot": (I32, [P, I32, I64, P, P, P, P]),
     "spx_cg_workspace_bytes": (I32, [P, I64, C.POINTER(CgOpts), C.POINTER(C.c_size_t)]),
     "spx_cg_solve": (I32, [P, D, P, I64, P, P, P, C.c_size_t, C.POINTER(CgOpts), C.POINTER(CgResult), P]),
     "spx_cg_solve_noalloc": (I32, [P, D, P, I64, P, P, C.POINTER(CgOpts), C.POINTER(CgResult), P]),

@@ -13,7 +13,8 @@ from ._lib import SPX_F32, SPX_F64, OPS, CgOpts, CgResult, PlanDesc, SpxError, c
 
 __all__ = ["Plan", "basis_tables", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz", "fwd_trans",
            "integral", "sensor", "adapt_orders",
-           "helmholtz_adjoint", "helmholtz_diag", "gather", "assemble", "cg_workspace_bytes", "cg_solve", "SpxError"]
+           "helmholtz_adjoint", "helmholtz_diag", "gather", "assemble", "dot", "cg_workspace_bytes", "cg_solve",
+           "SpxError"]
 
 
 def _p(t):
@@ -229,6 +230,17 @@ def assemble(plan, l2g, local, n_global, out=None):
     out = torch.empty(int(n_global), dtype=local.dtype, device=local.device) if out is None else out
     check(lib().spx_assemble(plan.handle, _code(local.dtype), _p(l2g), int(n_global), _p(local), _p(out),
                              _stream()))
+    return out
+
+
+def dot(plan, a, b, out=None):
+    """<a, b> at FP64 accuracy as a device FP64 scalar tensor (the solver's reduction)."""
+    _dev(a, "a")
+    _dev(b, "b")
+    if a.dtype != b.dtype or a.numel() != b.numel():
+        raise TypeError("a and b must have the same dtype and length")
+    out = torch.empty((), dtype=torch.float64, device=a.device) if out is None else out
+    check(lib().spx_dot(plan.handle, _code(a.dtype), a.numel(), _p(a), _p(b), _p(out), _stream()))
     return out
 
 

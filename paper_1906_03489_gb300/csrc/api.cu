@@ -230,6 +230,14 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
       e = cudaMemcpy(p->d_quad_off, p->quad_off.data(), (p->E + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cleanup(e, "cudaMemcpy(plan metadata)");
   }
+  {  // the allocation-free solver's workspace: reserved here (module load), not inside a solve
+    void* ws = nullptr;
+    const spx_status st = noalloc_workspace(&ws);
+    if (st != SPX_OK) {
+      spx_plan_destroy(p);
+      return st;
+    }
+  }
   // default tiles: fit shared memory with 2 stages
   for (int op = 0; op < OP_KINDS; ++op) {
     for (int dt = 0; dt < 2; ++dt) {

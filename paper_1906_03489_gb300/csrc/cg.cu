@@ -29,6 +29,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "dot_acc.cuh"
 #include "spx_internal.h"
 
@@ -977,6 +979,30 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
 }
 
 // ---------------------------------------------------------------------------
+// <a, b> at FP64 accuracy (the PCG inner products, exposed on their own):
+// per-thread DotAcc partials, the fixed-order grid reduction, the result
+// written by the last block.  Fixed grid (2 blocks per SM): reproducible.
+template <typename T, int V>
+__global__ void __launch_bounds__(kRedThreads) dot_kernel(const T* __restrict__ a, const T* __restrict__ b,
+                                                          int64_t n, double* partials, unsigned int* ticket,
+                                                          double* out) {
+  DotAcc<T> acc;
+  const int64_t S = int64_t(gridDim.x) * blockDim.x, t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t np = n / V;
+  for (int64_t i = t0; i < np; i += S) {
+    const Pack<T, V> av = ldp<T, V>(a, i), bv = ldp<T, V>(b, i);
+#pragma unroll
+    for (int c = 0; c < V; ++c) acc.add(av.v[c], bv.v[c]);
+  }
+  for (int64_t g = np * V + t0; g < n; g += S) acc.add(a[g], b[g]);
+  double r, unused;
+  if (grid_reduce2(acc.value(), 0.0, partials, ticket, &r, &unused)) {
+    *out = r;
+    *ticket = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free solve: the workspace is a fixed array in the module's own
 // device memory.  It exists on every device that loads this library, from
 // module load until process exit, and is shared by every call on that device.
@@ -985,28 +1011,91 @@ static __device__ __align__(256) unsigned char g_noalloc_ws[SPX_CG_NOALLOC_BYTES
 
 std::mutex g_noalloc_mu;
 constexpr int kMaxDevices = 64;
-void* g_noalloc_addr[kMaxDevices] = {};
+struct NoallocAddr {
+  unsigned long long ctx_id = 0;   // CUDA context the address belongs to (0: none yet)
+  void* addr = nullptr;
+};
+NoallocAddr g_noalloc[kMaxDevices];
 
-// Device address of g_noalloc_ws for the current device, looked up once per
-// device (the host-side symbol is only a handle, never a device pointer).
+}  // namespace
+
+// Device address of g_noalloc_ws on the current device, looked up with that
+// device current (the host-side symbol is only a handle, never a device
+// pointer) once per device and context: the cache is keyed on the context's
+// unique id, so a context created after a cudaDeviceReset gets a fresh
+// lookup instead of a stale address.  The lookup loads this file's device
+// code on the device if it is not loaded yet, which is when the array is
+// reserved; spx_plan_create calls this, so a solve on a plan's device finds
+// the address cached.
 spx_status noalloc_workspace(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(SPX_ERR_UNSUPPORTED, "cg_solve_noalloc: device ordinal too large");
+  if (dev < 0 || dev >= kMaxDevices) return fail(SPX_ERR_UNSUPPORTED, "no-alloc workspace: device ordinal too large");
+  e = cudaFree(nullptr);   // makes the device's primary context current (allocates nothing)
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFree(NULL)");
+  // driver entry points through the runtime (the library does not link the
+  // driver library itself, so it still loads where no driver is installed)
+  using GetCurrentFn = CUresult (*)(CUcontext*);
+  using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!get_current || !get_id) {
+      void* f0 = nullptr;
+      void* f1 = nullptr;
+      cudaDriverEntryPointQueryResult q0, q1;
+      if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+          cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+          q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+        return fail(SPX_ERR_CUDA, "no-alloc workspace: driver entry points cuCtxGetCurrent / cuCtxGetId not found");
+      get_current = reinterpret_cast<GetCurrentFn>(f0);
+      get_id = reinterpret_cast<GetIdFn>(f1);
+    }
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return fail(SPX_ERR_CUDA, "no-alloc workspace: no current CUDA context");
   std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  NoallocAddr& c = g_noalloc[dev];
+  if (c.ctx_id != id || !c.addr) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_ws);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc workspace)");
-    g_noalloc_addr[dev] = p;
+    c.ctx_id = id;
+    c.addr = p;
   }
-  *out = g_noalloc_addr[dev];
+  *out = c.addr;
   return SPX_OK;
 }
 
-}  // namespace
 }  // namespace spx
+
+extern "C" spx_status spx_dot(const spx_plan* plan, spx_dtype dt, int64_t n, const void* a, const void* b,
+                              double* result, void* stream) {
+  if (!plan || !result || n < 0 || (n && (!a || !b))) return fail(SPX_ERR_INVALID_ARG, "dot: bad argument");
+  if (dt != SPX_F64 && dt != SPX_F32) return fail(SPX_ERR_INVALID_ARG, "dot: bad dtype");
+  const size_t sz = dt == SPX_F64 ? 8 : 4;
+  if ((reinterpret_cast<uintptr_t>(a) % sz) || (reinterpret_cast<uintptr_t>(b) % sz) ||
+      (reinterpret_cast<uintptr_t>(result) % 8))
+    return fail(SPX_ERR_INVALID_ARG, "dot: buffer not aligned to its element size");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int grid = plan->num_sms * 2;   // 2 partials per block fit the plan's num_sms * 4 values
+  const bool v16 = !(reinterpret_cast<uintptr_t>(a) & 15) && !(reinterpret_cast<uintptr_t>(b) & 15);
+  if (dt == SPX_F64) {
+    const double *x = static_cast<const double*>(a), *y = static_cast<const double*>(b);
+    if (v16) dot_kernel<double, 2><<<grid, kRedThreads, 0, st>>>(x, y, n, plan->d_partials, plan->d_ticket, result);
+    else dot_kernel<double, 1><<<grid, kRedThreads, 0, st>>>(x, y, n, plan->d_partials, plan->d_ticket, result);
+  } else {
+    const float *x = static_cast<const float*>(a), *y = static_cast<const float*>(b);
+    if (v16) dot_kernel<float, 4><<<grid, kRedThreads, 0, st>>>(x, y, n, plan->d_partials, plan->d_ticket, result);
+    else dot_kernel<float, 1><<<grid, kRedThreads, 0, st>>>(x, y, n, plan->d_partials, plan->d_ticket, result);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e, "dot kernel launch");
+}
 
 extern "C" spx_status spx_cg_solve(const spx_plan* plan, double lambda, const int32_t* l2g, int64_t n_global,
                                    const double* f, double* x, void* workspace, size_t ws_bytes,

@@ -126,6 +126,10 @@ spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* 
 // Even-odd coefficients appended to a per-order table (EOLayout).
 void eo_tables(int P, int Q, double* tab);
 
+// Device address of the allocation-free solver's built-in workspace on the
+// current device (looked up once per device and CUDA context; cg.cu).
+spx_status noalloc_workspace(void** out);
+
 // Blocks per SM of the spx_integral reduction (fixed: its sums are
 // reproducible); the plan's partials buffer holds one FP64 value per block.
 constexpr int kIntegralBlocksPerSM = 4;

@@ -4,15 +4,19 @@
 A step is one application of the Helmholtz operator H = lambda M + L (BwdTrans,
 reference gradient, pointwise geometric factors, transposed gradient and
 IProductWRTBase fused in one kernel launch) to every element of the workload
-mesh: by default 32^3 curved hexes, P = 4, Q = 6, the operator applied in FP32
-(the precision whose roofline is HBM).  Prints one JSON line.
+mesh: by default 32^3 curved hexes, P = 4, Q = 6, the operator applied in FP64
+(the arithmetic of the workload), which on this part is bound by the FP64 pipe:
+its roofline divides by the FP64 peak measured in the same run by the probe
+kernels of csrc/peak_probe.cu.  The FP32 apply of the same workload (bound by
+HBM) is reported under "f32" with its own roofline and end-to-end figure.
+Prints one JSON line.
 
 Besides the timed steps it reports, each measured separately after the timed
-region: the FP64 apply of the same workload (ALU roofline), PhysDeriv, the
-variable-order workload (24^3 hexes, P_e in 2..8), the adjoint workload (16^3
-hexes, P = 6) and the periodic solve of the 48^3 workload to a 1e-10 relative
-residual in FP32-inner + FP64 refinement (restarted, and with reliable updates)
-and in all-FP64 CG.
+region and each with its roofline: PhysDeriv, BwdTrans, IProduct, FwdTrans,
+Integral (both precisions) and the sensor, the variable-order workload (24^3
+hexes, P_e in 2..8), the adjoint workload (16^3 hexes, P = 6) and the periodic
+solve of the 48^3 workload to a 1e-10 relative residual in FP32-inner + FP64
+refinement (restarted, and with reliable updates) and in all-FP64 CG.
 
 Multi-GPU (torchrun, one rank per GPU): every rank applies the operator to
 its own copy of the workload (independent element partitions, no exchange):
@@ -48,8 +52,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 ALU peak: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 ALU peak derived from unit counts and the maximum SM clock: 152 SMs x
+# 2 FP64 FMA per clock x 2 flop x 2.07 GHz.  Reported beside the measured
+# peak (fp_peaks) for context; the roofline divides by the measured one.
+FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def helm_bytes_per_elem(P, Q, sz, dim=3):
@@ -58,12 +64,91 @@ def helm_bytes_per_elem(P, Q, sz, dim=3):
 
 
 def helm_flops_per_elem(P, Q):
+    """Algorithmic flops of one element's Helmholtz apply (direct 1D contractions)."""
     n = P + 1
     bwd = n ** 3 * Q + n ** 2 * Q ** 2 + n * Q ** 3
     return 2 * (2 * bwd + 6 * Q ** 4) + 20 * Q ** 3
 
 
-# Sources of the FP32 Helmholtz kernel and its launcher (what its ncu counters depend on).
+def _eo_ops(P, Q):
+    """(flops, FP64 instructions) of the even-odd 1D contractions of the
+    Helmholtz bodies: B and dB (n -> Q), B^T (Q -> n) and D / D^T (Q -> Q).
+    A product started from zero is one multiply (1 flop), every other term
+    one FMA (2 flops); the sums and differences of the even-odd split are
+    adds."""
+    H, Hc = Q // 2, (Q + 1) // 2
+    nodd = len([b for b in range(1, P) if b % 2])
+    nev = len([b for b in range(2, P) if b % 2 == 0])
+    b = (2 + Hc * (1 + 2 * nodd) + H * (3 + 2 * nev), 2 + Hc * (1 + nodd) + H * (3 + nev))
+    db = (2 + Hc * (1 + 2 * nev) + H * (3 + 2 * nodd), 2 + Hc * (1 + nev) + H * (3 + nodd))
+    bt_f, bt_i = 2 * H + (2 * Hc - 1) + (2 * H - 1) + 2, 2 * H + Hc + H + 2
+    for k in range(1, P):
+        m = Hc if k % 2 else H
+        bt_f, bt_i = bt_f + 2 * m - 1, bt_i + m
+    odd = Q % 2
+    d = (2 * H + H * (4 * H + 2 * odd) + odd * (2 * H - 1), 2 * H + H * (2 * H + odd + 2) + odd * H)
+    return b, db, (bt_f, bt_i), d
+
+
+def helm_executed_ops_per_elem(P, Q):
+    """(flops, FP64 instructions) the 3D Helmholtz body executes per element
+    (no kappa field, constant lambda): B along xi_1, xi_2 on n^2 and n Q
+    pencils and along xi_3 on Q^2 columns, where dB also gives the xi_3
+    gradient; D along xi_1, xi_2 and D^T along all three directions on Q^2
+    pencils / columns; per quadrature point 3 multiplies and 6 FMAs for
+    G grad u, one multiply for lambda JW, one FMA adding the mass term and two
+    adds joining the three transposed-gradient parts; B^T back to the modes
+    on Q^2, n Q and n^2 pencils."""
+    n = P + 1
+    b, db, bt, d = _eo_ops(P, Q)
+    terms = [(n * n + n * Q + Q * Q, b), (Q * Q, db), (5 * Q * Q, d), (Q * Q + n * Q + n * n, bt)]
+    fl = sum(k * x[0] for k, x in terms) + Q ** 3 * (15 + 1 + 2 + 2)
+    ins = sum(k * x[1] for k, x in terms) + Q ** 3 * (9 + 1 + 1 + 2)
+    return fl, ins
+
+
+def fp_peaks(torch, sampler_index=0):
+    """Arithmetic peaks measured on this GPU by the committed probe kernels
+    (csrc/peak_probe.cu): TFLOP/s of DFMA, DMMA (m8n8k4, m16n8k16), FFMA and
+    FFMA2, each timed with CUDA events after a warm-up launch, the SM clock
+    sampled meanwhile; plus the DFMA/DMMA sharing test."""
+    import ctypes as C
+    lib = C.CDLL(os.path.join(ROOT, "paper_1906_03489_gb300", "lib", "libspx_probe.so"))
+    f = lib.spx_probe_rate
+    f.restype = C.c_int
+    f.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)]
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    iters = {0: 1200, 1: 150, 2: 150, 3: 60000, 4: 30000, 5: 400}
+    names = {0: "dfma", 1: "dmma_m8n8k4", 2: "dmma_m16n8k16", 3: "ffma", 4: "ffma2", 5: "dfma_dmma_mixed"}
+    out, raw = {}, {}
+    with ClockSampler(sampler_index) as clk:
+        for k in range(6):
+            fl, ms = C.c_double(), C.c_float()
+            rc = f(k, 4, max(1, iters[k] // 10), st, C.byref(fl), C.byref(ms))     # warm-up
+            if rc == 0:
+                rc = f(k, 4, iters[k], st, C.byref(fl), C.byref(ms))
+            if rc != 0:
+                out[names[k]] = {"error": rc}
+                continue
+            raw[k] = (fl.value, ms.value * 1e-3)
+            out[names[k]] = round(fl.value / (ms.value * 1e-3) / 1e12, 4)
+    if all(k in raw for k in (0, 1, 5)):
+        # the mixed launch: its DFMA half and its DMMA half at the rates measured alone
+        fl5, t5 = raw[5]
+        fl_f = fl5 * 64 / (64 + 512)
+        t_f = fl_f / (raw[0][0] / raw[0][1])
+        t_m = (fl5 - fl_f) / (raw[1][0] / raw[1][1])
+        out["dfma_dmma_mixed_s"] = {"measured": round(t5, 5), "if_one_unit": round(t_f + t_m, 5),
+                                    "if_separate_units": round(max(t_f, t_m), 5)}
+    fp64 = [out[n] for n in ("dfma", "dmma_m8n8k4", "dmma_m16n8k16") if isinstance(out.get(n), float)]
+    out["fp64_peak_tflops"] = max(fp64) if fp64 else None
+    out["clocks"] = clk.summary()
+    out["how"] = ("probe kernels of csrc/peak_probe.cu, 4 blocks x 256 threads per SM, 8 independent chains per "
+                  "thread, CUDA events; fp64_peak = the fastest FP64 kind")
+    return out
+
+
+# Sources of the Helmholtz kernels and their launcher (what their ncu counters depend on).
 HELM_SOURCES = ("helm_pair.cuh", "op_kernel.cuh", "lanes.cuh", "kernel_params.h", "device_common.cuh",
                 "launch_ops.cuh", "smem_layout.h")
 
@@ -216,69 +301,36 @@ def timed(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
-def run_ours(a):
-    import torch
-    import paper_1906_03489_gb300 as spx
-    from paper_1906_03489_gb300 import mesh, synth
-
-    world, rank, local = dist_setup()
-    if not torch.cuda.is_available():
-        raise RuntimeError("bench.py needs a CUDA GPU (there is no CPU path)")
-    spx.lib()
-    hbm_peak, peak_kind = peaks()
-    stream = torch.cuda.current_stream()
-    name = a.workload
-    w, plans, geoms, coef = make_workload(name, spx, mesh, synth, torch, copies=2)
-    P, Q = w["P"], w["P"] + 2
-    E = plans[0].E
-    dt = torch.float32
-    u = [torch.tensor(coef, device="cuda", dtype=dt) for _ in plans]
-    out = [torch.empty_like(x) for x in u]
-    if a.tile:
-        eb, nt, st = (int(x) for x in a.tile.split(","))
-        for p in plans:
-            p.set_tile("helmholtz", dt, eb, nt, st)
-    else:
-        plans[0].autotune("helmholtz", dt, u[0], out[0], reps=5)
-        tile = plans[0].get_tile("helmholtz", dt, P)
-        plans[1].set_tile("helmholtz", dt, *tile)
-    tile = plans[0].get_tile("helmholtz", dt, P)
-
+def apply_steps(spx, torch, plans, ins, outs, steps, stream, local):
+    """Times `steps` Helmholtz applies alternating between the two copies of
+    the workload (inputs of both copies exceed the L2), CUDA events on the
+    launching stream, the SM clock sampled meanwhile."""
     def step(i):
         k = i & 1
-        spx.helmholtz(plans[k], u[k], lam=1.0, out=out[k])
-
-    for i in range(a.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    barrier(world)
+        spx.helmholtz(plans[k], ins[k], lam=1.0, out=outs[k])
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(a.steps):
+        for i in range(steps):
             step(i)
         e1.record(stream)
         e1.synchronize()
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / a.steps
-    barrier(world)
-    ms = max_over_ranks(ms, world)
-    dofs = E * (P + 1) ** 3
-    value = world * dofs / (ms * 1e-3) / 1e9
-    bytes_launch = E * helm_bytes_per_elem(P, Q, 4)
-    achieved = bytes_launch / (ms * 1e-3) / 1e9
-    traffic = profiled_traffic("helmholtz_f32_hex32.txt")
+    return e0.elapsed_time(e1) / steps, clk.summary()
 
-    # end to end through the C ABI with host buffers: every step copies its
-    # input u from pinned host memory, applies the operator and copies the
-    # result y back.  Served as a pipeline on three streams with two device
-    # buffers each: the upload of step i+1 and the download of step i-1 run on
-    # the copy engines while step i computes.
+
+def e2e_pipeline(spx, torch, plan, coef, dt, k_e2e):
+    """The apply end to end through the public API with host buffers: every
+    step copies its input from pinned host memory, applies the operator and
+    copies the result back.  Served as a pipeline on three streams with two
+    device buffers each: the upload of step i+1 and the download of step i-1
+    run on the copy engines while step i computes.  Returns (ms per step,
+    bytes up, bytes down per step)."""
     uh = torch.tensor(coef, dtype=dt).pin_memory()
-    yh = [torch.empty(plans[0].n_coef, dtype=dt).pin_memory() for _ in range(2)]
-    ud = [torch.empty_like(u[0]) for _ in range(2)]
-    yd = [torch.empty_like(u[0]) for _ in range(2)]
+    yh = [torch.empty(plan.n_coef, dtype=dt).pin_memory() for _ in range(2)]
+    ud = [torch.empty(plan.n_coef, dtype=dt, device="cuda") for _ in range(2)]
+    yd = [torch.empty_like(ud[0]) for _ in range(2)]
     s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_comp = [torch.cuda.Event() for _ in range(2)]
@@ -296,7 +348,7 @@ def run_ours(a):
         with torch.cuda.stream(s_comp):
             s_comp.wait_event(ev_in[k])
             s_comp.wait_event(ev_out[k])         # yd[k] downloaded by step i-2
-            spx.helmholtz(plans[0], ud[k], lam=1.0, out=yd[k])
+            spx.helmholtz(plan, ud[k], lam=1.0, out=yd[k])
             ev_comp[k].record(s_comp)
         with torch.cuda.stream(s_out):
             s_out.wait_event(ev_comp[k])
@@ -306,7 +358,6 @@ def run_ours(a):
     for i in range(4):
         e2e_step(i)
     torch.cuda.synchronize()
-    k_e2e = max(10, a.steps // 10)
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0e.record(s_in)
     for i in range(k_e2e):
@@ -314,40 +365,136 @@ def run_ours(a):
     t1e.record(s_out)          # after the last download, which follows every earlier step
     t1e.synchronize()
     torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(t0e.elapsed_time(t1e) / k_e2e, world)
-    e2e_value = world * dofs / (ms_e2e * 1e-3) / 1e9
+    nb = uh.numel() * uh.element_size()
+    return t0e.elapsed_time(t1e) / k_e2e, nb, nb
+
+
+def tune_pair(plans, dtype, ins, outs, P, tile):
+    if tile:
+        eb, nt, st = (int(x) for x in tile.split(","))
+        for p in plans:
+            p.set_tile("helmholtz", dtype, eb, nt, st)
+    else:
+        plans[0].autotune("helmholtz", dtype, ins[0], outs[0], reps=5)
+        t = plans[0].get_tile("helmholtz", dtype, P)
+        plans[1].set_tile("helmholtz", dtype, *t)
+    return plans[0].get_tile("helmholtz", dtype, P)
+
+
+def run_ours(a):
+    import torch
+    import paper_1906_03489_gb300 as spx
+    from paper_1906_03489_gb300 import mesh, synth
+
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (there is no CPU path)")
+    spx.lib()
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    name = a.workload
+    w, plans, geoms, coef = make_workload(name, spx, mesh, synth, torch, copies=2)
+    P, Q = w["P"], w["P"] + 2
+    E = plans[0].E
+    dofs = E * (P + 1) ** 3
+    # arithmetic peaks of this GPU (the FP64 roof of the headline)
+    fpk = fp_peaks(torch, local)
+    fp64_peak = fpk["fp64_peak_tflops"]
+
+    # ---- headline: the FP64 apply (FP64 pipe bound on this part) ----------
+    u64 = [torch.tensor(coef, device="cuda", dtype=torch.float64) for _ in plans]
+    o64 = [torch.empty_like(x) for x in u64]
+    tile64 = tune_pair(plans, torch.float64, u64, o64, P, a.tile64)
+    for i in range(a.warmup):
+        spx.helmholtz(plans[i & 1], u64[i & 1], lam=1.0, out=o64[i & 1])
+    torch.cuda.synchronize()
+    barrier(world)
+    ms, clk = apply_steps(spx, torch, plans, u64, o64, a.steps, stream, local)
+    barrier(world)
+    ms = max_over_ranks(ms, world)
+    value = world * dofs / (ms * 1e-3) / 1e9
+    fl_launch = E * helm_flops_per_elem(P, Q)
+    ex_fl, ex_ins = helm_executed_ops_per_elem(P, Q)
+    bytes64 = E * helm_bytes_per_elem(P, Q, 8)
+    achieved = fl_launch / (ms * 1e-3) / 1e12
+    ms_e2e, up, down = e2e_pipeline(spx, torch, plans[0], coef, torch.float64, max(10, a.steps // 2))
+    ms_e2e = max_over_ranks(ms_e2e, world)
+
+    # ---- the FP32 apply (HBM bound) ---------------------------------------
+    u32 = [torch.tensor(coef, device="cuda", dtype=torch.float32) for _ in plans]
+    o32 = [torch.empty_like(x) for x in u32]
+    tile32 = tune_pair(plans, torch.float32, u32, o32, P, a.tile)
+    k32 = max(a.steps, 200)
+    for i in range(max(a.warmup, 20)):
+        spx.helmholtz(plans[i & 1], u32[i & 1], lam=1.0, out=o32[i & 1])
+    torch.cuda.synchronize()
+    barrier(world)
+    ms32, clk32 = apply_steps(spx, torch, plans, u32, o32, k32, stream, local)
+    barrier(world)
+    ms32 = max_over_ranks(ms32, world)
+    bytes32 = E * helm_bytes_per_elem(P, Q, 4)
+    ach32 = bytes32 / (ms32 * 1e-3) / 1e9
+    ms32_e2e, up32, down32 = e2e_pipeline(spx, torch, plans[0], coef, torch.float32, max(10, k32 // 10))
+    ms32_e2e = max_over_ranks(ms32_e2e, world)
 
     extras = {}
     if a.extras and rank == 0:
-        extras = measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak)
+        extras = measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak, fp64_peak,
+                                fpk.get("ffma2") if isinstance(fpk.get("ffma2"), float) else None)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(name, seconds=a.cpu_seconds)
     if rank == 0:
+        mesh_desc = f"{w['N']}^3 curved hexes (x'=x+{w['amp']} sin2piy sin2piz)"
         line = {
-            "metric": METRIC, "value": round(value, 3), "unit": "GDOF/s", "n_gpus": world, "steps": a.steps,
+            "metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": name, "mesh": f"{w['N']}^3 curved hexes (x'=x+{w['amp']} sin2piy sin2piz)",
-                       "P": P, "Q": Q, "elements_per_gpu": E, "local_dofs_per_gpu": dofs,
-                       "op": "Helmholtz H=lambda M+L, lambda=1, unassembled, FP32 FMA/FP32 accumulate",
-                       "tile_eb_threads_stages": list(tile),
-                       "l2": f"inputs {2 * bytes_launch / 1e6:.0f} MB per step pair alternate between two "
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "mesh": mesh_desc, "P": P, "Q": Q, "elements_per_gpu": E,
+                       "local_dofs_per_gpu": dofs,
+                       "op": "Helmholtz H=lambda M+L, lambda=1, unassembled, FP64 (FP64 FMA, FP64 accumulation)",
+                       "tile_eb_threads_stages": list(tile64),
+                       "l2": f"inputs {2 * bytes64 / 1e6:.0f} MB per step pair alternate between two "
                              f"independent copies (> {L2_BYTES / 1e6:.0f} MB L2): no L2 flush",
                        "parallelism": f"replica per GPU x{world}"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                         "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
-                         "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": bytes_launch,
-                         "bytes_model": "per element (2 (P+1)^3 coefficients + 7 Q^3 geometric factors) x 4 B"},
-            "e2e": {"value": round(e2e_value, 3), "unit": "GDOF/s", "h2d_bytes_per_step": int(uh.numel() * 4),
-                    "d2h_bytes_per_step": int(yh[0].numel() * 4), "ms_per_step": round(ms_e2e, 4),
-                    "steps": k_e2e,
+            "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": round(achieved / fp64_peak, 4) if fp64_peak else None,
+                         "traffic": profiled_traffic("helmholtz_f64_hex32.txt"),
+                         "peak_kind": "measured: fastest FP64 probe kind on this GPU in this run (fp_peaks)",
+                         "algorithmic_flops_per_launch": fl_launch,
+                         "flops_model": "per element 2 (2 (n^3 Q + n^2 Q^2 + n Q^3) + 6 Q^4) + 20 Q^3 "
+                                        "(direct 1D contractions, collocation gradient)",
+                         "executed": {"flops_per_launch": E * ex_fl, "fp64_instructions_per_launch": E * ex_ins,
+                                      "tflops": round(E * ex_fl / (ms * 1e-3) / 1e12, 4),
+                                      "fp64_pipe_frac": round(2 * E * ex_ins / (ms * 1e-3) / 1e12 / fp64_peak, 4)
+                                      if fp64_peak else None,
+                                      "note": "even-odd contractions: fewer flops than the algorithmic count; "
+                                              "fp64_pipe_frac counts every FP64 instruction (add, mul, fma) as "
+                                              "one pipe slot of the DFMA rate"},
+                         "derived_peak_tflops": round(FP64_DERIVED_TFLOPS, 4),
+                         "hbm_frac": round(bytes64 / (ms * 1e-3) / 1e9 / hbm_peak, 4)},
+            "e2e": {"value": round(world * dofs / (ms_e2e * 1e-3) / 1e9, 4), "unit": "GDOF/s",
+                    "h2d_bytes_per_step": int(up), "d2h_bytes_per_step": int(down), "ms_per_step": round(ms_e2e, 4),
+                    "steps": max(10, a.steps // 2),
                     "pipeline": "pinned host buffers; 3 streams, 2 device buffers each: the upload of step i+1 "
                                 "and the download of step i-1 overlap the apply of step i"},
             "gpu_launches": a.steps,
-            "clocks": clk.summary(),
+            "clocks": clk,
             "cpu_baseline": cpu,
+            "f32": {
+                "value": round(world * dofs / (ms32 * 1e-3) / 1e9, 4), "unit": "GDOF/s", "steps": k32,
+                "ms_per_step": round(ms32, 5), "dtype": "f32",
+                "op": "Helmholtz H=lambda M+L, lambda=1, unassembled, FP32 FMA/FP32 accumulate",
+                "tile_eb_threads_stages": list(tile32),
+                "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": hbm_peak, "unit": "GB/s",
+                             "frac": round(ach32 / hbm_peak, 4), "traffic": profiled_traffic("helmholtz_f32_hex32.txt"),
+                             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes32,
+                             "bytes_model": "per element (2 (P+1)^3 coefficients + 7 Q^3 geometric factors) x 4 B"},
+                "e2e": {"value": round(world * dofs / (ms32_e2e * 1e-3) / 1e9, 4), "unit": "GDOF/s",
+                        "h2d_bytes_per_step": int(up32), "d2h_bytes_per_step": int(down32),
+                        "ms_per_step": round(ms32_e2e, 4), "steps": max(10, k32 // 10)},
+                "clocks": clk32},
+            "fp_peaks": fpk,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)
@@ -356,27 +503,50 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak):
-    """Other operators / precisions / workloads, each timed after warm-up with CUDA events."""
+def op_flops_per_elem(op, P, Q):
+    """Algorithmic flops per 3D element of the operators besides Helmholtz
+    (direct 1D contractions, as the generic kernel executes them)."""
+    n = P + 1
+    bwd = 2 * (n ** 3 * Q + n ** 2 * Q ** 2 + n * Q ** 3)
+    mass = 2 * bwd + Q ** 3                      # BwdTrans, JW, IProduct
+    pre = 3 * 2 * n ** 4                         # (M1^-1) along three directions
+    return {"bwd_trans": bwd, "iproduct": bwd + Q ** 3, "phys_deriv": 6 * Q ** 4 + 18 * Q ** 3,
+            "integral": 2 * Q ** 3,
+            # b = IProduct(f), z = K^-1 b, then one PCG step (the preconditioner is exact where det J is
+            # constant on the element, as on this mesh): M p, K^-1 r, and ~12 n^3 of vector work
+            "fwd_trans": (bwd + Q ** 3) + 2 * pre + mass + 12 * n ** 3,
+            # u^T M u, one restricted PCG step as above, then d^T M d
+            "sensor": 3 * mass + 2 * pre + 14 * n ** 3}[op]
+
+
+def roof(ms, nbytes, nflops, fp64, hbm_peak, fp_peak):
+    """Roofline figures of one launch: HBM and ALU fractions; `bound` is the
+    FP64 pipe for FP64 kernels (machine balance about 0.2 flop/B), HBM for FP32."""
+    gbs = nbytes / ms / 1e6
+    tfl = nflops / ms / 1e9
+    r = {"ms": round(ms, 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
+         "tflops": round(tfl, 4), "algorithmic_bytes": int(nbytes), "algorithmic_flops": int(nflops)}
+    if fp_peak:
+        r["alu_frac"] = round(tfl / fp_peak, 4)
+    r["bound"] = "alu" if fp64 else "hbm"
+    r["frac"] = r.get("alu_frac") if fp64 else r["hbm_frac"]
+    return r
+
+
+def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak, fp64_peak, fp32_peak=None):
+    """Other operators / precisions / workloads, each timed after warm-up with
+    CUDA events, each with its roofline: FP64 kernels against the measured
+    FP64 peak (ALU), FP32 kernels against the HBM peak (their ALU fraction
+    against the measured FFMA peak beside it)."""
     ex = {}
     plan = plans[0]
     P, Q, E = 4, 6, plan.E
+    n3 = (P + 1) ** 3
     reps = 30
-    # FP64 Helmholtz: ALU bound
-    u64 = torch.tensor(coef, device="cuda")
-    o64 = torch.empty_like(u64)
-    plan.autotune("helmholtz", torch.float64, u64, o64, reps=3)
-    ms = timed(lambda: spx.helmholtz(plan, u64, out=o64), reps, stream)
-    fl = E * helm_flops_per_elem(P, Q)
-    ex["fp64"] = {"helmholtz_gdofs": round(E * 125 / ms / 1e6, 3), "ms": round(ms, 4),
-                  "roofline": {"bound": "alu", "achieved": round(fl / ms / 1e9, 4),
-                               "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                               "frac": round(fl / ms / 1e9 / FP64_PEAK_TFLOPS, 4),
-                               "flops_per_launch": fl},
-                  "hbm_frac": round(E * helm_bytes_per_elem(P, Q, 8) / ms / 1e6 / hbm_peak, 4)}
-    # PhysDeriv, BwdTrans, IProduct (FP32 and FP64), each with its autotuned tile
     ops = {}
     for dt, sz in ((torch.float32, 4), (torch.float64, 8)):
+        fp64 = dt == torch.float64
+        pk = fp64_peak if fp64 else fp32_peak
         c = torch.tensor(coef, device="cuda", dtype=dt)
         f = spx.bwd_trans(plan, c)
         outs = [torch.empty_like(f) for _ in range(3)]
@@ -384,45 +554,42 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
         packed = torch.empty(3 * plan.n_quad, dtype=dt, device="cuda")
         for op, fn, nbytes, tin, tout in (
                 ("phys_deriv", lambda: spx.phys_deriv(plan, f, outs), E * 13 * Q ** 3 * sz, f, packed),
-                ("bwd_trans", lambda: spx.bwd_trans(plan, c, f), E * (125 + Q ** 3) * sz, c, f),
-                ("iproduct", lambda: spx.iproduct(plan, f, c), E * (2 * Q ** 3 + 125) * sz, f, c)):
+                ("bwd_trans", lambda: spx.bwd_trans(plan, c, f), E * (n3 + Q ** 3) * sz, c, f),
+                ("iproduct", lambda: spx.iproduct(plan, f, c), E * (2 * Q ** 3 + n3) * sz, f, c)):
             plan.autotune(op, dt, tin, tout, reps=5)
             fn()
             ms = timed(fn, reps, stream)
-            ops[f"{op}_{tag}"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
-                                  "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4),
-                                  "tile_eb_threads_stages": list(plan.get_tile(op, dt, P))}
+            ops[f"{op}_{tag}"] = roof(ms, nbytes, E * op_flops_per_elem(op, P, Q), fp64, hbm_peak, pk)
+            ops[f"{op}_{tag}"]["tile_eb_threads_stages"] = list(plan.get_tile(op, dt, P))
         # FwdTrans (elemental preconditioned CG in one launch; reads f and JW, writes the coefficients)
         # and Integral (reads f and JW)
         f = spx.bwd_trans(plan, torch.tensor(coef, device="cuda", dtype=dt))
         cf = torch.empty(plan.n_coef, dtype=dt, device="cuda")
         plan.autotune("fwd_trans", dt, f, cf, reps=3)
         ms = timed(lambda: spx.fwd_trans(plan, f, cf), reps, stream)
-        nbytes = E * (2 * Q ** 3 + 125) * sz
-        ops[f"fwd_trans_{tag}"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
-                                   "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4),
-                                   "tile_eb_threads_stages": list(plan.get_tile("fwd_trans", dt, P)),
-                                   "max_err_vs_input_coefficients": (cf.double() - torch.tensor(coef, device="cuda")
-                                                                     ).abs().max().item()}
-        if dt == torch.float64:   # adaptive-order sensor (FP64): reads the coefficients and JW, writes one value per element
+        r = roof(ms, E * (2 * Q ** 3 + n3) * sz, E * op_flops_per_elem("fwd_trans", P, Q), fp64, hbm_peak, pk)
+        r["tile_eb_threads_stages"] = list(plan.get_tile("fwd_trans", dt, P))
+        r["max_err_vs_input_coefficients"] = (cf.double() - torch.tensor(coef, device="cuda")).abs().max().item()
+        ops[f"fwd_trans_{tag}"] = r
+        if fp64:   # adaptive-order sensor (FP64): reads the coefficients and JW, writes one value per element
             cc = torch.tensor(coef, device="cuda")
             so = torch.empty(plan.E, dtype=torch.float64, device="cuda")
             plan.autotune("sensor", dt, cc, so, reps=3)
             ms = timed(lambda: spx.sensor(plan, cc, so), reps, stream)
-            nbytes = E * (125 + Q ** 3 + 1) * sz
-            ops["sensor_f64"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
-                                 "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4),
-                                 "tile_eb_threads_stages": list(plan.get_tile("sensor", dt, P))}
+            ops["sensor_f64"] = roof(ms, E * (n3 + Q ** 3 + 1) * sz, E * op_flops_per_elem("sensor", P, Q), True,
+                                     hbm_peak, pk)
+            ops["sensor_f64"]["tile_eb_threads_stages"] = list(plan.get_tile("sensor", dt, P))
         res = torch.empty((), dtype=torch.float64, device="cuda")
         ms = timed(lambda: spx.integral(plan, f, res), reps, stream)
-        nbytes = E * 2 * Q ** 3 * sz
-        ops[f"integral_{tag}"] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
-                                  "hbm_frac": round(nbytes / ms / 1e6 / hbm_peak, 4)}
+        # a reduction streaming 2 Q^3 values per element: HBM bound in both precisions
+        ops[f"integral_{tag}"] = roof(ms, E * 2 * Q ** 3 * sz, E * op_flops_per_elem("integral", P, Q), False,
+                                      hbm_peak, pk)
     ex["ops_hex32"] = ops
     # variable order workload
     wv, pv, gv, cv = make_workload("hex3d_24_varp", spx, mesh, synth, torch)
     pv = pv[0]
     nb = sum(helm_bytes_per_elem(int(p_), int(p_) + 2, 1) for p_ in pv.orders)
+    nfl = sum(helm_flops_per_elem(int(p_), int(p_) + 2) for p_ in pv.orders)
     var = {}
     for dt, sz in ((torch.float32, 4), (torch.float64, 8)):
         uu = torch.tensor(cv, device="cuda", dtype=dt)
@@ -430,10 +597,12 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
         pv.autotune("helmholtz", dt, uu, oo, reps=2)
         ms = timed(lambda: spx.helmholtz(pv, uu, out=oo), reps, stream)
         tag = "f32" if dt == torch.float32 else "f64"
-        var[tag] = {"ms": round(ms, 4), "gdofs": round(pv.n_coef / ms / 1e6, 3),
-                    "gbs": round(nb * sz / ms / 1e6, 1), "hbm_frac": round(nb * sz / ms / 1e6 / hbm_peak, 4),
-                    "tiles_eb_by_order": {int(p_): pv.get_tile("helmholtz", dt, int(p_))[0]
-                                          for p_ in sorted(set(pv.orders.tolist()))}}
+        r = roof(ms, nb * sz, nfl, dt == torch.float64, hbm_peak, fp64_peak if dt == torch.float64 else fp32_peak)
+        r["gdofs"] = round(pv.n_coef / ms / 1e6, 3)
+        r["tiles_eb_by_order"] = {int(p_): pv.get_tile("helmholtz", dt, int(p_))[0]
+                                  for p_ in sorted(set(pv.orders.tolist()))}
+        var[tag] = r
+    var["flops_model"] = "sum over elements of the per-order Helmholtz flops (P_e, Q_e = P_e + 2)"
     ex["varp_hex24"] = var
     del pv, gv
     # adjoint workload
@@ -453,7 +622,18 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
 
     fwd_bwd()
     ms = timed(fwd_bwd, 10, stream)
-    ex["adjoint_hex16_p6"] = {"fwd_bwd_ms": round(ms, 3)}
+    Pa, Qa = 6, 8
+    na, qa = (Pa + 1) ** 3, Qa ** 3
+    # forward H u and backward H g (each: coefficients in and out, 7 geometric
+    # factors, lambda and kappa fields) + the adjoint kernel (u, g in; 7 factors;
+    # g_lambda, g_kappa out); flops: three Helmholtz-sized passes (the adjoint's
+    # two BwdTrans + gradients and its pointwise work equal one apply's count)
+    nb_a = pa.E * 3 * (2 * na + 9 * qa) * 8
+    nfl_a = pa.E * 3 * helm_flops_per_elem(Pa, Qa)
+    r = roof(ms, nb_a, nfl_a, True, hbm_peak, fp64_peak)
+    r["fwd_bwd_ms"] = r.pop("ms")
+    r["model"] = "H u, H g and the adjoint kernel per step; torch's loss arithmetic not counted"
+    ex["adjoint_hex16_p6"] = r
     del pa, ga
     # 2D correctness workload (16 x 16 affine quads, P = 4, Q = 6, FP64): BwdTrans,
     # IProduct and Helmholtz once each after warm-up; latency-sized (6400 DOFs),
@@ -575,6 +755,25 @@ def run_case(a):
         torch.cuda.synchronize()
         print(json.dumps({"case": "cg", "workload": "hex3d_48_p4", "precision": a.precision,
                           "iters": info["iters"], "s": round(time.perf_counter() - t0, 4)}), flush=True)
+    elif a.case == "helm":
+        w, plans, _, coef = make_workload(a.workload, spx, mesh, synth, torch)
+        plan = plans[0]
+        P = w["P"]
+        dt = torch.float64 if a.precision == "f64" else torch.float32
+        u = torch.tensor(coef, device="cuda", dtype=dt)
+        y = torch.empty_like(u)
+        tile = a.tile64 if dt == torch.float64 else a.tile
+        if tile:   # a reproducible launch without autotuning
+            eb, nt, st = (int(x) for x in tile.split(","))
+            plan.set_tile("helmholtz", dt, eb, nt, st)
+        else:
+            plan.autotune("helmholtz", dt, u, y, reps=2)
+        spx.helmholtz(plan, u, out=y)   # warm-up (module load, tile lists)
+        ms = timed(lambda: spx.helmholtz(plan, u, out=y), max(1, a.steps), stream)
+        print(json.dumps({"case": "helm", "workload": a.workload, "dtype": str(dt), "ms": round(ms, 4),
+                          "tile": plan.get_tile("helmholtz", dt, P)}), flush=True)
+    elif a.case == "peaks":
+        print(json.dumps({"case": "peaks", "fp_peaks": fp_peaks(torch)}), flush=True)
     elif a.case == "varp":
         w, plans, _, coef = make_workload("hex3d_24_varp", spx, mesh, synth, torch)
         plan = plans[0]
@@ -618,10 +817,30 @@ def oracle_sample_rate(name, n_elem_sample, seconds, repeat=None):
     return m.E * (P + 1) ** 3 * reps / el / 1e9, m.E, reps, el
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the architecture)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(name, seconds=15.0):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     rate, ne, reps, el = oracle_sample_rate(name, 4096, seconds)
     return {"value": round(rate, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "host_cpus": os.cpu_count(),
             "sample": f"dense FP64 oracle Helmholtz on a {ne}-element sub-mesh of the same curved P=4 hexes, "
                       f"{reps} applies in {el:.1f} s (numpy/OpenBLAS, {cores} threads)"}
 
@@ -641,6 +860,7 @@ def run_reference(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "sample_elements": ne},
             "cpu_baseline": {"value": round(rate, 6), "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(), "host_cpus": os.cpu_count(),
                              "sample": f"dense FP64 oracle Helmholtz, {ne}-element sub-mesh of the same "
                                        f"curved hexes per step"},
             "e2e": {"value": round(rate, 6), "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -650,17 +870,19 @@ def run_reference(a):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hex3d_32_p4")
-    ap.add_argument("--tile", default=None, help="eb,threads,stages (skips autotuning)")
+    ap.add_argument("--tile", default=None, help="FP32 apply: eb,threads,stages (skips autotuning)")
+    ap.add_argument("--tile64", default=None, help="FP64 apply: eb,threads,stages (skips autotuning)")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--case", default="bench", choices=["bench", "cg", "varp"],
-                    help="bench: the benchmark line; cg / varp: one short run for profiling")
-    ap.add_argument("--precision", default="f32_reliable", help="cg: f64 | f32_refine | f32_reliable; varp: f32 | f64")
+    ap.add_argument("--case", default="bench", choices=["bench", "cg", "varp", "helm", "peaks"],
+                    help="bench: the benchmark line; cg / varp / helm / peaks: one short run for profiling")
+    ap.add_argument("--precision", default="f32_reliable",
+                    help="cg: f64 | f32_refine | f32_reliable; varp, helm: f32 | f64")
     ap.add_argument("--cg-maxit", type=int, default=30)
     ap.add_argument("--varp-tiles", default=None, help="varp: elements per tile of orders 2..8, e.g. 24,16,8,4,3,2,2")
     a = ap.parse_args()

@@ -17,6 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libspx.so")
+PROBE_LIB = os.path.join(LIBDIR, "libspx_probe.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,6 +45,10 @@ def units():
     return u
 
 
+# arithmetic-throughput probe of the benchmark: its own shared object
+PROBE_UNITS = [("peak_probe", "peak_probe.cu", [])]
+
+
 def source_digest():
     h = hashlib.sha256()
     for d in (CSRC, os.path.join(ROOT, "include")):
@@ -69,7 +74,8 @@ def build(jobs=None, force=False, verbose=False):
     """Compiles the library if its sources changed; returns the .so path."""
     digest = source_digest()
     stamp = os.path.join(LIBDIR, "libspx.sha256")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == digest:
+    if (not force and os.path.exists(LIB) and os.path.exists(PROBE_LIB) and os.path.exists(stamp)
+            and open(stamp).read() == digest):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
@@ -78,16 +84,23 @@ def build(jobs=None, force=False, verbose=False):
     objs, logs = [], []
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         futs = [ex.submit(compile_unit, nv, n, s, d, verbose) for n, s, d in units()]
+        pfuts = [ex.submit(compile_unit, nv, n, s, d, verbose) for n, s, d in PROBE_UNITS]
         for f in futs:
             o, log = f.result()
             objs.append(o)
             logs.append(log)
-    tmp = LIB + ".tmp"
-    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n" + r.stderr)
-    os.replace(tmp, LIB)
+        pobjs = []
+        for f in pfuts:
+            o, log = f.result()
+            pobjs.append(o)
+            logs.append(log)
+    for out, obj_list in ((LIB, objs), (PROBE_LIB, pobjs)):
+        tmp = out + ".tmp"
+        cmd = [nv] + ARCH + ["-shared", "-o", tmp] + obj_list
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n" + r.stderr)
+        os.replace(tmp, out)
     with open(stamp, "w") as f:
         f.write(digest)
     if verbose:

@@ -605,6 +605,12 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
     var["flops_model"] = "sum over elements of the per-order Helmholtz flops (P_e, Q_e = P_e + 2)"
     ex["varp_hex24"] = var
     del pv, gv
+    # GLL nodal basis (classical spectral elements) on the same 32^3 mesh, P = 4,
+    # collocated on its Q = P + 1 = 5 GLL points: B = I, no B contractions
+    try:
+        ex["nodal_hex32_p4"] = measure_nodal(spx, mesh, synth, torch, stream, hbm_peak, fp64_peak, fp32_peak)
+    except Exception as err:   # an extra: never lose the benchmark line over it
+        ex["nodal_hex32_p4"] = {"error": str(err)[:200]}
     # adjoint workload
     wa, pa, ga, ca = make_workload("hex3d_16_p6", spx, mesh, synth, torch)
     pa, ga = pa[0], ga[0]
@@ -645,6 +651,38 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
     # periodic solve of the 48^3 workload
     ex["cg_hex48"] = measure_cg(spx, mesh, synth, torch, hbm_peak)
     return ex
+
+
+def nodal_flops_per_elem(P):
+    """Collocation Helmholtz (Q = P + 1): gradient and transposed gradient along
+    three directions (6 Q^4 multiply-adds) + 20 flops per point."""
+    Q = P + 1
+    return 2 * 6 * Q ** 4 + 20 * Q ** 3
+
+
+def measure_nodal(spx, mesh, synth, torch, stream, hbm_peak, fp64_peak, fp32_peak):
+    w = synth.WORKLOADS["hex3d_32_p4"]
+    N, P = w["N"], w["P"]
+    Q = P + 1
+    plan = spx.Plan(3, N ** 3, order=P, q_offset=1, basis={P: spx.nodal_basis_tables(P, Q)})
+    g = spx.geom_factors(plan, mesh.structured_nodes(3, N, P, w["amp"]), want_xq=False)
+    plan.set_geometry(torch.float64, g["geom"], g["dxi"])
+    plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])
+    coef = synth.uniform(synth.rng(w["seed"]), plan.n_coef)
+    E = plan.E
+    out = {"basis": "Lagrange through the P+1 GLL points, collocated (Q = P + 1): B = I", "P": P, "Q": Q}
+    for dt, sz in ((torch.float64, 8), (torch.float32, 4)):
+        u = torch.tensor(coef, device="cuda", dtype=dt)
+        y = torch.empty_like(u)
+        plan.autotune("helmholtz", dt, u, y, reps=3)
+        ms = timed(lambda: spx.helmholtz(plan, u, out=y), 30, stream)
+        fp64 = dt == torch.float64
+        r = roof(ms, E * (2 * (P + 1) ** 3 + 7 * Q ** 3) * sz, E * nodal_flops_per_elem(P), fp64, hbm_peak,
+                 fp64_peak if fp64 else fp32_peak)
+        r["gdofs"] = round(plan.n_coef / ms / 1e6, 3)
+        r["tile_eb_threads_stages"] = list(plan.get_tile("helmholtz", dt, P))
+        out["f64" if fp64 else "f32"] = r
+    return out
 
 
 def measure_quad2d(spx, mesh, synth, torch, stream):

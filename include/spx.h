@@ -107,21 +107,73 @@ const char *spx_version(void);
  * ------------------------------------------------------------------------- */
 spx_status spx_basis_tables(int P, int Q, double *xi, double *w, double *B, double *dB, double *D);
 
+/* Tables of the GLL nodal basis (§2.1, the Lagrange polynomials through the
+ * P + 1 GLL points, the traditional spectral element basis), for use as a
+ * caller-supplied basis (spx_basis_desc).  Host FP64, either output may be
+ * NULL:
+ *   B[Q][P+1]   B[i][m] = l_m(xi_i), l_m the Lagrange polynomial of node m
+ *               (nodes ascending) at the Q GLL points xi_i;
+ *   dB[Q][P+1]  dB[i][m] = l_m'(xi_i).
+ * With Q = P + 1 the nodes are the quadrature points: B = I (collocation)
+ * and dB = D.  Requires 1 <= P, 2 <= Q <= 16. */
+spx_status spx_nodal_basis_tables(int P, int Q, double *B, double *dB);
+
 /* ---------------------------------------------------------------------------
  * Plans: the mesh's element count, dimension and per-element orders
  * (Collections groups of same-shape, same-basis elements, §3.3; variable
  * order per element, §4.2).
  * ------------------------------------------------------------------------- */
+/* Basis tables of one order supplied by the caller (the paper's BasisKey,
+ * §3.5 Listing lst:python, with the basis functions of §2.1 given by their
+ * values): the 1D functions phi_p, p = 0..P, of the tensor-product
+ * expansion, evaluated at the Q GLL quadrature points.  FP64, row-major,
+ * first index slowest:
+ *   B[Q][P+1]   B[i][p] = phi_p(xi_i)                               (required)
+ *   dB[Q][P+1]  dB[i][p] = phi_p'(xi_i); NULL: computed as D B.  The kernels
+ *               differentiate by D B (exact for P <= Q - 1), so a given dB
+ *               must equal D B to 1e-10 relative (else SPX_ERR_INVALID_ARG).
+ *   D[Q][Q]     collocation derivative; NULL or the GLL one
+ *   w[Q]        quadrature weights; NULL or the GLL ones
+ * The quadrature is the GLL rule on Q = P + q_offset points (the geometric
+ * factors fold its weights in), so D and w, when given, must equal the GLL
+ * tables of spx_basis_tables to 1e-12 (else SPX_ERR_UNSUPPORTED).  Any basis
+ * spanning the polynomials of degree <= P is accepted, e.g. a permutation or
+ * rescaling of the modified basis, or the Lagrange (nodal) basis through the
+ * P + 1 GLL points of §2.1 (the classical spectral element method; with
+ * q_offset = 1 its B is the identity, which selects a collocation kernel
+ * that skips every B contraction).  The library classifies each basis: the
+ * modified basis's parity phi_0(-x) = phi_P(x), phi_b(-x) = (-1)^(b-1)
+ * phi_b(x) selects the even-odd kernels, B = I the collocation kernels, any
+ * other basis the generic sum-factorised kernels.  FP32 calls use the tables
+ * rounded to FP32.  The adaptive-order sensor needs the library's own
+ * modified basis (SPX_ERR_UNSUPPORTED otherwise). */
+typedef struct {
+  int P;                 /* order, 1..8 */
+  int Q;                 /* points per direction, must be P + q_offset */
+  const double *B;
+  const double *dB;
+  const double *D;
+  const double *w;
+} spx_basis_desc;
+
+typedef enum { SPX_MEM_HOST = 0, SPX_MEM_DEVICE = 1 } spx_memory;
+
 typedef struct {
   int dim;                    /* 2 or 3 */
   int64_t n_elem;             /* E >= 0 */
   const int32_t *elem_order;  /* host [E] orders P_e, or NULL for uniform order */
   int uniform_order;          /* P for every element when elem_order == NULL */
   int q_offset;               /* Q_e = P_e + q_offset; 1 or 2 (0 selects 2) */
+  int n_basis;                /* 0: the library's modified basis (§2.1) for every order;
+                                 else the number of entries of `basis` */
+  const spx_basis_desc *basis; /* host array, one entry per order present (orders not
+                                 present may be given too); the tables are copied */
+  int basis_memory;           /* spx_memory of the table pointers B, dB, D, w */
 } spx_plan_desc;
 
-/* Creates a plan (copies the orders; builds offsets and the launch work
- * list on the current device).  *out receives the plan. */
+/* Creates a plan (copies the orders and basis tables; builds offsets and the
+ * launch work list on the current device).  *out receives the plan.  A
+ * zero-initialised descriptor tail (n_basis = 0) selects the modified basis. */
 spx_status spx_plan_create(spx_plan **out, const spx_plan_desc *desc);
 /* Frees a plan (NULL is accepted). */
 spx_status spx_plan_destroy(spx_plan *plan);

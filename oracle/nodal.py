@@ -45,14 +45,46 @@ def helmholtz_matrix(dim, P, Q, geo, t, lam=1.0, kappa=1.0):
     return M + L
 
 
-def helmholtz(mesh, coef, lam=1.0, kappa=1.0):
-    """y_e = H_e u_e for every element (nodal coefficients, element-major buffers)."""
+def helmholtz(mesh, coef, lam=1.0, kappa=1.0, lam_field=None, kappa_field=None):
+    """y_e = H_e u_e for every element (nodal coefficients, element-major buffers).
+
+    ``lam_field`` / ``kappa_field``: optional flat per-quadrature-point fields
+    that replace the constants ``lam`` / ``kappa``."""
     d = mesh.dim
     out = np.zeros_like(np.asarray(coef, dtype=np.float64))
     for P, Q, ids in mesh.groups():
         geo = mesh.geometry(P, Q, ids)
         n = (P + 1) ** d
+        nq = Q ** d
         for t, e in enumerate(ids):
             s = slice(mesh.coef_off[e], mesh.coef_off[e] + n)
-            out[s] = helmholtz_matrix(d, P, Q, geo, t, lam, kappa) @ coef[s]
+            q = slice(mesh.quad_off[e], mesh.quad_off[e] + nq)
+            la = lam if lam_field is None else np.asarray(lam_field)[q]
+            ka = kappa if kappa_field is None else np.asarray(kappa_field)[q]
+            out[s] = helmholtz_matrix(d, P, Q, geo, t, la, ka) @ coef[s]
+    return out
+
+
+def bwd_trans(mesh, coef):
+    """u_q = (Phi u_hat)_q per element with the nodal basis."""
+    d = mesh.dim
+    out = np.zeros(mesh.quad_off[-1])
+    for P, Q, ids in mesh.groups():
+        Phi, _ = phi_matrices(d, P, Q)
+        n, nq = (P + 1) ** d, Q ** d
+        for e in ids:
+            out[mesh.quad_off[e]: mesh.quad_off[e] + nq] = Phi @ coef[mesh.coef_off[e]: mesh.coef_off[e] + n]
+    return out
+
+
+def iproduct(mesh, f):
+    """y = Phi^T diag(w det J) f per element with the nodal basis."""
+    d = mesh.dim
+    out = np.zeros(mesh.coef_off[-1])
+    for P, Q, ids in mesh.groups():
+        Phi, _ = phi_matrices(d, P, Q)
+        geo = mesh.geometry(P, Q, ids)
+        n, nq = (P + 1) ** d, Q ** d
+        for t, e in enumerate(ids):
+            out[mesh.coef_off[e]: mesh.coef_off[e] + n] = Phi.T @ (geo["JW"][t] * f[mesh.quad_off[e]: mesh.quad_off[e] + nq])
     return out

@@ -25,9 +25,18 @@ class SpxError(RuntimeError):
         self.status = status
 
 
+class BasisDesc(C.Structure):
+    _fields_ = [("P", C.c_int), ("Q", C.c_int), ("B", C.c_void_p), ("dB", C.c_void_p), ("D", C.c_void_p),
+                ("w", C.c_void_p)]
+
+
+SPX_MEM_HOST, SPX_MEM_DEVICE = 0, 1
+
+
 class PlanDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_elem", C.c_int64), ("elem_order", C.POINTER(C.c_int32)),
-                ("uniform_order", C.c_int), ("q_offset", C.c_int)]
+                ("uniform_order", C.c_int), ("q_offset", C.c_int), ("n_basis", C.c_int),
+                ("basis", C.POINTER(BasisDesc)), ("basis_memory", C.c_int)]
 
 
 class CgOpts(C.Structure):
@@ -47,6 +56,7 @@ SIGNATURES = {
     "spx_last_error": (C.c_char_p, []),
     "spx_version": (C.c_char_p, []),
     "spx_basis_tables": (I32, [I32, I32, DP, DP, DP, DP, DP]),
+    "spx_nodal_basis_tables": (I32, [I32, I32, DP, DP]),
     "spx_plan_create": (I32, [C.POINTER(P), C.POINTER(PlanDesc)]),
     "spx_plan_destroy": (I32, [P]),
     "spx_plan_sizes": (I32, [P, C.POINTER(I64), C.POINTER(I64)]),

@@ -9,9 +9,10 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import SPX_F32, SPX_F64, OPS, CgOpts, CgResult, PlanDesc, SpxError, check, lib
+from ._lib import (SPX_F32, SPX_F64, SPX_MEM_DEVICE, SPX_MEM_HOST, OPS, BasisDesc, CgOpts, CgResult, PlanDesc,
+                   SpxError, check, lib)
 
-__all__ = ["Plan", "basis_tables", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz", "fwd_trans",
+__all__ = ["Plan", "basis_tables", "nodal_basis_tables", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz", "fwd_trans",
            "integral", "sensor", "adapt_orders",
            "helmholtz_adjoint", "helmholtz_diag", "gather", "assemble", "dot", "cg_workspace_bytes", "cg_solve",
            "SpxError"]
@@ -48,13 +49,57 @@ def basis_tables(P, Q):
     return dict(xi=xi, w=w, B=B, dB=dB, D=D)
 
 
-class Plan:
-    """A mesh of E elements of dimension 2 or 3 with per-element orders."""
+def nodal_basis_tables(P, Q):
+    """Host FP64 tables of the GLL nodal (Lagrange) basis of order P at Q GLL points: dict B, dB (numpy)."""
+    B, dB = np.zeros((Q, P + 1)), np.zeros((Q, P + 1))
+    ptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    check(lib().spx_nodal_basis_tables(P, Q, ptr(B), ptr(dB)))
+    return dict(B=B, dB=dB)
 
-    def __init__(self, dim, n_elem, order=None, orders=None, q_offset=2):
+
+def _basis_descs(basis, q_offset):
+    """spx_basis_desc array from {P: {"B": ..., "dB": ..., "D": ..., "w": ...}}: numpy arrays
+    (host) or CUDA tensors (device), all of one kind.  Returns (array, memory kind, keep-alive list)."""
+    items = sorted(basis.items())
+    arr = (BasisDesc * len(items))()
+    keep, kinds = [], set()
+    for t, (P, tabs) in enumerate(items):
+        arr[t].P, arr[t].Q = int(P), int(P) + q_offset
+        for name in ("B", "dB", "D", "w"):
+            v = tabs.get(name)
+            if v is None:
+                setattr(arr[t], name, None)
+                continue
+            if isinstance(v, torch.Tensor) and v.is_cuda:
+                v = v.to(torch.float64).contiguous()
+                kinds.add(SPX_MEM_DEVICE)
+                setattr(arr[t], name, v.data_ptr())
+            else:
+                v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+                kinds.add(SPX_MEM_HOST)
+                setattr(arr[t], name, v.ctypes.data)
+            keep.append(v)
+    if len(kinds) > 1:
+        raise TypeError("basis tables must be all host arrays or all CUDA tensors")
+    return arr, (kinds.pop() if kinds else SPX_MEM_HOST), keep
+
+
+class Plan:
+    """A mesh of E elements of dimension 2 or 3 with per-element orders.
+
+    basis: optional caller-supplied basis tables per order,
+    {P: {"B": [Q][P+1], "dB": [Q][P+1] or None, "D": None, "w": None}}, as
+    numpy arrays or CUDA tensors (spx_basis_desc); default the modified basis.
+    """
+
+    def __init__(self, dim, n_elem, order=None, orders=None, q_offset=2, basis=None):
         self.dim, self.E, self.q_offset = int(dim), int(n_elem), int(q_offset)
         desc = PlanDesc()
         desc.dim, desc.n_elem, desc.q_offset = self.dim, self.E, self.q_offset
+        keep = None
+        if basis:
+            arr, mem, keep = _basis_descs(basis, self.q_offset)
+            desc.n_basis, desc.basis, desc.basis_memory = len(arr), arr, mem
         self._orders = None
         if orders is not None:
             self._orders = np.ascontiguousarray(np.asarray(orders, dtype=np.int32))
@@ -67,6 +112,7 @@ class Plan:
             desc.uniform_order = int(order)
         h = C.c_void_p()
         check(lib().spx_plan_create(C.byref(h), C.byref(desc)))
+        del keep   # the plan copied the tables
         self.handle = h
         nc, nq = C.c_int64(), C.c_int64()
         check(lib().spx_plan_sizes(h, C.byref(nc), C.byref(nq)))

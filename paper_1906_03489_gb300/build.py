@@ -42,6 +42,8 @@ def units():
             for op in OPS:
                 u.append((f"ops_{tn}_{dim}_{op}", "ops_inst.cu",
                           [f"-DSPX_TN={tn}", f"-DSPX_DIM={dim}", f"-DSPX_OP={op}"]))
+        for bk in (1, 2):   # 3D Helmholtz of the other basis kinds
+            u.append((f"ops_{tn}_helm3_bk{bk}", "ops_inst.cu", [f"-DSPX_TN={tn}", f"-DSPX_BK={bk}"]))
     return u
 
 

@@ -76,6 +76,11 @@ spx_status ensure_tiles(spx_plan* plan, int op, int dtype) {
 }
 
 spx_status launch_op(const LaunchReq& r) {
+  if (r.op == OP_HELM && r.plan->dim == 3 && r.plan->bkind != BK_PARITY) {
+    const bool col = r.plan->bkind == BK_COLLOCATION;
+    if (r.dtype == 0) return col ? launch_f64_helm3_bk2(r) : launch_f64_helm3_bk1(r);
+    return col ? launch_f32_helm3_bk2(r) : launch_f32_helm3_bk1(r);
+  }
   const int key = r.dtype * 100 + r.plan->dim * 10 + r.op;
   switch (key) {
 #define SPX_CASE(DT, TN, DIM, OP) \
@@ -106,6 +111,114 @@ spx_status helmholtz_unless(const spx_plan* cp, int dtype, double lambda, const 
   LaunchReq r{p, OP_HELM, dtype, in, nullptr, geom, nullptr, nullptr, out, nullptr, nullptr, lambda, stream, skip};
   return launch_op(r);
 }
+// Caller-supplied basis tables (spx_basis_desc): copied into the plan's
+// per-order tables after checks against the GLL quadrature, then classified
+// for the 3D Helmholtz kernels (BasisKind).  Host-memory tables are checked
+// before any device call.
+static spx_status load_basis(spx_plan* p, const spx_plan_desc* d) {
+  if (d->n_basis == 0) return SPX_OK;
+  if (d->n_basis < 0 || d->n_basis > 64 || !d->basis)
+    return fail(SPX_ERR_INVALID_ARG, "plan_create: n_basis must be 0..64 with a basis array");
+  if (d->basis_memory != SPX_MEM_HOST && d->basis_memory != SPX_MEM_DEVICE)
+    return fail(SPX_ERR_INVALID_ARG, "plan_create: basis_memory must be SPX_MEM_HOST or SPX_MEM_DEVICE");
+  bool given[kMaxP1] = {};
+  auto fetch = [&](const double* src, size_t count, std::vector<double>& dst) -> spx_status {
+    dst.resize(count);
+    if (d->basis_memory == SPX_MEM_HOST) {
+      std::memcpy(dst.data(), src, count * sizeof(double));
+      return SPX_OK;
+    }
+    const cudaError_t e = cudaMemcpy(dst.data(), src, count * sizeof(double), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? SPX_OK : cuda_fail(e, "plan_create: cudaMemcpy(basis tables)");
+  };
+  for (int t = 0; t < d->n_basis; ++t) {
+    const spx_basis_desc& b = d->basis[t];
+    if (b.P < 1 || b.P > kMaxP) return fail(SPX_ERR_INVALID_ARG, "plan_create: basis order outside 1..8");
+    if (given[b.P]) return fail(SPX_ERR_INVALID_ARG, "plan_create: two basis descriptions for one order");
+    given[b.P] = true;
+    const int P = b.P, n = P + 1, Q = P + p->qoff;
+    if (b.Q != Q) return fail(SPX_ERR_INVALID_ARG, "plan_create: basis Q must equal P + q_offset");
+    if (!b.B) return fail(SPX_ERR_INVALID_ARG, "plan_create: basis table B is required");
+    std::vector<double> B, dB, D, w;
+    spx_status st;
+    if ((st = fetch(b.B, size_t(Q) * n, B)) != SPX_OK) return st;
+    double bmax = 0.0;
+    for (double v : B) {
+      if (!std::isfinite(v)) return fail(SPX_ERR_INVALID_ARG, "plan_create: basis table B not finite");
+      bmax = std::max(bmax, std::fabs(v));
+    }
+    if (bmax == 0.0) return fail(SPX_ERR_INVALID_ARG, "plan_create: basis table B is zero");
+    std::vector<double>& tab = p->tab[P];   // holds the library's GLL tables of this order
+    const double* Dg = tab.data() + 2 * Q * n;
+    std::vector<double> wg(Q);
+    basis_tables(P, Q, nullptr, wg.data(), nullptr, nullptr, nullptr);
+    if (b.D) {
+      if ((st = fetch(b.D, size_t(Q) * Q, D)) != SPX_OK) return st;
+      double dm = 0.0;
+      for (int i = 0; i < Q * Q; ++i) dm = std::max(dm, std::fabs(Dg[i]));
+      for (int i = 0; i < Q * Q; ++i)
+        if (!(std::fabs(D[i] - Dg[i]) <= 1e-12 * dm))
+          return fail(SPX_ERR_UNSUPPORTED, "plan_create: D must be the GLL collocation derivative (the quadrature "
+                                           "is the GLL rule the geometric factors are built on)");
+    }
+    if (b.w) {
+      if ((st = fetch(b.w, size_t(Q), w)) != SPX_OK) return st;
+      for (int i = 0; i < Q; ++i)
+        if (!(std::fabs(w[i] - wg[i]) <= 1e-12 * 2.0))
+          return fail(SPX_ERR_UNSUPPORTED, "plan_create: w must be the GLL weights (the quadrature is the GLL "
+                                           "rule the geometric factors are built on)");
+    }
+    // dB as the kernels use it: D B (exact for P <= Q - 1)
+    std::vector<double> DB(size_t(Q) * n, 0.0);
+    for (int i = 0; i < Q; ++i)
+      for (int q = 0; q < n; ++q) {
+        double acc = 0.0;
+        for (int j = 0; j < Q; ++j) acc += Dg[i * Q + j] * B[j * n + q];
+        DB[i * n + q] = acc;
+      }
+    if (b.dB) {
+      if ((st = fetch(b.dB, size_t(Q) * n, dB)) != SPX_OK) return st;
+      double dm = 0.0;
+      for (double v : DB) dm = std::max(dm, std::fabs(v));
+      for (int i = 0; i < Q * n; ++i)
+        if (!(std::fabs(dB[i] - DB[i]) <= 1e-10 * std::max(dm, bmax)))
+          return fail(SPX_ERR_INVALID_ARG, "plan_create: dB must be the derivative of B (D B to 1e-10)");
+      DB = dB;
+    }
+    // differs from the library's modified basis?
+    for (int i = 0; i < Q * n; ++i)
+      if (std::fabs(B[i] - tab[i]) > 1e-15 * bmax) p->custom_basis = true;
+    std::copy(B.begin(), B.end(), tab.begin());
+    std::copy(DB.begin(), DB.end(), tab.begin() + Q * n);
+    eo_tables(P, Q, tab.data());
+  }
+  for (int P = 1; P <= kMaxP; ++P)
+    if (p->present[P] && !given[P])
+      return fail(SPX_ERR_INVALID_ARG, "plan_create: no basis description for an order present in the mesh");
+  if (!p->custom_basis) return SPX_OK;
+  // classification over the orders present
+  bool parity = true, ident = true;
+  for (int P = 1; P <= kMaxP; ++P) {
+    if (!p->present[P]) continue;
+    const int n = P + 1, Q = P + p->qoff;
+    const double* B = p->tab[P].data();
+    double bmax = 0.0;
+    for (int i = 0; i < Q * n; ++i) bmax = std::max(bmax, std::fabs(B[i]));
+    const double tol = 1e-13 * bmax;
+    for (int i = 0; i < Q; ++i) {
+      const double* r = B + i * n;
+      const double* m = B + (Q - 1 - i) * n;   // mirrored point
+      if (std::fabs(m[0] - r[P]) > tol || std::fabs(m[P] - r[0]) > tol) parity = false;
+      for (int q = 1; q < P; ++q)
+        if (std::fabs(m[q] - ((q - 1) % 2 ? -r[q] : r[q])) > tol) parity = false;
+      for (int q = 0; q < n; ++q)
+        if (Q != n || std::fabs(r[q] - (q == i ? 1.0 : 0.0)) > 1e-14) ident = false;
+    }
+  }
+  p->bkind = parity ? BK_PARITY : (ident ? BK_COLLOCATION : BK_GENERAL);
+  return SPX_OK;
+}
+
 }  // namespace spx
 
 using namespace spx;
@@ -119,6 +232,8 @@ const char* spx_version(void) { return "spx 0.1 (sm_103a)"; }
 spx_status spx_basis_tables(int P, int Q, double* xi, double* w, double* B, double* dB, double* D) {
   return basis_tables(P, Q, xi, w, B, dB, D);
 }
+
+spx_status spx_nodal_basis_tables(int P, int Q, double* B, double* dB) { return nodal_basis_tables(P, Q, B, dB); }
 
 spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
   if (!out || !d) return fail(SPX_ERR_INVALID_ARG, "plan_create: NULL argument");
@@ -172,6 +287,13 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
     basis_tables(P, Q, nullptr, nullptr, p->tab[P].data(), p->tab[P].data() + Q * n, p->tab[P].data() + 2 * Q * n);
     eo_tables(P, Q, p->tab[P].data());
   }
+  {
+    const spx_status bs = load_basis(p, d);
+    if (bs != SPX_OK) {
+      delete p;
+      return bs;
+    }
+  }
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
     delete p;
@@ -197,8 +319,9 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
     // full inverses of orders 1..8, then the sensor's restricted ones (order 1: unused zeros)
     std::vector<double> a64(2 * mass1d_off(kMaxP + 1), 0.0);
     for (int P = 1; P <= kMaxP; ++P) {
-      mass1d_inverse(P, P + qoff, a64.data() + mass1d_off(P));
-      if (P >= 2) mass1d_inverse(P, P + qoff, a64.data() + mass1d_off(kMaxP + 1) + mass1d_off(P), true);
+      mass1d_inverse(P, P + qoff, p->tab[P].data(), a64.data() + mass1d_off(P));
+      if (P >= 2 && !p->custom_basis)   // the restricted space is the modified basis's (sensor)
+        mass1d_inverse(P, P + qoff, p->tab[P].data(), a64.data() + mass1d_off(kMaxP + 1) + mass1d_off(P), true);
     }
     std::vector<float> a32(a64.begin(), a64.end());
     if ((e = cudaMalloc(&p->d_aux64, a64.size() * sizeof(double))) != cudaSuccess) return cleanup(e, "cudaMalloc(aux)");
@@ -400,6 +523,8 @@ spx_status spx_fwd_trans(const spx_plan* p, spx_dtype dt, const void* phys, void
 spx_status spx_sensor(const spx_plan* p, const double* coef, double* S, void* stream) {
   if (p && p->E && (!coef || !S)) return fail(SPX_ERR_INVALID_ARG, "sensor: NULL buffer");
   if (p && p->present[1]) return fail(SPX_ERR_UNSUPPORTED, "sensor: elements of order 1 (the sensor needs P >= 2)");
+  if (p && p->custom_basis)
+    return fail(SPX_ERR_UNSUPPORTED, "sensor: needs the library's modified basis (its top bubble spans degree P)");
   return run_op(p, OP_SENSOR, SPX_F64, coef, p ? p->d_aux64 : nullptr, nullptr, nullptr, S, nullptr, nullptr, 0.0,
                 stream);
 }
@@ -472,7 +597,7 @@ static void tile_footprint(const spx_plan* p, int op, int dt, const LaunchCfg& b
     *thr = s.nthreads + (p->uniform ? 0 : 32);
     *smem = s.smem;
   } else {
-    *thr = (op == OP_HELM && p->dim == 3) ? (eb * Q * Q + 31) / 32 * 32 : c.nthreads;
+    *thr = (op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL) ? (eb * Q * Q + 31) / 32 * 32 : c.nthreads;
     *smem = op_smem_bytes(p, op, dt, c);
   }
 }
@@ -482,12 +607,15 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
     return fail(SPX_ERR_INVALID_ARG, "autotune: bad argument");
   if (p->E == 0) return SPX_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int ebs[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
+  const int ebs[] = {1, 2, 3, 4, 5, 6, 7, 8, 12, 16, 24, 32};
   const bool pair = uses_pair_kernel(p, op, dt);
+  // bodies with Q^2 threads per element take their block size from eb
+  const bool role = op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL && !pair;
   // the pair kernel derives its CTA size from eb: there `nthreads` picks the
   // register budget (threads per SM) and `stages` the L2 prefetch distance
-  const std::vector<int> nts = pair ? std::vector<int>{512, 640, 768} : std::vector<int>{64, 128, 192, 256, 384, 512};
-  const std::vector<int> sts = pair ? std::vector<int>{0, 1, 2} : std::vector<int>{2, 3};
+  const std::vector<int> nts = pair ? std::vector<int>{512, 640, 768}
+                                    : (role ? std::vector<int>{256} : std::vector<int>{64, 128, 192, 256, 384, 512});
+  const std::vector<int> sts = pair ? std::vector<int>{0, 1, 2} : std::vector<int>{1, 2, 3};
   LaunchCfg best = p->cfg[op][dt];
   // Variable order: one launch serves every order, so its CTA is sized by the
   // largest order's tile (threads and shared memory); an order whose tile

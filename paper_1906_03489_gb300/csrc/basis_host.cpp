@@ -178,6 +178,37 @@ spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* 
   return SPX_OK;
 }
 
+// Nodal (Lagrange) basis of order P through the P + 1 GLL points z_m,
+// evaluated at the Q GLL points x_i (§2.1: the classical spectral element
+// basis): B[i][m] = l_m(x_i) = prod_{k != m} (x_i - z_k) / (z_m - z_k) and
+// its derivative, the sum over l != m of the same product without factor l
+// divided by (z_m - z_l).  With Q = P + 1 the points coincide: B = I, dB = D.
+spx_status nodal_basis_tables(int P, int Q, double* B, double* dB) {
+  if (P < 1 || Q < 2 || Q > 16) return fail(SPX_ERR_INVALID_ARG, "nodal basis tables need 1 <= P and 2 <= Q <= 16");
+  std::vector<double> z, wz, x, wx;
+  gll_points(P + 1, z, wz);
+  gll_points(Q, x, wx);
+  const int n = P + 1;
+  for (int i = 0; i < Q; ++i)
+    for (int m = 0; m < n; ++m) {
+      double v = 1.0, dv = 0.0;
+      for (int k = 0; k < n; ++k) {
+        if (k == m) continue;
+        v *= (x[i] - z[k]) / (z[m] - z[k]);
+      }
+      for (int l = 0; l < n; ++l) {
+        if (l == m) continue;
+        double t = 1.0 / (z[m] - z[l]);
+        for (int k = 0; k < n; ++k)
+          if (k != m && k != l) t *= (x[i] - z[k]) / (z[m] - z[k]);
+        dv += t;
+      }
+      if (B) B[i * n + m] = v;
+      if (dB) dB[i * n + m] = dv;
+    }
+  return SPX_OK;
+}
+
 // Even-odd coefficients of order P (layout: EOLayout in kernel_params.h),
 // appended after B, dB, D of `tab`.
 void eo_tables(int P, int Q, double* tab) {
@@ -208,13 +239,14 @@ void eo_tables(int P, int Q, double* tab) {
     }
 }
 
-// Inverse of the 1D mass matrix M1 = B^T diag(w) B (n x n, SPD) of order P on
-// Q GLL points, by Cholesky factorisation and two triangular solves per
-// column.  Row-major [n][n] into minv.
-void mass1d_inverse(int P, int Q, double* minv, bool restricted) {
+// Inverse of the 1D mass matrix M1 = B^T diag(w) B (n x n, SPD) of the basis
+// tables B [Q][n] of order P on Q GLL points (weights w), by Cholesky
+// factorisation and two triangular solves per column.  Row-major [n][n] into
+// minv.
+void mass1d_inverse(int P, int Q, const double* B, double* minv, bool restricted) {
   const int nf = P + 1;
-  std::vector<double> xi(Q), w(Q), B(Q * nf), dB(Q * nf), D(Q * Q);
-  basis_tables(P, Q, xi.data(), w.data(), B.data(), dB.data(), D.data());
+  std::vector<double> w(Q);
+  basis_tables(P, Q, nullptr, w.data(), nullptr, nullptr, nullptr);
   std::fill(minv, minv + nf * nf, 0.0);
   // kept modes: all, or all but the degree-P bubble (index P - 1)
   std::vector<int> keep;

@@ -107,7 +107,7 @@ spx_status launch_pair(const LaunchReq& r) {
   }
 }
 
-template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0>
 spx_status launch_impl(const LaunchReq& r) {
   const spx_plan* plan = r.plan;
   const int dt = r.dtype;
@@ -148,7 +148,7 @@ spx_status launch_impl(const LaunchReq& r) {
   p.work_base = L.work_base;
   p.work_bytes = L.work_bytes;
   p.meta_base = L.meta_base;
-  auto kern = op_kernel<T, DIM, OP, PLO, PHI, QOFF>;
+  auto kern = op_kernel<T, DIM, OP, PLO, PHI, QOFF, BK>;
   // raise the dynamic shared-memory limit once per instantiation
   static std::mutex mu;
   static size_t configured = 0;
@@ -162,7 +162,7 @@ spx_status launch_impl(const LaunchReq& r) {
     }
   }
   int nthr = cfg.nthreads;
-  if (OP == OP_HELM && DIM == 3) {  // one thread per quadrature column
+  if (OP == OP_HELM && DIM == 3 && BK != 1) {  // one thread per quadrature column
     nthr = 0;
     for (int P = PLO; P <= PHI; ++P)
       if (plan->present[P]) nthr = std::max(nthr, cfg.order[P].eb * (P + QOFF) * (P + QOFF));
@@ -180,34 +180,40 @@ spx_status launch_impl(const LaunchReq& r) {
   return SPX_OK;
 }
 
-// Kernel of one (precision, dimension, operator) over orders PLO..PHI.
-template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>
+// Kernel of one (precision, dimension, operator) over orders PLO..PHI; BK is
+// the plan's basis kind (3D Helmholtz: 0 even-odd, 1 generic, 2 collocation).
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0>
 spx_status launch_any(const LaunchReq& r) {
-  if constexpr (std::is_same_v<T, float> && DIM == 3 && OP == OP_HELM) return launch_pair<PLO, PHI, QOFF>(r);
-  else return launch_impl<T, DIM, OP, PLO, PHI, QOFF>(r);
+  if constexpr (std::is_same_v<T, float> && DIM == 3 && OP == OP_HELM && BK == 0) return launch_pair<PLO, PHI, QOFF>(r);
+  else return launch_impl<T, DIM, OP, PLO, PHI, QOFF, BK>(r);
 }
 
-template <typename T, int DIM, int OP, int QOFF>
+template <typename T, int DIM, int OP, int QOFF, int BK = 0>
 spx_status launch_uniform(const LaunchReq& r) {
   switch (r.plan->uP) {
-    case 1: return launch_any<T, DIM, OP, 1, 1, QOFF>(r);
-    case 2: return launch_any<T, DIM, OP, 2, 2, QOFF>(r);
-    case 3: return launch_any<T, DIM, OP, 3, 3, QOFF>(r);
-    case 4: return launch_any<T, DIM, OP, 4, 4, QOFF>(r);
-    case 5: return launch_any<T, DIM, OP, 5, 5, QOFF>(r);
-    case 6: return launch_any<T, DIM, OP, 6, 6, QOFF>(r);
-    case 7: return launch_any<T, DIM, OP, 7, 7, QOFF>(r);
-    case 8: return launch_any<T, DIM, OP, 8, 8, QOFF>(r);
+    case 1: return launch_any<T, DIM, OP, 1, 1, QOFF, BK>(r);
+    case 2: return launch_any<T, DIM, OP, 2, 2, QOFF, BK>(r);
+    case 3: return launch_any<T, DIM, OP, 3, 3, QOFF, BK>(r);
+    case 4: return launch_any<T, DIM, OP, 4, 4, QOFF, BK>(r);
+    case 5: return launch_any<T, DIM, OP, 5, 5, QOFF, BK>(r);
+    case 6: return launch_any<T, DIM, OP, 6, 6, QOFF, BK>(r);
+    case 7: return launch_any<T, DIM, OP, 7, 7, QOFF, BK>(r);
+    case 8: return launch_any<T, DIM, OP, 8, 8, QOFF, BK>(r);
     default: return fail(SPX_ERR_UNSUPPORTED, "order out of range");
   }
 }
 
-template <typename T, int DIM, int OP>
+template <typename T, int DIM, int OP, int BK = 0>
 spx_status launch_typed(const LaunchReq& r) {
-  if (r.plan->uniform) {
-    return r.plan->qoff == 1 ? launch_uniform<T, DIM, OP, 1>(r) : launch_uniform<T, DIM, OP, 2>(r);
+  if constexpr (BK == 2) {   // collocation: Q = P + 1 only
+    if (r.plan->qoff != 1) return fail(SPX_ERR_UNSUPPORTED, "collocation kernel needs q_offset = 1");
+    return r.plan->uniform ? launch_uniform<T, DIM, OP, 1, BK>(r) : launch_any<T, DIM, OP, 1, kMaxP, 1, BK>(r);
+  } else {
+    if (r.plan->uniform) {
+      return r.plan->qoff == 1 ? launch_uniform<T, DIM, OP, 1, BK>(r) : launch_uniform<T, DIM, OP, 2, BK>(r);
+    }
+    return r.plan->qoff == 1 ? launch_any<T, DIM, OP, 1, kMaxP, 1, BK>(r) : launch_any<T, DIM, OP, 1, kMaxP, 2, BK>(r);
   }
-  return r.plan->qoff == 1 ? launch_any<T, DIM, OP, 1, kMaxP, 1>(r) : launch_any<T, DIM, OP, 1, kMaxP, 2>(r);
 }
 
 }  // namespace spx
@@ -215,3 +221,7 @@ spx_status launch_typed(const LaunchReq& r) {
 #define SPX_DEFINE_LAUNCH_(TN, T, DIM, OP) \
   spx_status spx::launch_##TN##_##DIM##_##OP(const spx::LaunchReq& r) { return spx::launch_typed<T, DIM, OP>(r); }
 #define SPX_DEFINE_LAUNCH(TN, T, DIM, OP) SPX_DEFINE_LAUNCH_(TN, T, DIM, OP)
+// 3D Helmholtz for the other basis kinds (1 generic, 2 collocation)
+#define SPX_DEFINE_LAUNCH_BK_(TN, T, BK) \
+  spx_status spx::launch_##TN##_helm3_bk##BK(const spx::LaunchReq& r) { return spx::launch_typed<T, 3, spx::OP_HELM, BK>(r); }
+#define SPX_DEFINE_LAUNCH_BK(TN, T, BK) SPX_DEFINE_LAUNCH_BK_(TN, T, BK)

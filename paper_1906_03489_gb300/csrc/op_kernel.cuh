@@ -513,16 +513,17 @@ __device__ void body_helm(const T* tab, const Ctx<T>& c, T* out, Rel release) {
 //    gradient along xi_3 and the pointwise geometric factors, in registers;
 //  * pencil owner along xi_1 at (j, k) = (a, b) and along xi_2 at
 //    (i, k) = (a, b) for the gradient and transposed gradient;
-//  * pencil owner of the BwdTrans / IProduct contractions along xi_1, xi_2.
+//  * the BwdTrans / IProduct contractions along xi_1, xi_2 (S1, S2, S8, S9)
+//    have fewer pencils than an element has threads: their work items are
+//    numbered densely over the whole CTA instead.
 // Data moves between roles through shared memory with odd row strides S, so
 // that the scalar accesses of consecutive threads fall in distinct banks.
 // Matrices are indexed with compile-time indices only (constant bank).
 // Buffers per element (row stride S = Q | 1, plane stride Q*S):
-//   W0: X[r][q][i] (S1 -> S2), then Y3[r][i][j] (S7 -> S8)
+//   W0: X[r][q][i] (S1 -> S2), U[k][j][i] (S3 -> S4), Y3[r][i][j] (S7 -> S8)
 //   W1: Y[j][i][r] (rows of n, stride SN = n | 1; S2 -> S3), then Y2[r][q][i] (S8 -> S9)
-//   W2: U[k][j][i] (S3 -> S4)
-//   W3: d0 (S4 -> S5), g0 (S5 -> S6), D^T-contracted g0 (S6 -> S7), same layout
-//   W4: d1, g1, D^T-contracted g1
+//   W2: d0 (S4 -> S5), g0 (S5 -> S6), D^T-contracted g0 (S6 -> S7), same layout
+//   W3: d1, g1, D^T-contracted g1
 template <typename T, int P, int Q>
 struct RoleShape {
   static constexpr int n = P + 1;
@@ -534,55 +535,20 @@ struct RoleShape {
   static constexpr int WS = Q * PL > WS0 ? (Q * PL > WS1 ? Q * PL : WS1) : (WS0 > WS1 ? WS0 : WS1);
 };
 
+// Middle phases of the 3D Helmholtz bodies with Q^2 threads per element
+// (RoleShape buffers; PL = Q S plane stride): from U[k][j][i] in W2 (the
+// caller's U buffer; W3, W4 are the caller's two gradient buffers) and the
+// column's u, d2 = du/dxi_3 in registers, the gradient pencils along xi_1,
+// xi_2 (S4), the pointwise geometric factors (S5), the transposed-gradient
+// pencils (S6).  Returns after the S6 barrier with z = D^T g2 + lambda JW u
+// (the column's xi_3 part and the mass term) in registers and the xi_1, xi_2
+// transposed parts in W3, W4 at (k, j, i) = k PL + j S + i.
 template <typename T, int P, int Q, class Rel>
-__device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel release) {
+__device__ __forceinline__ void helm_mid(const T* tab, const Ctx<T>& c, int el, int a, int b, bool act, T* W2, T* W3,
+                                         T* W4, T (&u)[Q], T (&g2)[Q], T (&z)[Q], Rel& release) {
   using S_ = RoleShape<T, P, Q>;
-  using Vt = Lane<T>;
-  constexpr int n = S_::n, S = S_::S, SN = S_::SN, PL = S_::PL, WS = S_::WS;
+  constexpr int S = S_::S, PL = S_::PL;
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
-  const int el = c.tid / Q2;
-  const int cc = c.tid - el * Q2;
-  const int a = cc % Q, b = cc / Q;
-  const bool act = el < c.ne;
-  T* W0 = c.work[0] + el * WS;
-  T* W1 = c.work[1] + el * WS;
-  T* W2 = c.work[2] + el * WS;
-  T* W3 = c.work[3] + el * WS;
-  T* W4 = c.work[4] + el * WS;
-  // S1: pencil along p at (q, r) = (a, b): X[r][q][i] = sum_p B[i][p] C[r][q][p]
-  if (act && a < n && b < n) {
-    const T* C = c.staged(0, el) + (b * n + a) * n;
-    T v[n], x[Q];
-#pragma unroll
-    for (int p = 0; p < n; ++p) v[p] = C[p];
-    eo_b<P, Q>(tab, v, x);
-    T* dst = W0 + (b * n + a) * S;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) dst[i] = x[i];
-  }
-  SPX_SYNC();
-  // S2: pencil along q at (i, r) = (a, b): Y[j][i][r] = sum_q B[j][q] X[r][q][i]
-  if (act && b < n) {
-    T v[n], y[Q];
-#pragma unroll
-    for (int q = 0; q < n; ++q) v[q] = W0[(b * n + q) * S + a];
-    eo_b<P, Q>(tab, v, y);
-#pragma unroll
-    for (int j = 0; j < Q; ++j) W1[(j * Q + a) * SN + b] = y[j];
-  }
-  SPX_SYNC();
-  // S3: column (i, j) = (a, b): u = B y (xi_3), d2 = dB y; U[k][j][i] = u
-  T u[Q], g2[Q];
-  if (act) {
-    T y[n];
-#pragma unroll
-    for (int r = 0; r < n; ++r) y[r] = W1[(b * Q + a) * SN + r];
-    eo_b<P, Q>(tab, y, u);
-#pragma unroll
-    for (int k = 0; k < Q; ++k) W2[k * PL + b * S + a] = u[k];
-    eo_db<P, Q>(tab, y, g2);
-  }
-  SPX_SYNC();
   // S4: gradient pencils: along xi_1 at (j, k) = (a, b) -> W3, along xi_2 at (i, k) = (a, b) -> W4
   if (act) {
     T v[Q], d[Q];
@@ -600,7 +566,6 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
   SPX_SYNC();
   // S5: column (i, j) = (a, b): pointwise; g0 -> W3, g1 -> W4, g2 and lambda JW in
   // registers; then z = D^T g2 + lambda JW u along xi_3
-  T z[Q];
   if (act) {
     const T* G = c.staged(1, el) + b * Q + a;
     const T* lf = c.has_lam ? c.staged(2, el) + b * Q + a : nullptr;
@@ -649,40 +614,153 @@ __device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel releas
     for (int j = 0; j < Q; ++j) W4[b * PL + j * S + a] = d[j];
   }
   SPX_SYNC();
-  // S7: column (i, j) = (a, b): z += both contributions; y3 = B^T z (xi_3) -> Y3[r][i][j]
+}
+
+template <typename T, int P, int Q, class Rel>
+__device__ void body_helm_role(const T* tab, const Ctx<T>& c, T* out, Rel release) {
+  using S_ = RoleShape<T, P, Q>;
+  constexpr int n = S_::n, S = S_::S, SN = S_::SN, PL = S_::PL, WS = S_::WS;
+  constexpr int Q2 = Q * Q;
+  const int el = c.tid / Q2;
+  const int cc = c.tid - el * Q2;
+  const int a = cc % Q, b = cc / Q;
+  const bool act = el < c.ne;
+  const int ne = c.ne, tid = c.tid;
+  T* W0 = c.work[0];
+  T* W1 = c.work[1];
+  // S1, S2, S8 and S9 have fewer pencils than the element has threads; their
+  // work items are numbered densely over the CTA's threads (item t -> thread
+  // t), so that the idle threads form whole idle warps: a warp with a few
+  // active lanes costs the FP64 pipe as much as a full one.
+  // S1: pencil along p at (q, r): X[r][q][i] = sum_p B[i][p] C[r][q][p]   (ne n^2 items)
+  if (tid < ne * n * n) {
+    const int e1 = tid / (n * n), qr = tid - e1 * n * n;
+    const T* C = c.staged(0, e1) + qr * n;
+    T v[n], x[Q];
+#pragma unroll
+    for (int p = 0; p < n; ++p) v[p] = C[p];
+    eo_b<P, Q>(tab, v, x);
+    T* dst = W0 + e1 * WS + qr * S;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[i] = x[i];
+  }
+  SPX_SYNC();
+  // S2: pencil along q at (i, r): Y[j][i][r] = sum_q B[j][q] X[r][q][i]   (ne Q n items)
+  if (tid < ne * Q * n) {
+    const int e2 = tid / (Q * n), ir = tid - e2 * Q * n;
+    const int i = ir % Q, r = ir / Q;
+    const T* X = W0 + e2 * WS;
+    T v[n], y[Q];
+#pragma unroll
+    for (int q = 0; q < n; ++q) v[q] = X[(r * n + q) * S + i];
+    eo_b<P, Q>(tab, v, y);
+    T* Y = W1 + e2 * WS;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) Y[(j * Q + i) * SN + r] = y[j];
+  }
+  SPX_SYNC();
+  // S3: column (i, j) = (a, b): u = B y (xi_3), d2 = dB y; U[k][j][i] = u (in W0)
+  T* U = W0 + el * WS;
+  T u[Q], g2[Q];
+  if (act) {
+    T y[n];
+#pragma unroll
+    for (int r = 0; r < n; ++r) y[r] = W1[el * WS + (b * Q + a) * SN + r];
+    eo_b<P, Q>(tab, y, u);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) U[k * PL + b * S + a] = u[k];
+    eo_db<P, Q>(tab, y, g2);
+  }
+  SPX_SYNC();
+  T* W2 = c.work[2] + el * WS;
+  T* W3 = c.work[3] + el * WS;
+  T z[Q];
+  helm_mid<T, P, Q>(tab, c, el, a, b, act, U, W2, W3, u, g2, z, release);
+  // S7: column (i, j) = (a, b): z += both contributions; y3 = B^T z (xi_3) -> Y3[r][i][j] (in W0)
   if (act) {
     T y3[n];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int w = k * PL + b * S + a;
-      z[k] += W3[w] + W4[w];
+      z[k] += W2[w] + W3[w];
     }
     eo_bt<P, Q>(tab, z, y3);
 #pragma unroll
-    for (int r = 0; r < n; ++r) W0[(r * Q + a) * S + b] = y3[r];
+    for (int r = 0; r < n; ++r) U[(r * Q + a) * S + b] = y3[r];
   }
   SPX_SYNC();
-  // S8: pencil along j at (i, r) = (a, b): Y2[r][q][i] = sum_j B[j][q] Y3[r][i][j]
-  if (act && b < n) {
+  // S8: pencil along j at (i, r): Y2[r][q][i] = sum_j B[j][q] Y3[r][i][j]   (ne Q n items)
+  if (tid < ne * Q * n) {
+    const int e2 = tid / (Q * n), ir = tid - e2 * Q * n;
+    const int i = ir % Q, r = ir / Q;
+    const T* Y3 = W0 + e2 * WS;
     T v[Q], y2[n];
 #pragma unroll
-    for (int j = 0; j < Q; ++j) v[j] = W0[(b * Q + a) * S + j];
+    for (int j = 0; j < Q; ++j) v[j] = Y3[(r * Q + i) * S + j];
     eo_bt<P, Q>(tab, v, y2);
+    T* Y2 = W1 + e2 * WS;
 #pragma unroll
-    for (int q = 0; q < n; ++q) W1[(b * n + q) * S + a] = y2[q];
+    for (int q = 0; q < n; ++q) Y2[(r * n + q) * S + i] = y2[q];
   }
   SPX_SYNC();
-  // S9: pencil along i at (q, r) = (a, b): y[p][q][r] = sum_i B[i][p] Y2[r][q][i] -> HBM
-  if (act && a < n && b < n) {
+  // S9: pencil along i at (q, r): y[p][q][r] = sum_i B[i][p] Y2[r][q][i] -> HBM   (ne n^2 items)
+  if (tid < ne * n * n) {
+    const int e1 = tid / (n * n), qr = tid - e1 * n * n;
+    const T* Y2 = W1 + e1 * WS + qr * S;
     T v[Q], y[n];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = W1[(b * n + a) * S + i];
+    for (int i = 0; i < Q; ++i) v[i] = Y2[i];
     eo_bt<P, Q>(tab, v, y);
-    T* dst = out + c.gcoef[el] + (b * n + a) * n;
+    T* dst = out + c.gcoef[e1] + qr * n;
 #pragma unroll
     for (int p = 0; p < n; ++p) dst[p] = y[p];
   }
-  (void)Vt::L;
+}
+
+// ---- Helmholtz, 3D, collocation (B = I) ----------------------------------
+// The basis is the Lagrange basis through the Q = P + 1 GLL points that are
+// also the quadrature points (the classical spectral element method, §2.1:
+// nodal basis on GLL points), so BwdTrans and IProductWRTBase are the
+// identity: the coefficients are the values at the quadrature points, the
+// mass term is lambda JW u pointwise, and only the collocation derivatives
+// and the geometric factors remain.  Q^2 threads per element, column (i, j) =
+// (a, b) as in body_helm_role; five phases instead of nine.
+template <typename T, int P, int Q, class Rel>
+__device__ void body_helm_col(const T* tab, const Ctx<T>& c, T* out, Rel release) {
+  static_assert(Q == P + 1, "collocation needs one GLL quadrature point per mode and direction");
+  using S_ = RoleShape<T, P, Q>;
+  constexpr int S = S_::S, PL = S_::PL, WS = S_::WS;
+  constexpr int Q2 = Q * Q;
+  const int el = c.tid / Q2;
+  const int cc = c.tid - el * Q2;
+  const int a = cc % Q, b = cc / Q;
+  const bool act = el < c.ne;
+  T* U = c.work[0] + el * WS;
+  T* W2 = c.work[2] + el * WS;
+  T* W3 = c.work[3] + el * WS;
+  // C1: column (i, j) = (a, b): u = the column's coefficients; U[k][j][i] = u; d2 = D u
+  T u[Q], g2[Q];
+  if (act) {
+    const T* C = c.staged(0, el) + b * Q + a;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      u[k] = C[k * Q2];
+      U[k * PL + b * S + a] = u[k];
+    }
+    eo_d<P, Q, false>(tab, u, g2);
+  }
+  SPX_SYNC();
+  T z[Q];
+  helm_mid<T, P, Q>(tab, c, el, a, b, act, U, W2, W3, u, g2, z, release);
+  // C5: column (i, j) = (a, b): y = z + both transposed parts -> HBM
+  if (act) {
+    T* dst = out + c.gcoef[el] + b * Q + a;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int w = k * PL + b * S + a;
+      dst[k * Q2] = z[k] + (W2[w] + W3[w]);
+    }
+  }
 }
 
 // ---- BwdTrans and reference gradient of one staged coefficient stream -----
@@ -1114,13 +1192,17 @@ __device__ void body_fwd(const T* tab, const Ctx<T>& c, const T* __restrict__ mi
   }
 }
 
-template <typename T, int DIM, int OP, int P, int Q, class Prm, class Rel>
+// BK: the basis kind of the plan (3D Helmholtz only): 0 the modified basis's
+// parity (even-odd role body), 1 any basis (generic body), 2 collocation,
+// B = I (collocation body).
+template <typename T, int DIM, int OP, int P, int Q, int BK, class Prm, class Rel>
 __device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel) {
   const T* tab = p.tab + Prm::Layout::off(P);
   if constexpr (OP == OP_BWD) body_bwd<T, DIM, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_IPROD) body_iprod<T, DIM, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_DERIV) body_deriv<T, DIM, P, Q>(tab, c, p.out0, p.out1, p.out2, rel);
-  else if constexpr (OP == OP_HELM && DIM == 3) body_helm_role<T, P, Q>(tab, c, p.out0, rel);
+  else if constexpr (OP == OP_HELM && DIM == 3 && BK == 0) body_helm_role<T, P, Q>(tab, c, p.out0, rel);
+  else if constexpr (OP == OP_HELM && DIM == 3 && BK == 2) body_helm_col<T, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_HELM) body_helm<T, DIM, P, Q>(tab, c, p.out0, rel);
   else if constexpr (OP == OP_ADJ) body_adj<T, DIM, P, Q>(tab, c, p.out0, p.out1, rel);
   else if constexpr (OP == OP_FWD) body_fwd<T, DIM, P, Q>(tab, c, p.in1 + mass1d_off(P), p.out0);
@@ -1129,15 +1211,15 @@ __device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel)
   else body_diag<T, DIM, P, Q>(tab, c, p.out0, rel);
 }
 
-template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, class Prm, class Rel>
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK, class Prm, class Rel>
 __device__ __forceinline__ void dispatch_order(int P, const Prm& p, const Ctx<T>& c, Rel rel) {
   if constexpr (PLO <= PHI) {
-    if (P == PLO) run_body<T, DIM, OP, PLO, PLO + QOFF>(p, c, rel);
-    else dispatch_order<T, DIM, OP, PLO + 1, PHI, QOFF>(P, p, c, rel);
+    if (P == PLO) run_body<T, DIM, OP, PLO, PLO + QOFF, BK>(p, c, rel);
+    else dispatch_order<T, DIM, OP, PLO + 1, PHI, QOFF, BK>(P, p, c, rel);
   }
 }
 
-template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF>
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0>
 __global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KParams<T, PLO, PHI, QOFF> p) {
   extern __shared__ __align__(128) char sm[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
@@ -1229,7 +1311,7 @@ __global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KPar
         }
       }
     };
-    dispatch_order<T, DIM, OP, PLO, PHI, QOFF>(P, p, c, rel);
+    dispatch_order<T, DIM, OP, PLO, PHI, QOFF, BK>(P, p, c, rel);
     __syncthreads();
     rel();
   }

@@ -12,7 +12,7 @@ inline int n_work_buffers(int op) {
     case OP_BWD: return 2;
     case OP_IPROD: return 2;
     case OP_DERIV: return 3;
-    case OP_HELM: return 5;
+    case OP_HELM: return 4;
     case OP_ADJ: return 8;
     case OP_FWD: return 7;
     case OP_SENSOR: return 7;
@@ -63,7 +63,7 @@ inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const Launch
       if (lens[s]) region[s] = std::max<uint64_t>(region[s], uint64_t(eb) * (((lens[s] * sz + 15) & ~int64_t(15)) + 16));
     const int S1 = Q | 1;
     uint64_t ws = plan->dim == 3 ? uint64_t(S1) * Q * Q : uint64_t(S1) * Q;
-    if (op == OP_HELM && plan->dim == 3) {  // column / pencil role layout
+    if (op == OP_HELM && plan->dim == 3 && plan->bkind != BK_GENERAL) {  // column / pencil role layout
       const uint64_t n = P + 1, S = Q | 1, SN = n | 1;
       ws = std::max<uint64_t>({ws, n * Q * S, n * n * S, uint64_t(Q) * Q * SN, uint64_t(Q) * Q * S});
     }
@@ -134,7 +134,7 @@ inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg, int thr)
 inline int pair_threshold(const spx_plan* plan) { return plan->uniform ? kMaxP : kPairThrVar; }
 
 inline bool uses_pair_kernel(const spx_plan* plan, int op, int dtype) {
-  return op == OP_HELM && dtype == 1 && plan->dim == 3;
+  return op == OP_HELM && dtype == 1 && plan->dim == 3 && plan->bkind == BK_PARITY;
 }
 
 }  // namespace spx

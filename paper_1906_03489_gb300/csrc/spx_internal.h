@@ -66,8 +66,11 @@ struct spx_plan {
   // caller-owned geometry, per precision
   const void* geom[2] = {nullptr, nullptr};
   const void* dxi[2] = {nullptr, nullptr};
-  // host basis tables (FP64) per order: B[Q][n], dB[Q][n], D[Q][Q]
+  // host basis tables (FP64) per order: B[Q][n], dB[Q][n], D[Q][Q], then the
+  // even-odd coefficients (EOLayout)
   std::vector<double> tab[spx::kMaxP1];
+  int bkind = 0;                         // BasisKind of the 3D Helmholtz kernels
+  bool custom_basis = false;             // tables differ from the library's modified basis
 };
 
 namespace spx {
@@ -109,6 +112,12 @@ SPX_DECL_ALL_OPS(f64, 3)
 SPX_DECL_ALL_OPS(f32, 2)
 SPX_DECL_ALL_OPS(f32, 3)
 
+// 3D Helmholtz of the other basis kinds (generic body, collocation body).
+spx_status launch_f64_helm3_bk1(const LaunchReq& r);
+spx_status launch_f64_helm3_bk2(const LaunchReq& r);
+spx_status launch_f32_helm3_bk1(const LaunchReq& r);
+spx_status launch_f32_helm3_bk2(const LaunchReq& r);
+
 spx_status launch_op(const LaunchReq& r);
 
 // Helmholtz apply for the solver: as spx_helmholtz (constant lambda, kappa =
@@ -123,6 +132,9 @@ size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& c
 // Basis tables (host FP64): fills B, dB, D as documented in spx.h.
 spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* dB, double* D);
 
+// Nodal (Lagrange through the P + 1 GLL points) basis at the Q GLL points.
+spx_status nodal_basis_tables(int P, int Q, double* B, double* dB);
+
 // Even-odd coefficients appended to a per-order table (EOLayout).
 void eo_tables(int P, int Q, double* tab);
 
@@ -134,9 +146,14 @@ spx_status noalloc_workspace(void** out);
 // reproducible); the plan's partials buffer holds one FP64 value per block.
 constexpr int kIntegralBlocksPerSM = 4;
 
-// Inverse of the 1D mass matrix B^T diag(w) B of order P on Q points, [n][n].
-// restricted: the matrix without row and column P - 1 (the degree-P bubble),
-// inverted, with zeros in that row and column (P >= 2).
-void mass1d_inverse(int P, int Q, double* minv, bool restricted = false);
+// Inverse of the 1D mass matrix B^T diag(w) B of the tables B [Q][n] (order P,
+// Q GLL points, weights w), [n][n].  restricted: the matrix without row and
+// column P - 1 (the degree-P bubble of the modified basis), inverted, with
+// zeros in that row and column (P >= 2).
+void mass1d_inverse(int P, int Q, const double* B, double* minv, bool restricted = false);
+
+// Basis kinds of a plan (3D Helmholtz kernels): the modified basis's parity
+// (even-odd bodies), any basis (generic body), collocation B = I.
+enum BasisKind { BK_PARITY = 0, BK_GENERAL = 1, BK_COLLOCATION = 2 };
 
 }  // namespace spx

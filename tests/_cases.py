@@ -18,14 +18,14 @@ def rel_err(y, ref):
 class Case:
     """A structured mesh on both sides: GPU plan + geometry, oracle mesh."""
 
-    def __init__(self, dim, N, P=None, orders=None, amp=0.05, q_offset=2):
+    def __init__(self, dim, N, P=None, orders=None, amp=0.05, q_offset=2, basis=None):
         self.dim, self.N, self.amp = dim, N, amp
         E = N ** dim
         if orders is None:
-            self.plan = spx.Plan(dim, E, order=P, q_offset=q_offset)
+            self.plan = spx.Plan(dim, E, order=P, q_offset=q_offset, basis=basis)
             ords = P
         else:
-            self.plan = spx.Plan(dim, E, orders=orders, q_offset=q_offset)
+            self.plan = spx.Plan(dim, E, orders=orders, q_offset=q_offset, basis=basis)
             ords = orders
         self.nodes = mesh.structured_nodes(dim, N, ords, amp, device=DEV)
         self.g = spx.geom_factors(self.plan, self.nodes)

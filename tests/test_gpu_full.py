@@ -118,7 +118,11 @@ def test_hex48_solve(hex48):
     x64, i64 = spx.cg_solve(plan, 1.0, l2g, ng, f, tol=1e-10, precision="f64")
     assert i32["status"] == 0 and i32["rel_residual"] <= 1e-10
     assert i64["status"] == 0 and i64["rel_residual"] <= 1e-10
-    assert rel_err(x32, x64.cpu().numpy()) <= 1e-8
+    # both meet the residual criterion (reading c12: ||f - A x|| <= 1e-10 ||f||), which fixes
+    # x only up to cond(A) x 2e-10 relative; the FP64 Jacobi-PCG's 364 iterations to 1e-10
+    # put cond(D^-1 A) near 1e3 (CG's sqrt(cond) ln(2/tol) / 2 bound), so the two solutions
+    # may differ by ~2e-7; the sampled oracle rows below check the residual itself
+    assert rel_err(x32, x64.cpu().numpy()) <= 2e-7
     # independent FP64 residual on the GPU
     r = f - spx.assemble(plan, l2g, spx.helmholtz(plan, spx.gather(plan, l2g, x32)), ng)
     assert (r.norm() / f.norm()).item() <= 1e-10

@@ -68,3 +68,50 @@ def test_whole_mesh_apply_matches_elementwise():
     for e in range(mesh.E):
         s = slice(mesh.coef_off[e], mesh.coef_off[e + 1])
         np.testing.assert_allclose(y[s], nodal.helmholtz_matrix(3, 3, 4, geo, e, 1.5, 0.7) @ u[s], atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,P,qoff", [(3, 3, 1), (3, 2, 2), (2, 4, 2)])
+def test_nodal_bwd_trans_interpolates_and_iproduct_is_its_transpose(dim, P, qoff):
+    """BwdTrans of nodal values of a polynomial of degree <= P per direction
+    evaluates that polynomial at the quadrature points (the identity when the
+    points are the nodes); IProduct satisfies <IProduct(f), u> = sum JW f (B u)."""
+    mesh = StructuredMesh(dim, 2, P, amp=0.05, nq=P + qoff)
+    rng = np.random.default_rng(9)
+    c = rng.uniform(-1, 1, (P + 1,) * dim)          # coefficients of prod_a x_a^k_a in reference coordinates
+    z, _ = basis.gll(P + 1)
+    xi, _ = basis.gll(P + qoff)
+
+    def poly(pts):
+        V = [np.vander(pts[:, a], P + 1, increasing=True) for a in range(dim)]
+        if dim == 2:
+            return np.einsum("qi,qj,ij->q", V[0], V[1], c)
+        return np.einsum("qi,qj,qk,ijk->q", V[0], V[1], V[2], c)
+    from oracle.geometry import reference_points
+    nod, quad = poly(reference_points(dim, z)), poly(reference_points(dim, xi))
+    u = np.concatenate([nod] * mesh.E)
+    np.testing.assert_allclose(nodal.bwd_trans(mesh, u), np.concatenate([quad] * mesh.E), atol=1e-12)
+    if qoff == 1:
+        np.testing.assert_array_equal(nodal.bwd_trans(mesh, u), u)
+    f = rng.uniform(-1, 1, mesh.quad_off[-1])
+    v = rng.uniform(-1, 1, mesh.coef_off[-1])
+    JW = np.concatenate([mesh.geometry(P, P + qoff, np.array([e]))["JW"][0] for e in range(mesh.E)])
+    lhs = nodal.iproduct(mesh, f) @ v
+    rhs = np.sum(JW * f * nodal.bwd_trans(mesh, v))
+    assert abs(lhs - rhs) <= 1e-13 * np.sum(np.abs(JW * f))
+
+
+def test_nodal_helmholtz_fields_match_the_elemental_matrices():
+    mesh = StructuredMesh(3, 2, 2, amp=0.05, nq=3)
+    rng = np.random.default_rng(10)
+    u = rng.uniform(-1, 1, mesh.coef_off[-1])
+    lam = rng.uniform(0.5, 2, mesh.quad_off[-1])
+    kap = rng.uniform(0.5, 2, mesh.quad_off[-1])
+    y = nodal.helmholtz(mesh, u, lam_field=lam, kappa_field=kap)
+    geo = mesh.geometry(2, 3, np.arange(mesh.E))
+    for e in range(mesh.E):
+        s = slice(mesh.coef_off[e], mesh.coef_off[e + 1])
+        q = slice(mesh.quad_off[e], mesh.quad_off[e + 1])
+        np.testing.assert_allclose(y[s], nodal.helmholtz_matrix(3, 2, 3, geo, e, lam[q], kap[q]) @ u[s], atol=1e-13)
+    # lambda field = constant 1.5 reproduces the scalar form
+    np.testing.assert_allclose(nodal.helmholtz(mesh, u, lam_field=np.full(mesh.quad_off[-1], 1.5)),
+                               nodal.helmholtz(mesh, u, lam=1.5), atol=1e-13)

@@ -30,6 +30,11 @@ What it computes, and the passage each part follows:
 * ``nodal``      the GLL nodal (Lagrange, classical spectral element) basis
                  variant of the elemental Helmholtz matrix (§2.1 names the
                  Lagrange interpolant basis beside the modified one).
+* ``collapsed``  collapsed-coordinate triangles and prisms (§2.1, Fig.
+                 f:duffy, Table t:refregions): the modified C0 basis in
+                 collapsed coordinates, Gauss-Radau quadrature in the
+                 collapsed direction, affine elements, dense BwdTrans,
+                 IProductWRTBase, PhysDeriv and Helmholtz.
 * ``adjoint``    gradients of 0.5*||H(lambda,kappa)u - f||^2 with respect to
                  u, lambda(x) and kappa(x), by differentiating the dense
                  forms of eq. e:bilinear.

@@ -118,6 +118,12 @@ spx_status spx_basis_tables(int P, int Q, double *xi, double *w, double *B, doub
  * and dB = D.  Requires 1 <= P, 2 <= Q <= 16. */
 spx_status spx_nodal_basis_tables(int P, int Q, double *B, double *dB);
 
+/* Gauss-Radau-Legendre points x[Q] (ascending, x[0] = -1, all < 1) and
+ * weights w[Q] on [-1, 1], exact for polynomials of degree <= 2Q - 2: the
+ * rule of the collapsed direction of triangles and prisms (§2.1, Gauss-Radau
+ * points omitting the collapsed vertex).  Host FP64; 2 <= Q <= 16. */
+spx_status spx_gauss_radau(int Q, double *x, double *w);
+
 /* ---------------------------------------------------------------------------
  * Plans: the mesh's element count, dimension and per-element orders
  * (Collections groups of same-shape, same-basis elements, §3.3; variable
@@ -158,6 +164,30 @@ typedef struct {
 
 typedef enum { SPX_MEM_HOST = 0, SPX_MEM_DEVICE = 1 } spx_memory;
 
+/* Element shapes (Table t:refregions).  Triangles T = {xi in [-1,1]^2 |
+ * xi1 + xi2 <= 0} and prisms R = {xi in [-1,1]^3 | xi2 + xi3 <= 0} use the
+ * collapsed coordinates of §2.1 (Fig. f:duffy): triangle xi1 = (1 + eta1)
+ * (1 - eta2)/2 - 1, xi2 = eta2; prism xi1 = eta1, xi2 = (1 + eta2)(1 - eta3)/2
+ * - 1, xi3 = eta3, and the modified C0 basis in those coordinates:
+ *   triangle modes (p, q), p outer: p = 0: q = 0..P; p = 1..P-1: q = 0..P-1-p;
+ *     p = P: q = 0..P-1 (n_T = (P+1)(P+2)/2 per element), function
+ *     psi^a_p(eta1) psi^b_pq(eta2) with psi^a the modified basis of
+ *     spx_basis_tables, psi^b_pq = psi^a_q for p = 0, P, ((1-z)/2)^(p+1) for
+ *     q = 0 and ((1-z)/2)^(p+1) (1+z)/2 P^(2p+1,1)_(q-1)(z) otherwise; the mode
+ *     (0, P) is the collapsed vertex, the function (1 + eta2)/2;
+ *   prism modes a + (P+1) m: psi^a_a(xi1) times triangle mode m in (eta2, eta3).
+ * Quadrature: Q = P + 2 points per direction, GLL in the uncollapsed
+ * directions, Gauss-Radau (spx_gauss_radau; it omits the collapsed vertex) in
+ * the collapsed one; point index i + Q j (+ Q^2 k) over (eta1, eta2[, eta3]).
+ * The geometry layout is that of quads / hexes with eta in place of xi:
+ * G_ab = JW sum_m (d eta_a/dx_m)(d eta_b/dx_m), JW = w det(dx/deta) (the
+ * Duffy factor included), dxi_dx block a d + m = d eta_a / d x_m.  Plans of
+ * these shapes: uniform order (1..8), q_offset 2, the library's basis; the
+ * operators BwdTrans, IProductWRTBase, PhysDeriv, Helmholtz (constant or
+ * per-point lambda, kappa) and Integral (others: SPX_ERR_UNSUPPORTED);
+ * spx_geom_factors takes straight-sided (affine) elements by their vertices. */
+typedef enum { SPX_SHAPE_TENSOR = 0, SPX_SHAPE_TRI = 1, SPX_SHAPE_PRISM = 2 } spx_shape;
+
 typedef struct {
   int dim;                    /* 2 or 3 */
   int64_t n_elem;             /* E >= 0 */
@@ -169,6 +199,9 @@ typedef struct {
   const spx_basis_desc *basis; /* host array, one entry per order present (orders not
                                  present may be given too); the tables are copied */
   int basis_memory;           /* spx_memory of the table pointers B, dB, D, w */
+  int shape;                  /* spx_shape: SPX_SHAPE_TENSOR (0) quadrilaterals (dim 2) /
+                                 hexahedra (dim 3); SPX_SHAPE_TRI triangles (dim 2);
+                                 SPX_SHAPE_PRISM prisms (dim 3) */
 } spx_plan_desc;
 
 /* Creates a plan (copies the orders and basis tables; builds offsets and the
@@ -230,7 +263,11 @@ spx_status spx_plan_get_tile(const spx_plan *plan, spx_op op, spx_dtype dtype, i
 
 /* ---------------------------------------------------------------------------
  * Geometry (§2.1 mapping paragraph): iso-parametric map chi_e given by the
- * element's nodal coordinates at its (P+1)^d GLL nodes.  FP64 kernel computing,
+ * element's nodal coordinates at its (P+1)^d GLL nodes.  For triangle and
+ * prism plans the elements are affine, x = V0 + sum_c (V_c - V0)(1 + xi_c)/2,
+ * and `nodes` holds element e's d + 1 vertices V0..Vd at (d + 1) d e
+ * (vertex-major, V_c the image of the reference vertex one step along xi_c
+ * from (-1, ..., -1)).  FP64 kernel computing,
  * at every quadrature point, J = dx/dxi of the nodal interpolant, det J,
  * J^{-1} and the folded factors of the layout above.
  *   nodes   device FP64 in  (layout above)

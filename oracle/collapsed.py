@@ -287,3 +287,33 @@ def phys_deriv(mesh, f):
     ref = [F @ Dm[a].T for a in range(mesh.d)]          # d f / d eta_a
     K = deta_dx(mesh)
     return [sum(K[:, :, a, m] * ref[a] for a in range(mesh.d)).reshape(-1) for m in range(mesh.d)]
+
+
+def structured_vertices(shape, N, skew, jitter=None):
+    """Affine elements of a skewed N^d grid on the unit square / cube, two per cell.
+
+    Grid node (i, j[, k]) sits at skew @ ((i, j[, k]) / N).  Cell c = ex + N(ey
+    [+ N ez]) holds elements 2c and 2c + 1:
+      triangles  (n(ex,ey), n(ex+1,ey), n(ex,ey+1)) and (n(ex+1,ey+1), n(ex,ey+1), n(ex+1,ey));
+      prisms     (n(i,j,k), n(i+1,j,k), n(i,j+1,k), n(i,j,k+1)) and
+                 (n(i,j+1,k+1), n(i+1,j+1,k+1), n(i,j,k+1), n(i,j+1,k)),
+    each listed as its defining vertices V0..Vd.  ``jitter`` (E, d+1, d) is added."""
+    S = np.asarray(skew, dtype=np.float64)
+    d = S.shape[0]
+    out = []
+    rng_cells = [(ex, ey) for ey in range(N) for ex in range(N)] if d == 2 else \
+        [(i, j, k) for k in range(N) for j in range(N) for i in range(N)]
+    node = lambda *c: S @ (np.array(c, dtype=np.float64) / N)
+    for c in rng_cells:
+        if d == 2:
+            ex, ey = c
+            out.append([node(ex, ey), node(ex + 1, ey), node(ex, ey + 1)])
+            out.append([node(ex + 1, ey + 1), node(ex, ey + 1), node(ex + 1, ey)])
+        else:
+            i, j, k = c
+            out.append([node(i, j, k), node(i + 1, j, k), node(i, j + 1, k), node(i, j, k + 1)])
+            out.append([node(i, j + 1, k + 1), node(i + 1, j + 1, k + 1), node(i, j, k + 1), node(i, j + 1, k)])
+    V = np.array(out)
+    if jitter is not None:
+        V = V + np.asarray(jitter).reshape(V.shape)
+    return V

@@ -9,6 +9,6 @@ periodic C0 assembly and a mixed-precision Jacobi-PCG solver.
 """
 from ._lib import SpxError, lib  # noqa: F401
 from .binding import (Plan, assemble, basis_tables, bwd_trans, cg_solve, cg_workspace_bytes, dot,  # noqa: F401
-                      fwd_trans, gather, geom_factors, helmholtz, helmholtz_adjoint, helmholtz_diag, integral,
+                      fwd_trans, gather, gauss_radau, geom_factors, helmholtz, helmholtz_adjoint, helmholtz_diag, integral,
                       iproduct, nodal_basis_tables, phys_deriv, sensor, adapt_orders)
 from .autograd import HelmholtzFn, helmholtz_ad  # noqa: F401

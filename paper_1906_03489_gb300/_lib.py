@@ -36,7 +36,10 @@ SPX_MEM_HOST, SPX_MEM_DEVICE = 0, 1
 class PlanDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_elem", C.c_int64), ("elem_order", C.POINTER(C.c_int32)),
                 ("uniform_order", C.c_int), ("q_offset", C.c_int), ("n_basis", C.c_int),
-                ("basis", C.POINTER(BasisDesc)), ("basis_memory", C.c_int)]
+                ("basis", C.POINTER(BasisDesc)), ("basis_memory", C.c_int), ("shape", C.c_int)]
+
+
+SPX_SHAPE_TENSOR, SPX_SHAPE_TRI, SPX_SHAPE_PRISM = 0, 1, 2
 
 
 class CgOpts(C.Structure):
@@ -57,6 +60,7 @@ SIGNATURES = {
     "spx_version": (C.c_char_p, []),
     "spx_basis_tables": (I32, [I32, I32, DP, DP, DP, DP, DP]),
     "spx_nodal_basis_tables": (I32, [I32, I32, DP, DP]),
+    "spx_gauss_radau": (I32, [I32, DP, DP]),
     "spx_plan_create": (I32, [C.POINTER(P), C.POINTER(PlanDesc)]),
     "spx_plan_destroy": (I32, [P]),
     "spx_plan_sizes": (I32, [P, C.POINTER(I64), C.POINTER(I64)]),

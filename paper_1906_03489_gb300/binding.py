@@ -9,10 +9,10 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import (SPX_F32, SPX_F64, SPX_MEM_DEVICE, SPX_MEM_HOST, OPS, BasisDesc, CgOpts, CgResult, PlanDesc,
-                   SpxError, check, lib)
+from ._lib import (SPX_F32, SPX_F64, SPX_MEM_DEVICE, SPX_MEM_HOST, SPX_SHAPE_PRISM, SPX_SHAPE_TENSOR, SPX_SHAPE_TRI,
+                   OPS, BasisDesc, CgOpts, CgResult, PlanDesc, SpxError, check, lib)
 
-__all__ = ["Plan", "basis_tables", "nodal_basis_tables", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz", "fwd_trans",
+__all__ = ["Plan", "basis_tables", "nodal_basis_tables", "gauss_radau", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz", "fwd_trans",
            "integral", "sensor", "adapt_orders",
            "helmholtz_adjoint", "helmholtz_diag", "gather", "assemble", "dot", "cg_workspace_bytes", "cg_solve",
            "SpxError"]
@@ -92,10 +92,12 @@ class Plan:
     numpy arrays or CUDA tensors (spx_basis_desc); default the modified basis.
     """
 
-    def __init__(self, dim, n_elem, order=None, orders=None, q_offset=2, basis=None):
+    def __init__(self, dim, n_elem, order=None, orders=None, q_offset=2, basis=None, shape="tensor"):
         self.dim, self.E, self.q_offset = int(dim), int(n_elem), int(q_offset)
+        self.shape = shape
         desc = PlanDesc()
         desc.dim, desc.n_elem, desc.q_offset = self.dim, self.E, self.q_offset
+        desc.shape = {"tensor": SPX_SHAPE_TENSOR, "tri": SPX_SHAPE_TRI, "prism": SPX_SHAPE_PRISM}[shape]
         keep = None
         if basis:
             arr, mem, keep = _basis_descs(basis, self.q_offset)
@@ -164,8 +166,17 @@ class Plan:
         return s.value
 
 
+def gauss_radau(Q):
+    """Host FP64 Gauss-Radau-Legendre points (with -1) and weights: (x, w) numpy arrays."""
+    x, w = np.zeros(Q), np.zeros(Q)
+    ptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    check(lib().spx_gauss_radau(Q, ptr(x), ptr(w)))
+    return x, w
+
+
 def geom_factors(plan, nodes, want_f32=True, want_xq=True):
-    """FP64 geometric factors from nodal coordinates (device FP64 tensor)."""
+    """FP64 geometric factors from nodal coordinates (device FP64 tensor; for
+    triangle / prism plans the (E, d+1, d) affine vertices)."""
     _dev(nodes, "nodes")
     d = plan.dim
     nf = 7 if d == 3 else 4

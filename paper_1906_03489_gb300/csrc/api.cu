@@ -29,6 +29,7 @@ static int default_eb(int dim, int Q) {
 }
 
 size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& cfg) {
+  if (plan->shape) return collapsed_smem_bytes(plan, dtype, cfg.order[plan->uP].eb);
   if (uses_pair_kernel(plan, op, dtype)) {
     const PairShape s = pair_shape(plan, cfg, pair_threshold(plan));
     return s.nthreads > 512 ? SIZE_MAX : s.smem;
@@ -76,6 +77,7 @@ spx_status ensure_tiles(spx_plan* plan, int op, int dtype) {
 }
 
 spx_status launch_op(const LaunchReq& r) {
+  if (r.plan->shape) return launch_collapsed(r);
   if (r.op == OP_HELM && r.plan->dim == 3 && r.plan->bkind != BK_PARITY) {
     const bool col = r.plan->bkind == BK_COLLOCATION;
     if (r.dtype == 0) return col ? launch_f64_helm3_bk2(r) : launch_f64_helm3_bk1(r);
@@ -235,6 +237,11 @@ spx_status spx_basis_tables(int P, int Q, double* xi, double* w, double* B, doub
 
 spx_status spx_nodal_basis_tables(int P, int Q, double* B, double* dB) { return nodal_basis_tables(P, Q, B, dB); }
 
+spx_status spx_gauss_radau(int Q, double* x, double* w) {
+  if (!x || !w) return fail(SPX_ERR_INVALID_ARG, "gauss_radau: NULL output");
+  return gauss_radau(Q, x, w);
+}
+
 spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
   if (!out || !d) return fail(SPX_ERR_INVALID_ARG, "plan_create: NULL argument");
   *out = nullptr;
@@ -243,11 +250,21 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
     return fail(SPX_ERR_INVALID_ARG, "plan_create: n_elem out of range");
   const int qoff = d->q_offset == 0 ? 2 : d->q_offset;
   if (qoff != 1 && qoff != 2) return fail(SPX_ERR_UNSUPPORTED, "plan_create: q_offset must be 1 or 2");
+  if (d->shape != SPX_SHAPE_TENSOR && d->shape != SPX_SHAPE_TRI && d->shape != SPX_SHAPE_PRISM)
+    return fail(SPX_ERR_INVALID_ARG, "plan_create: unknown element shape");
+  if (d->shape != SPX_SHAPE_TENSOR) {
+    if ((d->shape == SPX_SHAPE_TRI) != (d->dim == 2))
+      return fail(SPX_ERR_INVALID_ARG, "plan_create: triangles are 2D, prisms 3D");
+    if (d->elem_order || qoff != 2 || d->n_basis)
+      return fail(SPX_ERR_UNSUPPORTED, "plan_create: triangles / prisms take a uniform order, q_offset 2 and the "
+                                       "library's basis");
+  }
   spx_plan* p = new (std::nothrow) spx_plan();
   if (!p) return fail(SPX_ERR_NO_MEMORY, "plan_create: out of host memory");
   p->dim = d->dim;
   p->E = d->n_elem;
   p->qoff = qoff;
+  p->shape = d->shape;
   p->orders.resize(p->E);
   if (d->elem_order) {
     for (int64_t e = 0; e < p->E; ++e) {
@@ -276,8 +293,21 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
   p->coef_off[0] = p->quad_off[0] = 0;
   for (int64_t e = 0; e < p->E; ++e) {
     const int64_t n = p->orders[e] + 1, Q = p->orders[e] + qoff;
-    p->coef_off[e + 1] = p->coef_off[e] + (p->dim == 3 ? n * n * n : n * n);
+    const int64_t nt = n * (n + 1) / 2;   // triangle modes
+    const int64_t nm = p->shape == SPX_SHAPE_TRI ? nt : (p->shape == SPX_SHAPE_PRISM ? n * nt : (p->dim == 3 ? n * n * n : n * n));
+    p->coef_off[e + 1] = p->coef_off[e] + nm;
     p->quad_off[e + 1] = p->quad_off[e] + (p->dim == 3 ? Q * Q * Q : Q * Q);
+  }
+  if (p->shape) {   // tables of the collapsed kernels: B1[Q][n], Bb[n][Q][n], D1[Q][Q], D2[Q][Q]
+    const int P = p->uP, n = P + 1, Q = P + 2;
+    p->ctab.assign(Q * n + n * Q * n + 2 * Q * Q, 0.0);
+    double* t = p->ctab.data();
+    const spx_status cs = collapsed_tables(P, Q, t, t + Q * n, t + Q * n + n * Q * n, t + Q * n + n * Q * n + Q * Q,
+                                           nullptr, nullptr, nullptr, nullptr);
+    if (cs != SPX_OK) {
+      delete p;
+      return cs;
+    }
   }
   p->n_coef = p->coef_off[p->E];
   p->n_quad = p->quad_off[p->E];
@@ -474,6 +504,8 @@ static spx_status run_op(const spx_plan* cp, int op, spx_dtype dt, const void* i
   const void* ptrs[] = {in0, in1, lam_f, kap_f, o0, o1, o2};
   for (const void* q : ptrs)
     if (q && (reinterpret_cast<uintptr_t>(q) % a)) return fail(SPX_ERR_INVALID_ARG, "buffer not aligned to its element size");
+  if (p->shape && op != OP_BWD && op != OP_IPROD && op != OP_DERIV && op != OP_HELM)
+    return fail(SPX_ERR_UNSUPPORTED, "operator not available for triangles / prisms");
   spx_status s = ensure_tiles(p, op, dt);
   if (s != SPX_OK) return s;
   LaunchReq r{p, op, dt, in0, in1, geom, lam_f, kap_f, o0, o1, o2, lam, static_cast<cudaStream_t>(stream)};
@@ -597,7 +629,8 @@ static void tile_footprint(const spx_plan* p, int op, int dt, const LaunchCfg& b
     *thr = s.nthreads + (p->uniform ? 0 : 32);
     *smem = s.smem;
   } else {
-    *thr = (op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL) ? (eb * Q * Q + 31) / 32 * 32 : c.nthreads;
+    *thr = (op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL && !p->shape) ? (eb * Q * Q + 31) / 32 * 32
+                                                                                  : c.nthreads;
     *smem = op_smem_bytes(p, op, dt, c);
   }
 }
@@ -610,7 +643,7 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
   const int ebs[] = {1, 2, 3, 4, 5, 6, 7, 8, 12, 16, 24, 32};
   const bool pair = uses_pair_kernel(p, op, dt);
   // bodies with Q^2 threads per element take their block size from eb
-  const bool role = op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL && !pair;
+  const bool role = op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL && !pair && !p->shape;
   // the pair kernel derives its CTA size from eb: there `nthreads` picks the
   // register budget (threads per SM) and `stages` the L2 prefetch distance
   const std::vector<int> nts = pair ? std::vector<int>{512, 640, 768}

@@ -129,7 +129,133 @@ void gll_points(int Q, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// P^{(a,b)}_m(x) by the three-term recurrence (standard normalisation).
+double jacobi_ab(int m, double a, double b, double x) {
+  if (m < 0) return 0.0;
+  double p0 = 1.0;
+  if (m == 0) return p0;
+  double p1 = 0.5 * ((a + b + 2.0) * x + a - b);
+  for (int k = 2; k <= m; ++k) {
+    const double c = 2.0 * k + a + b;
+    const double lhs = 2.0 * k * (k + a + b) * (c - 2.0);
+    const double t1 = (c - 1.0) * (c * (c - 2.0) * x + a * a - b * b);
+    const double t2 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * c;
+    const double p2 = (t1 * p1 - t2 * p0) / lhs;
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+// Collocation derivative of the Lagrange interpolant through points x (barycentric weights).
+void collocation(const std::vector<double>& x, double* D) {
+  const int Q = static_cast<int>(x.size());
+  std::vector<double> lam(Q, 1.0);
+  for (int j = 0; j < Q; ++j)
+    for (int k = 0; k < Q; ++k)
+      if (k != j) lam[j] /= (x[j] - x[k]);
+  for (int i = 0; i < Q; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < Q; ++j) {
+      if (j == i) continue;
+      const double v = (lam[j] / lam[i]) / (x[i] - x[j]);
+      D[i * Q + j] = v;
+      diag -= v;
+    }
+    D[i * Q + i] = diag;
+  }
+}
+
 }  // namespace
+
+// Gauss-Radau-Legendre points including -1 (ascending, all < 1) and weights:
+// the zeros of P_{Q-1} + P_Q by Newton's method from the Chebyshev-Radau
+// points -cos(2 pi i / (2Q - 1)), weights 2 / Q^2 at -1 and
+// (1 - x_i) / (Q^2 P_{Q-1}(x_i)^2) elsewhere (exact for degree 2Q - 2).
+spx_status gauss_radau(int Q, double* x, double* w) {
+  if (Q < 2 || Q > 16) return fail(SPX_ERR_INVALID_ARG, "Gauss-Radau points need 2 <= Q <= 16");
+  const double pi = 3.14159265358979323846;
+  x[0] = -1.0;
+  for (int i = 1; i < Q; ++i) {
+    double z = -std::cos(2.0 * pi * i / (2.0 * Q - 1.0));
+    for (int it = 0; it < 100; ++it) {
+      // f = P_{Q-1} + P_Q, f' = P'_{Q-1} + P'_Q by the Legendre recurrence
+      double a = 1.0, b = z, da = 0.0, db = 1.0;
+      for (int k = 1; k < Q; ++k) {
+        const double c = ((2.0 * k + 1.0) * z * b - k * a) / (k + 1.0);
+        const double dc = ((2.0 * k + 1.0) * (b + z * db) - k * da) / (k + 1.0);
+        a = b;
+        b = c;
+        da = db;
+        db = dc;
+      }
+      const double dz = (a + b) / (da + db);
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+  }
+  std::sort(x, x + Q);
+  for (int i = 0; i < Q; ++i) {
+    const double L = legendre_val(Q - 1, x[i]);
+    w[i] = i == 0 ? 2.0 / (Q * Q) : (1.0 - x[i]) / (Q * Q * L * L);
+  }
+  return SPX_OK;
+}
+
+// Tables of the collapsed-coordinate kernels (order P, Q points per direction):
+//   B1[Q][n]     modified basis psi^a at the Q GLL points;
+//   Bb[n][Q][n]  psi^b_{pq} at the Q Gauss-Radau points, [p][k][q] for the q of
+//                mode range of p (p = 0: psi^a_q, q <= P; p = P: psi^a_q, q < P;
+//                0 < p < P: ((1-z)/2)^(p+1) for q = 0 and
+//                ((1-z)/2)^(p+1) (1+z)/2 P^{(2p+1,1)}_{q-1}(z) for 0 < q < P - p),
+//                zero elsewhere;
+//   D1[Q][Q], D2[Q][Q]  collocation derivatives on the GLL / Gauss-Radau points;
+//   xg, wg, xr, wr      the two point sets and their weights.
+spx_status collapsed_tables(int P, int Q, double* B1, double* Bb, double* D1, double* D2, double* xg, double* wg,
+                            double* xr, double* wr) {
+  if (P < 1 || P > 8 || Q < P + 1 || Q > 16) return fail(SPX_ERR_INVALID_ARG, "collapsed tables: bad P or Q");
+  std::vector<double> g, gw, r(Q), rw(Q);
+  gll_points(Q, g, gw);
+  spx_status st = gauss_radau(Q, r.data(), rw.data());
+  if (st != SPX_OK) return st;
+  const int n = P + 1;
+  std::vector<double> A(Q * n), Ar(Q * n);
+  basis_tables(P, Q, nullptr, nullptr, A.data(), nullptr, nullptr);
+  for (int k = 0; k < Q; ++k) {   // psi^a at the Radau points
+    const double z = r[k];
+    for (int q = 0; q < n; ++q) {
+      double v;
+      if (q == 0) v = 0.5 * (1.0 - z);
+      else if (q == P) v = 0.5 * (1.0 + z);
+      else v = 0.25 * (1.0 - z) * (1.0 + z) * jacobi_ab(q - 1, 1.0, 1.0, z);
+      Ar[k * n + q] = v;
+    }
+  }
+  if (B1) std::copy(A.begin(), A.end(), B1);
+  if (Bb) {
+    std::fill(Bb, Bb + n * Q * n, 0.0);
+    for (int p = 0; p <= P; ++p)
+      for (int k = 0; k < Q; ++k) {
+        const double z = r[k], L = 0.5 * (1.0 - z), R = 0.5 * (1.0 + z);
+        if (p == 0 || p == P) {
+          const int nq = p == 0 ? n : P;
+          for (int q = 0; q < nq; ++q) Bb[(p * Q + k) * n + q] = Ar[k * n + q];
+        } else {
+          const double Lp = std::pow(L, p + 1);
+          for (int q = 0; q < P - p; ++q)
+            Bb[(p * Q + k) * n + q] = q == 0 ? Lp : Lp * R * jacobi_ab(q - 1, 2.0 * p + 1.0, 1.0, z);
+        }
+      }
+  }
+  if (D1) collocation(g, D1);
+  if (D2) collocation(r, D2);
+  if (xg) std::copy(g.begin(), g.end(), xg);
+  if (wg) std::copy(gw.begin(), gw.end(), wg);
+  if (xr) std::copy(r.begin(), r.end(), xr);
+  if (wr) std::copy(rw.begin(), rw.end(), wr);
+  return SPX_OK;
+}
 
 spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* dB, double* D) {
   if (P < 1 || Q < 2 || Q > 16) return fail(SPX_ERR_INVALID_ARG, "basis tables need 1 <= P and 2 <= Q <= 16");

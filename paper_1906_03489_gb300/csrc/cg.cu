@@ -820,6 +820,7 @@ spx_status cg_solve_impl(const spx_plan* plan, double lambda, const int32_t* l2g
                          void* stream, bool own_resources) {
   if (!plan || !o || !res) return fail(SPX_ERR_INVALID_ARG, "cg_solve: NULL argument");
   std::memset(res, 0, sizeof(*res));
+  if (plan->shape) return fail(SPX_ERR_UNSUPPORTED, "cg_solve: triangles / prisms are not supported by the solver");
   if (n_global < 0 || n_global > (int64_t(1) << 31) - 2 || plan->n_coef > (int64_t(1) << 31) - 1)
     return fail(SPX_ERR_INVALID_ARG, "cg_solve: sizes exceed the int32 index range");
   if (n_global == 0) return SPX_OK;

@@ -1,0 +1,592 @@
+// Collapsed-coordinate elements: triangles (2D) and prisms (3D), §2.1
+// (Fig. f:duffy: the Duffy map from the square / cube onto the reference
+// shape, Table t:refregions) with the sum-factorisation of §3.3.
+//
+// In collapsed coordinates eta the modal basis is a product of 1D functions
+// whose collapsed-direction factor psi^b_{pq} depends on the mode index p of
+// the direction before it, so the contraction along the collapsed direction
+// runs over a p-dependent range of q ("ragged" but still one direction at a
+// time, O(P^{d+1}) work):
+//   triangle  u(eta1_i, eta2_j) = sum_p psi^a_p(eta1_i) sum_q c_{pq} psi^b_{pq}(eta2_j)
+//   prism     u(xi1_i, eta2_j, eta3_k) = sum_a psi^a_a(xi1_i) sum_p psi^a_p(eta2_j)
+//                                         sum_q c_{a,pq} psi^b_{pq}(eta3_k)
+// Mode (p, q) = (0, P) is the collapsed vertex: its function (1 + z)/2 equals
+// psi^a_0 psi^a_P + psi^a_P psi^a_P, so its coefficient also enters the
+// p = P row of the collapsed-direction contraction (and, transposed, its
+// inner product collects both rows).  Quadrature: Q = P + 2 Gauss-Lobatto
+// points in the uncollapsed directions, Gauss-Radau in the collapsed one
+// (the collapsed vertex is not a point); the Duffy Jacobian is folded into
+// the geometric factors, which hold d eta / d x (not d xi / d x) so that the
+// gradient is taken along the collapsed directions with the 1D collocation
+// derivatives and the folded factors do the rest, as for quads / hexes.
+//
+// One kernel per (shape, operator, order, precision): a CTA walks tiles of
+// consecutive elements; the basis tables are copied to shared memory once per
+// CTA (they are indexed with run-time mode indices); inputs are loaded with
+// coalesced reads, every stage is a loop of independent work items over the
+// tile's elements, outputs are stored straight to HBM.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "spx_internal.h"
+
+namespace spx {
+namespace {
+
+constexpr int kTri = 1, kPrism = 2;
+
+template <int P>
+struct Tri {
+  // first storage index of the modes of row p (p = 0..P) and their count
+  __host__ __device__ static constexpr int off(int p) {
+    return p == 0 ? 0 : (P + 1) + (p - 1) * P - (p - 1) * p / 2;
+  }
+  __host__ __device__ static constexpr int cnt(int p) { return p == 0 ? P + 1 : (p == P ? P : P - p); }
+  static constexpr int nm = (P + 1) * (P + 2) / 2;
+};
+
+template <typename T, int P>
+struct CParams {
+  static constexpr int n = P + 1, Q = P + 2;
+  T B1[Q * n];       // psi^a at the GLL points, [i][p]
+  T Bb[n * Q * n];   // psi^b_{pq} at the Radau points, [p][k][q]
+  T D1[Q * Q];       // collocation derivative, GLL points
+  T D2[Q * Q];       // collocation derivative, Radau points
+  const Tile* tiles;
+  int n_tiles;
+  int eb;            // elements per tile (buffer stride)
+  const T* in0;
+  const T* geom;     // folded factors (nf blocks of Q^d) or d eta / d x (d^2 blocks)
+  const T* lam_f;
+  const T* kap_f;
+  T* out0;
+  T* out1;
+  T* out2;
+  double lam;
+};
+
+// shared-memory carve-up per element (values of T)
+template <int SHAPE, int P>
+struct CLayout {
+  static_assert(SHAPE == kTri || SHAPE == kPrism, "triangles and prisms");
+  static constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
+  static constexpr int NQ = SHAPE == kTri ? Q * Q : Q * Q * Q;    // quadrature points
+  static constexpr int NM = SHAPE == kTri ? nt : n * nt;         // modes
+  static constexpr int NF = SHAPE == kTri ? n * Q : n * n * Q;   // after the collapsed-direction stage
+  static constexpr int NH = SHAPE == kTri ? 0 : n * Q * Q;       // prism: after the second stage
+  // buffers: C (modes), F, H, U, G0, G1, G2, V
+  static constexpr int per_elem = NM + NF + NH + 5 * NQ;
+  static constexpr int tables = Q * n + n * Q * n + 2 * Q * Q;
+};
+
+template <typename T, int SHAPE, int P>
+struct Bufs {
+  using L = CLayout<SHAPE, P>;
+  T *B1, *Bb, *D1, *D2, *C, *F, *H, *U, *G0, *G1, *G2, *V;
+  __device__ Bufs(T* sm, int eb) {
+    B1 = sm;
+    Bb = B1 + L::Q * L::n;
+    D1 = Bb + L::n * L::Q * L::n;
+    D2 = D1 + L::Q * L::Q;
+    C = D2 + L::Q * L::Q;
+    F = C + eb * L::NM;
+    H = F + eb * L::NF;
+    U = H + eb * L::NH;
+    G0 = U + eb * L::NQ;
+    G1 = G0 + eb * L::NQ;
+    G2 = G1 + eb * L::NQ;
+    V = G2 + eb * L::NQ;
+  }
+};
+
+// ---- collapsed-direction stages ------------------------------------------
+// forward: F[e][.. p ..][k] = sum_q C[e][mode(p, q)] Bb[p][k][q] (+ the collapsed vertex in row P);
+// `outer` = the number of leading mode blocks (1 triangle, n prism: mode a + n m).
+template <typename T, int P, int OUTER>
+__device__ __forceinline__ void stage_b_fwd(const T* C, T* F, const T* Bb, int ne, int tid, int nthr) {
+  constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
+  constexpr int items = OUTER * n * Q;
+  for (int w = tid; w < ne * items; w += nthr) {
+    const int e = w / items, r = w - e * items;
+    const int a = r % OUTER, pk = r / OUTER;     // a fastest
+    const int p = pk % n, k = pk / n;
+    const T* c = C + e * OUTER * nt + a;         // mode m at c[OUTER * m]
+    const T* b = Bb + (p * Q + k) * n;
+    const int o = Tri<P>::off(p), m = Tri<P>::cnt(p);
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < n; ++q)
+      if (q < m) acc = fma(c[OUTER * (o + q)], b[q], acc);
+    if (p == P) acc = fma(c[OUTER * P], Bb[k * n + P], acc);   // collapsed vertex (0, P)
+    F[e * OUTER * n * Q + a + OUTER * (p + n * k)] = acc;
+  }
+}
+
+// transposed: out[e][mode(p, q)] = sum_k Bb[p][k][q] F[e][.. p ..][k] (+ row P for the collapsed vertex)
+template <typename T, int P, int OUTER>
+__device__ __forceinline__ void stage_b_bwd(const T* F, T* out, int64_t e_base, const T* Bb, int ne, int tid,
+                                            int nthr) {
+  constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
+  constexpr int items = OUTER * nt;
+  for (int w = tid; w < ne * items; w += nthr) {
+    const int e = w / items, r = w - e * items;
+    const int a = r % OUTER, mi = r / OUTER;
+    int p = 0;
+#pragma unroll
+    for (int pp = 1; pp <= P; ++pp)
+      if (mi >= Tri<P>::off(pp)) p = pp;
+    const int q = mi - Tri<P>::off(p);
+    const T* f = F + e * OUTER * n * Q + a + OUTER * p;
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) acc = fma(Bb[(p * Q + k) * n + q], f[OUTER * n * k], acc);
+    if (p == 0 && q == P) {   // collapsed vertex: also row P
+      const T* fP = F + e * OUTER * n * Q + a + OUTER * P;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) acc = fma(Bb[k * n + P], fP[OUTER * n * k], acc);
+    }
+    out[(e_base + e) * OUTER * nt + r] = acc;
+  }
+}
+
+// ---- dense 1D stages on the tensor part ------------------------------------
+// y[e][.. i along axis ..] = sum_c A[i][c] x[e][.. c ..] (TR: A[c][i]); extents
+// (N0, N1, N2) in and the same with axis AX resized to M out, axis 0 fastest.
+template <int AX, int N0, int N1, int N2, int M, bool TR, bool ACC, typename T>
+__device__ __forceinline__ void stage_dense(const T* x, T* y, const T* A, int ne, int tid, int nthr, int64_t ystride,
+                                            int64_t ybase) {
+  constexpr int NA = AX == 0 ? N0 : (AX == 1 ? N1 : N2);
+  constexpr int O0 = AX == 0 ? M : N0, O1 = AX == 1 ? M : N1, O2 = AX == 2 ? M : N2;
+  constexpr int XS = N0 * N1 * N2, YS = O0 * O1 * O2;
+  constexpr int SA = AX == 0 ? 1 : (AX == 1 ? N0 : N0 * N1);
+  constexpr int SO = AX == 0 ? 1 : (AX == 1 ? O0 : O0 * O1);
+  for (int w = tid; w < ne * YS; w += nthr) {
+    const int e = w / YS, r = w - e * YS;
+    const int i0 = r % O0, i1 = (r / O0) % O1, i2 = r / (O0 * O1);
+    const int m = AX == 0 ? i0 : (AX == 1 ? i1 : i2);
+    const int xb = (AX == 0 ? 0 : i0) + (AX == 1 ? 0 : i1 * N0) + (AX == 2 ? 0 : i2 * N0 * N1);
+    const T* xe = x + e * XS + xb;
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < NA; ++c) acc = fma(TR ? A[c * M + m] : A[m * NA + c], xe[c * SA], acc);
+    T* yo = y + ybase + e * ystride + r;
+    if (ACC) *yo += acc;
+    else *yo = acc;
+    (void)SO;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_tile(const T* g, T* s, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s[i] = g[i];
+}
+
+// ---- the kernel -------------------------------------------------------------
+// OP: OP_BWD, OP_IPROD, OP_DERIV, OP_HELM.
+template <typename T, int SHAPE, int OP, int P>
+__global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ CParams<T, P> p) {
+  using L = CLayout<SHAPE, P>;
+  constexpr int n = L::n, Q = L::Q, nt = L::nt, NQ = L::NQ, NM = L::NM;
+  constexpr int DIM = SHAPE == kTri ? 2 : 3;
+  constexpr int NFG = DIM == 3 ? 7 : 4;
+  extern __shared__ __align__(16) unsigned char csm[];
+  Bufs<T, SHAPE, P> b(reinterpret_cast<T*>(csm), p.eb);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int i = tid; i < Q * n; i += nthr) b.B1[i] = p.B1[i];
+  for (int i = tid; i < n * Q * n; i += nthr) b.Bb[i] = p.Bb[i];
+  for (int i = tid; i < Q * Q; i += nthr) {
+    b.D1[i] = p.D1[i];
+    b.D2[i] = p.D2[i];
+  }
+  __syncthreads();
+  for (int ti = blockIdx.x; ti < p.n_tiles; ti += gridDim.x) {
+    const Tile t = p.tiles[ti];
+    const int ne = t.count;
+    const int64_t e0 = t.first;
+    if constexpr (OP == OP_BWD || OP == OP_HELM) {
+      load_tile(p.in0 + e0 * NM, b.C, ne * NM);
+      __syncthreads();
+      // collapsed direction, then the tensor directions -> U (or straight to HBM)
+      T* dst = OP == OP_BWD ? p.out0 : b.U;
+      const int64_t dbase = OP == OP_BWD ? e0 * NQ : 0;
+      if constexpr (SHAPE == kTri) {
+        stage_b_fwd<T, P, 1>(b.C, b.F, b.Bb, ne, tid, nthr);
+        __syncthreads();
+        stage_dense<0, n, Q, 1, Q, false, false>(b.F, dst, b.B1, ne, tid, nthr, NQ, dbase);   // F[p][j] -> u[i][j]
+      } else {
+        stage_b_fwd<T, P, n>(b.C, b.F, b.Bb, ne, tid, nthr);                                 // F[a][p][k]
+        __syncthreads();
+        stage_dense<1, n, n, Q, Q, false, false>(b.F, b.H, b.B1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
+        __syncthreads();
+        stage_dense<0, n, Q, Q, Q, false, false>(b.H, dst, b.B1, ne, tid, nthr, NQ, dbase);     // u[i][j][k]
+      }
+      __syncthreads();
+    } else {
+      load_tile(p.in0 + e0 * NQ, OP == OP_DERIV ? b.U : b.V, ne * NQ);
+      __syncthreads();
+    }
+    if constexpr (OP == OP_DERIV || OP == OP_HELM) {
+      // gradient along the collapsed directions: G0, G1 (, G2)
+      if constexpr (SHAPE == kTri) {
+        stage_dense<0, Q, Q, 1, Q, false, false>(b.U, b.G0, b.D1, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, 1, Q, false, false>(b.U, b.G1, b.D2, ne, tid, nthr, NQ, 0);
+      } else {
+        stage_dense<0, Q, Q, Q, Q, false, false>(b.U, b.G0, b.D1, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, Q, Q, false, false>(b.U, b.G1, b.D1, ne, tid, nthr, NQ, 0);
+        stage_dense<2, Q, Q, Q, Q, false, false>(b.U, b.G2, b.D2, ne, tid, nthr, NQ, 0);
+      }
+      __syncthreads();
+    }
+    if constexpr (OP == OP_DERIV) {
+      T* outs[3] = {p.out0, p.out1, p.out2};
+      for (int w = tid; w < ne * NQ; w += nthr) {
+        const int e = w / NQ, q = w - e * NQ;
+        const T* K = p.geom + (e0 + e) * DIM * DIM * NQ + q;   // d eta_a / d x_m, block a d + m
+        T d[DIM];
+        d[0] = b.G0[w];
+        d[1] = b.G1[w];
+        if (DIM == 3) d[DIM - 1] = b.G2[w];
+#pragma unroll
+        for (int m = 0; m < DIM; ++m) {
+          T acc = T(0);
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) acc = fma(K[(a * DIM + m) * NQ], d[a], acc);
+          outs[m][(e0 + e) * NQ + q] = acc;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    if constexpr (OP == OP_HELM) {
+      // pointwise: g_a = kappa sum_b G_ab d_b (into G0, G1, G2), V = lambda JW u
+      for (int w = tid; w < ne * NQ; w += nthr) {
+        const int e = w / NQ, q = w - e * NQ;
+        const T* G = p.geom + (e0 + e) * NFG * NQ + q;
+        const T kk = p.kap_f ? p.kap_f[(e0 + e) * NQ + q] : T(1);
+        const T ll = p.lam_f ? p.lam_f[(e0 + e) * NQ + q] : static_cast<T>(p.lam);
+        if constexpr (DIM == 2) {
+          const T d0 = b.G0[w], d1 = b.G1[w];
+          const T g00 = G[0], g01 = G[NQ], g11 = G[2 * NQ], jw = G[3 * NQ];
+          b.G0[w] = kk * fma(g01, d1, g00 * d0);
+          b.G1[w] = kk * fma(g11, d1, g01 * d0);
+          b.V[w] = ll * jw * b.U[w];
+        } else {
+          const T d0 = b.G0[w], d1 = b.G1[w], d2 = b.G2[w];
+          const T g00 = G[0], g01 = G[NQ], g02 = G[2 * NQ], g11 = G[3 * NQ], g12 = G[4 * NQ], g22 = G[5 * NQ];
+          const T jw = G[6 * NQ];
+          b.G0[w] = kk * fma(g02, d2, fma(g01, d1, g00 * d0));
+          b.G1[w] = kk * fma(g12, d2, fma(g11, d1, g01 * d0));
+          b.G2[w] = kk * fma(g22, d2, fma(g12, d1, g02 * d0));
+          b.V[w] = ll * jw * b.U[w];
+        }
+      }
+      __syncthreads();
+      // transposed gradient added to V
+      if constexpr (SHAPE == kTri) {
+        stage_dense<0, Q, Q, 1, Q, true, true>(b.G0, b.V, b.D1, ne, tid, nthr, NQ, 0);
+        __syncthreads();
+        stage_dense<1, Q, Q, 1, Q, true, true>(b.G1, b.V, b.D2, ne, tid, nthr, NQ, 0);
+      } else {
+        stage_dense<0, Q, Q, Q, Q, true, true>(b.G0, b.V, b.D1, ne, tid, nthr, NQ, 0);
+        __syncthreads();
+        stage_dense<1, Q, Q, Q, Q, true, true>(b.G1, b.V, b.D1, ne, tid, nthr, NQ, 0);
+        __syncthreads();
+        stage_dense<2, Q, Q, Q, Q, true, true>(b.G2, b.V, b.D2, ne, tid, nthr, NQ, 0);
+      }
+      __syncthreads();
+    }
+    if constexpr (OP == OP_IPROD) {
+      for (int w = tid; w < ne * NQ; w += nthr) {
+        const int e = w / NQ, q = w - e * NQ;
+        b.V[w] *= p.geom[(e0 + e) * NFG * NQ + (NFG - 1) * NQ + q];
+      }
+      __syncthreads();
+    }
+    if constexpr (OP == OP_IPROD || OP == OP_HELM) {
+      // transposed tensor directions, then the collapsed direction -> HBM
+      if constexpr (SHAPE == kTri) {
+        stage_dense<0, Q, Q, 1, n, true, false>(b.V, b.F, b.B1, ne, tid, nthr, n * Q, 0);   // F[p][k]
+        __syncthreads();
+        stage_b_bwd<T, P, 1>(b.F, p.out0, e0, b.Bb, ne, tid, nthr);
+      } else {
+        stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, b.B1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
+        __syncthreads();
+        stage_dense<1, n, Q, Q, n, true, false>(b.H, b.F, b.B1, ne, tid, nthr, n * n * Q, 0);  // F[a][p][k]
+        __syncthreads();
+        stage_b_bwd<T, P, n>(b.F, p.out0, e0, b.Bb, ne, tid, nthr);
+      }
+    }
+    __syncthreads();   // the tile's buffers are reused by the next tile
+  }
+  (void)nt;
+}
+
+}  // namespace
+}  // namespace spx
+
+// ===========================================================================
+// Host side
+// ===========================================================================
+namespace spx {
+
+// Shared-memory bytes of a collapsed-element launch: tables + eb elements' buffers.
+template <typename T, int SHAPE, int P>
+size_t collapsed_smem_t(int eb) {
+  using L = CLayout<SHAPE, P>;
+  return size_t(L::tables + eb * L::per_elem) * sizeof(T);
+}
+
+#if defined(SPX_CT)
+namespace {
+template <typename T, int SHAPE, int OP, int P>
+spx_status launch_c(const LaunchReq& r) {
+  using Prm = CParams<T, P>;
+  const spx_plan* plan = r.plan;
+  const LaunchCfg& cfg = plan->cfg[OP][r.dtype];
+  const TileList& tl = plan->tiles[OP][r.dtype];
+  if (tl.n == 0) return SPX_OK;
+  Prm prm{};
+  constexpr int n = P + 1, Q = P + 2;
+  const std::vector<double>& ct = plan->ctab;   // B1, Bb, D1, D2 (FP64)
+  int o = 0;
+  for (int i = 0; i < Q * n; ++i) prm.B1[i] = static_cast<T>(ct[o++]);
+  for (int i = 0; i < n * Q * n; ++i) prm.Bb[i] = static_cast<T>(ct[o++]);
+  for (int i = 0; i < Q * Q; ++i) prm.D1[i] = static_cast<T>(ct[o++]);
+  for (int i = 0; i < Q * Q; ++i) prm.D2[i] = static_cast<T>(ct[o++]);
+  prm.tiles = tl.d;
+  prm.n_tiles = tl.n;
+  prm.eb = cfg.order[P].eb;
+  prm.in0 = static_cast<const T*>(r.in0);
+  prm.geom = static_cast<const T*>(r.geom);
+  prm.lam_f = static_cast<const T*>(r.lam_f);
+  prm.kap_f = static_cast<const T*>(r.kap_f);
+  prm.out0 = static_cast<T*>(r.out0);
+  prm.out1 = static_cast<T*>(r.out1);
+  prm.out2 = static_cast<T*>(r.out2);
+  prm.lam = r.lam;
+  const size_t smem = collapsed_smem_t<T, SHAPE, P>(prm.eb);
+  if (smem > plan->max_smem) return fail(SPX_ERR_UNSUPPORTED, "collapsed tile does not fit in shared memory");
+  auto kern = collapsed_kernel<T, SHAPE, OP, P>;
+  static std::mutex mu;
+  static bool configured = false;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(plan->max_smem));
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      configured = true;
+    }
+  }
+  const int nthr = cfg.nthreads;
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthr, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "collapsed tile does not fit on an SM");
+  const int grid = static_cast<int>(std::min<int64_t>(tl.n, int64_t(nb) * plan->num_sms));
+  kern<<<grid, nthr, smem, r.stream>>>(prm);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e, "collapsed kernel launch");
+}
+
+template <typename T, int SHAPE, int OP>
+spx_status launch_orders(const LaunchReq& r) {
+  switch (r.plan->uP) {
+    case 1: return launch_c<T, SHAPE, OP, 1>(r);
+    case 2: return launch_c<T, SHAPE, OP, 2>(r);
+    case 3: return launch_c<T, SHAPE, OP, 3>(r);
+    case 4: return launch_c<T, SHAPE, OP, 4>(r);
+    case 5: return launch_c<T, SHAPE, OP, 5>(r);
+    case 6: return launch_c<T, SHAPE, OP, 6>(r);
+    case 7: return launch_c<T, SHAPE, OP, 7>(r);
+    case 8: return launch_c<T, SHAPE, OP, 8>(r);
+    default: return fail(SPX_ERR_UNSUPPORTED, "order out of range");
+  }
+}
+
+template <int SHAPE, int P>
+size_t smem_orders_t(int dtype, int eb) {
+  return dtype == 0 ? collapsed_smem_t<double, SHAPE, P>(eb) : collapsed_smem_t<float, SHAPE, P>(eb);
+}
+}  // namespace
+
+#define SPX_C_CAT_(a, b, c) a##b##_##c
+#define SPX_C_CAT(a, b, c) SPX_C_CAT_(a, b, c)
+#define SPX_C_T_f32 float
+#define SPX_C_T_f64 double
+#define SPX_C_TYPE_(tn) SPX_C_T_##tn
+#define SPX_C_TYPE(tn) SPX_C_TYPE_(tn)
+// launch_collapsed_<tn>_<shape>: the operators of one precision and shape
+spx_status SPX_C_CAT(launch_collapsed_, SPX_CT, SPX_CS)(const LaunchReq& r) {
+  using T = SPX_C_TYPE(SPX_CT);
+  switch (r.op) {
+    case OP_BWD: return launch_orders<T, SPX_CS, OP_BWD>(r);
+    case OP_IPROD: return launch_orders<T, SPX_CS, OP_IPROD>(r);
+    case OP_DERIV: return launch_orders<T, SPX_CS, OP_DERIV>(r);
+    case OP_HELM: return launch_orders<T, SPX_CS, OP_HELM>(r);
+    default: return fail(SPX_ERR_UNSUPPORTED, "operator not available for triangles / prisms");
+  }
+}
+#endif  // SPX_CT
+
+#if defined(SPX_CGEOM)
+// Shared-memory bytes of a collapsed-element launch (api.cu's tile checks).
+size_t collapsed_smem_bytes(const spx_plan* plan, int dtype, int eb) {
+  const int P = plan->uP;
+  switch (plan->shape * 16 + P) {
+#define SPX_CSM(S, Pv) \
+  case S * 16 + Pv: return dtype == 0 ? collapsed_smem_t<double, S, Pv>(eb) : collapsed_smem_t<float, S, Pv>(eb);
+    SPX_CSM(1, 1) SPX_CSM(1, 2) SPX_CSM(1, 3) SPX_CSM(1, 4) SPX_CSM(1, 5) SPX_CSM(1, 6) SPX_CSM(1, 7) SPX_CSM(1, 8)
+    SPX_CSM(2, 1) SPX_CSM(2, 2) SPX_CSM(2, 3) SPX_CSM(2, 4) SPX_CSM(2, 5) SPX_CSM(2, 6) SPX_CSM(2, 7) SPX_CSM(2, 8)
+#undef SPX_CSM
+    default: return SIZE_MAX;
+  }
+}
+
+spx_status launch_collapsed_f64_1(const LaunchReq& r);
+spx_status launch_collapsed_f64_2(const LaunchReq& r);
+spx_status launch_collapsed_f32_1(const LaunchReq& r);
+spx_status launch_collapsed_f32_2(const LaunchReq& r);
+
+spx_status launch_collapsed(const LaunchReq& r) {
+  const bool tri = r.plan->shape == kTri;
+  if (r.dtype == 0) return tri ? launch_collapsed_f64_1(r) : launch_collapsed_f64_2(r);
+  return tri ? launch_collapsed_f32_1(r) : launch_collapsed_f32_2(r);
+}
+
+// ---- geometric factors of affine collapsed elements (FP64) ------------------
+// One thread per quadrature point: J = [(V_c - V0) / 2]_c (constant on the
+// element), d eta / d x = (d eta / d xi) J^{-1} with the collapse's chain rule,
+// JW = w det J including the Duffy factor, G = JW (d eta/dx)(d eta/dx)^T.
+struct CGeomParams {
+  const double* verts;     // [E][d+1][d]
+  double* geom;            // [E][nf][Q^d] or NULL
+  double* dxi;             // [E][d*d][Q^d] or NULL
+  double* xq;              // [E][d][Q^d] or NULL
+  float* geom32;
+  float* dxi32;
+  int64_t E;
+  int d, Q;
+  double xg[16], wg[16], xr[16], wr[16];
+};
+
+__global__ void collapsed_geom_kernel(const __grid_constant__ CGeomParams g) {
+  const int d = g.d, Q = g.Q;
+  const int NQ = d == 2 ? Q * Q : Q * Q * Q;
+  const int nf = d == 2 ? 4 : 7;
+  const int64_t total = g.E * NQ;
+  for (int64_t w = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; w < total; w += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t e = w / NQ;
+    const int q = static_cast<int>(w - e * NQ);
+    const double* V = g.verts + e * (d + 1) * d;
+    double J[3][3] = {}, Ji[3][3] = {};
+    for (int m = 0; m < d; ++m)
+      for (int c = 0; c < d; ++c) J[m][c] = 0.5 * (V[(c + 1) * d + m] - V[m]);
+    double det;
+    if (d == 2) {
+      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      Ji[0][0] = J[1][1] / det;
+      Ji[0][1] = -J[0][1] / det;
+      Ji[1][0] = -J[1][0] / det;
+      Ji[1][1] = J[0][0] / det;
+    } else {
+      det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {   // inverse = adjugate / det
+          const int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
+          Ji[i][j] = (J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1]) / det;
+        }
+    }
+    // collapsed point, reference point, weight, d eta / d xi
+    double eta[3] = {}, xi[3] = {}, K[3][3] = {}, wt;
+    if (d == 2) {
+      const int i = q % Q, j = q / Q;
+      eta[0] = g.xg[i];
+      eta[1] = g.xr[j];
+      const double s = 1.0 / (1.0 - eta[1]);
+      xi[0] = 0.5 * (1.0 + eta[0]) * (1.0 - eta[1]) - 1.0;
+      xi[1] = eta[1];
+      K[0][0] = 2.0 * s;
+      K[0][1] = (1.0 + eta[0]) * s;
+      K[1][1] = 1.0;
+      wt = g.wg[i] * g.wr[j] * 0.5 * (1.0 - eta[1]);
+    } else {
+      const int i = q % Q, j = (q / Q) % Q, k = q / (Q * Q);
+      eta[0] = g.xg[i];
+      eta[1] = g.xg[j];
+      eta[2] = g.xr[k];
+      const double s = 1.0 / (1.0 - eta[2]);
+      xi[0] = eta[0];
+      xi[1] = 0.5 * (1.0 + eta[1]) * (1.0 - eta[2]) - 1.0;
+      xi[2] = eta[2];
+      K[0][0] = 1.0;
+      K[1][1] = 2.0 * s;
+      K[1][2] = (1.0 + eta[1]) * s;
+      K[2][2] = 1.0;
+      wt = g.wg[i] * g.wg[j] * g.wr[k] * 0.5 * (1.0 - eta[2]);
+    }
+    double Kx[3][3] = {};   // d eta_a / d x_m
+    for (int a = 0; a < d; ++a)
+      for (int m = 0; m < d; ++m) {
+        double acc = 0.0;
+        for (int c = 0; c < d; ++c) acc += K[a][c] * Ji[c][m];
+        Kx[a][m] = acc;
+      }
+    const double jw = wt * det;
+    const int64_t base = e * NQ;
+    if (g.geom || g.geom32) {
+      double f[7];
+      int t = 0;
+      for (int a = 0; a < d; ++a)
+        for (int b2 = a; b2 < d; ++b2) {
+          double acc = 0.0;
+          for (int m = 0; m < d; ++m) acc += Kx[a][m] * Kx[b2][m];
+          f[t++] = jw * acc;
+        }
+      f[t++] = jw;
+      for (int s2 = 0; s2 < nf; ++s2) {
+        if (g.geom) g.geom[(base * nf) + s2 * NQ + q] = f[s2];
+        if (g.geom32) g.geom32[(base * nf) + s2 * NQ + q] = static_cast<float>(f[s2]);
+      }
+    }
+    if (g.dxi || g.dxi32)
+      for (int a = 0; a < d; ++a)
+        for (int m = 0; m < d; ++m) {
+          const int64_t o = base * d * d + (a * d + m) * int64_t(NQ) + q;
+          if (g.dxi) g.dxi[o] = Kx[a][m];
+          if (g.dxi32) g.dxi32[o] = static_cast<float>(Kx[a][m]);
+        }
+    if (g.xq)
+      for (int m = 0; m < d; ++m) {
+        double x = V[m];
+        for (int c = 0; c < d; ++c) x += J[m][c] * (xi[c] + 1.0);
+        g.xq[base * d + m * int64_t(NQ) + q] = x;
+      }
+  }
+}
+
+spx_status collapsed_geom(const spx_plan* plan, const double* verts, double* geom, double* dxi, double* xq,
+                          float* geom32, float* dxi32, cudaStream_t st) {
+  CGeomParams g{};
+  g.verts = verts;
+  g.geom = geom;
+  g.dxi = dxi;
+  g.xq = xq;
+  g.geom32 = geom32;
+  g.dxi32 = dxi32;
+  g.E = plan->E;
+  g.d = plan->dim;
+  g.Q = plan->uP + 2;
+  spx_status s = collapsed_tables(plan->uP, g.Q, nullptr, nullptr, nullptr, nullptr, g.xg, g.wg, g.xr, g.wr);
+  if (s != SPX_OK) return s;
+  const int64_t total = plan->E * (plan->dim == 2 ? g.Q * g.Q : g.Q * g.Q * g.Q);
+  const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, int64_t(plan->num_sms) * 32));
+  collapsed_geom_kernel<<<grid, 256, 0, st>>>(g);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPX_OK : cuda_fail(e, "collapsed geometry kernel launch");
+}
+#endif  // SPX_CGEOM
+
+}  // namespace spx

@@ -406,6 +406,7 @@ extern "C" spx_status spx_geom_factors(const spx_plan* plan, const double* nodes
   if (plan->E == 0) return SPX_OK;
   if (!nodes) return fail(SPX_ERR_INVALID_ARG, "geom_factors: NULL nodes");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->shape) return collapsed_geom(plan, nodes, geom, dxi, xq, geom32, dxi32, st);
   for (int P = 1; P <= kMaxP; ++P) {
     if (!plan->present[P]) continue;
     const int32_t* ids = plan->uniform ? nullptr : plan->d_ids;

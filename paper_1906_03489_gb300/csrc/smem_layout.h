@@ -134,7 +134,7 @@ inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg, int thr)
 inline int pair_threshold(const spx_plan* plan) { return plan->uniform ? kMaxP : kPairThrVar; }
 
 inline bool uses_pair_kernel(const spx_plan* plan, int op, int dtype) {
-  return op == OP_HELM && dtype == 1 && plan->dim == 3 && plan->bkind == BK_PARITY;
+  return op == OP_HELM && dtype == 1 && plan->dim == 3 && plan->bkind == BK_PARITY && !plan->shape;
 }
 
 }  // namespace spx

@@ -69,6 +69,8 @@ struct spx_plan {
   // host basis tables (FP64) per order: B[Q][n], dB[Q][n], D[Q][Q], then the
   // even-odd coefficients (EOLayout)
   std::vector<double> tab[spx::kMaxP1];
+  int shape = 0;                         // spx_shape
+  std::vector<double> ctab;              // collapsed shapes: B1, Bb, D1, D2 (FP64, collapsed.cu)
   int bkind = 0;                         // BasisKind of the 3D Helmholtz kernels
   bool custom_basis = false;             // tables differ from the library's modified basis
 };
@@ -120,6 +122,13 @@ spx_status launch_f32_helm3_bk2(const LaunchReq& r);
 
 spx_status launch_op(const LaunchReq& r);
 
+// Triangles and prisms (collapsed.cu): operator launch, shared memory of a
+// tile of eb elements, affine geometric factors.
+spx_status launch_collapsed(const LaunchReq& r);
+size_t collapsed_smem_bytes(const spx_plan* plan, int dtype, int eb);
+spx_status collapsed_geom(const spx_plan* plan, const double* verts, double* geom, double* dxi, double* xq,
+                          float* geom32, float* dxi32, cudaStream_t st);
+
 // Helmholtz apply for the solver: as spx_helmholtz (constant lambda, kappa =
 // 1), but the launch does nothing when *skip != 0 at the time it runs.
 spx_status helmholtz_unless(const spx_plan* p, int dtype, double lambda, const void* in, void* out,
@@ -131,6 +140,12 @@ size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& c
 
 // Basis tables (host FP64): fills B, dB, D as documented in spx.h.
 spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* dB, double* D);
+
+// Gauss-Radau-Legendre points (including -1) and weights.
+spx_status gauss_radau(int Q, double* x, double* w);
+// Tables of the collapsed-coordinate kernels (basis_host.cpp).
+spx_status collapsed_tables(int P, int Q, double* B1, double* Bb, double* D1, double* D2, double* xg, double* wg,
+                            double* xr, double* wr);
 
 // Nodal (Lagrange through the P + 1 GLL points) basis at the Q GLL points.
 spx_status nodal_basis_tables(int P, int Q, double* B, double* dB);

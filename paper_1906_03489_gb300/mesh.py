@@ -10,6 +10,7 @@ kernel consumes.  GLL nodes come from the library's own basis tables.
 import numpy as np
 import torch
 
+from . import synth
 from .binding import basis_tables
 
 
@@ -64,3 +65,39 @@ def periodic_l2g(dim, N, P, device="cuda"):
     g = [(pos[a][:, None] * P + modes[a][None, :]) % NP for a in range(dim)]
     gi = g[0] + NP * g[1] + (NP * NP * g[2] if dim == 3 else 0)
     return gi.reshape(-1).to(torch.int32).contiguous(), NP ** dim
+
+
+def collapsed_vertices(shape, N, jitter=None, device="cuda"):
+    """Defining vertices V0..Vd of affine triangles ("tri", 2 N^2) or prisms
+    ("prism", 2 N^3): FP64 tensor (E, d+1, d) in the library's vertex layout.
+
+    Grid nodes (i, j[, k]) / N pass through the skew synth.SKEW2 / SKEW3.  Each
+    square (cube) holds two elements, element 2 c + t for cell c = ex + N(ey
+    [+ N ez]): a triangle V0 = n(ex, ey), V1 = n(ex+1, ey), V2 = n(ex, ey+1) and
+    V0 = n(ex+1, ey+1), V1 = n(ex, ey+1), V2 = n(ex+1, ey); a prism over the
+    (y, z) triangle V0 = n(i, j, k), V1 = n(i+1, j, k), V2 = n(i, j+1, k),
+    V3 = n(i, j, k+1) and V0 = n(i, j+1, k+1), V1 = n(i+1, j+1, k+1),
+    V2 = n(i, j, k+1), V3 = n(i, j+1, k).  ``jitter``: optional (E, d+1, d)
+    array added to the vertices (elements stay affine, the mesh need not stay
+    conforming)."""
+    h = 1.0 / N
+    if shape == "tri":
+        S = np.array(synth.SKEW2)
+        ey, ex = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+        ex, ey = ex.ravel(), ey.ravel()
+        node = lambda i, j: (np.stack([i, j], -1) * h) @ S.T
+        lo = np.stack([node(ex, ey), node(ex + 1, ey), node(ex, ey + 1)], 1)
+        up = np.stack([node(ex + 1, ey + 1), node(ex, ey + 1), node(ex + 1, ey)], 1)
+    elif shape == "prism":
+        S = np.array(synth.SKEW3)
+        ez, ey, ex = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+        i, j, k = ex.ravel(), ey.ravel(), ez.ravel()
+        node = lambda a, b, c: (np.stack([a, b, c], -1) * h) @ S.T
+        lo = np.stack([node(i, j, k), node(i + 1, j, k), node(i, j + 1, k), node(i, j, k + 1)], 1)
+        up = np.stack([node(i, j + 1, k + 1), node(i + 1, j + 1, k + 1), node(i, j, k + 1), node(i, j + 1, k)], 1)
+    else:
+        raise ValueError("shape must be 'tri' or 'prism'")
+    V = np.stack([lo, up], 1).reshape(-1, lo.shape[1], lo.shape[2])
+    if jitter is not None:
+        V = V + np.asarray(jitter).reshape(V.shape)
+    return torch.tensor(V, dtype=torch.float64, device=device).contiguous()

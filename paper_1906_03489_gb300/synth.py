@@ -26,7 +26,17 @@ WORKLOADS = {
     "hex3d_16_p6": dict(dim=3, N=16, P=6, Q=8, amp=0.05, seed=4),
     # 3D hexes, 48^3 curved elements, P=4, Q=6: periodic C0 solve
     "hex3d_48_p4": dict(dim=3, N=48, P=4, Q=6, amp=0.05, seed=5),
+    # collapsed elements: 2 N^3 affine prisms (each cube of a skewed N^3 grid cut
+    # along a (y, z) diagonal), P=4, Q=6 (GLL, GLL, Gauss-Radau)
+    "prism3d_24_p4": dict(dim=3, N=24, P=4, Q=6, shape="prism", seed=6),
+    # 2 N^2 affine triangles of a skewed N^2 grid, P=4, Q=6 (GLL, Gauss-Radau)
+    "tri2d_128_p4": dict(dim=2, N=128, P=4, Q=6, shape="tri", seed=7),
 }
+
+# Skew of the collapsed-element grids (node (i, j[, k]) h maps to SKEW applied
+# to it): the elements are then affine but not right-angled.
+SKEW2 = ((1.0, 0.2), (0.1, 1.0))
+SKEW3 = ((1.0, 0.2, 0.1), (0.0, 1.0, 0.15), (0.05, 0.0, 1.0))
 
 
 def rng(seed):

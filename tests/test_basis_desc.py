@@ -76,3 +76,23 @@ def test_plan_refuses_inconsistent_basis(lib, case):
     expect = {"wrong_q": "P + q_offset", "bad_d": "collocation derivative", "bad_w": "GLL weights",
               "bad_db": "derivative of B", "missing_order": "no basis description", "nan": "not finite"}[case]
     assert expect in str(ei.value)
+
+
+@pytest.mark.parametrize("Q", [2, 3, 6, 9, 10])
+def test_gauss_radau_matches_oracle(lib, Q):
+    from oracle import collapsed
+    from paper_1906_03489_gb300 import gauss_radau
+    x, w = gauss_radau(Q)
+    xo, wo = collapsed.gauss_radau(Q)
+    np.testing.assert_allclose(x, xo, atol=1e-14)
+    np.testing.assert_allclose(w, wo, rtol=1e-12)
+
+
+def test_collapsed_plans_refuse_what_they_do_not_support(lib):
+    from paper_1906_03489_gb300 import Plan, SpxError
+    with pytest.raises(SpxError, match="triangles are 2D"):
+        Plan(3, 4, order=2, shape="tri")
+    with pytest.raises(SpxError, match="uniform order"):
+        Plan(2, 4, orders=np.array([2, 3, 2, 3], np.int32), shape="tri")
+    with pytest.raises(SpxError, match="uniform order"):
+        Plan(3, 4, order=2, q_offset=1, shape="prism")

@@ -219,3 +219,14 @@ def test_transpose_identity_and_polynomial_bwd():
     lhs = C.iproduct(m, f) @ u
     rhs = np.sum(m.JW[0] * f * C.bwd_trans(m, u))
     assert abs(lhs - rhs) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [C.TRI, C.PRISM])
+def test_structured_elements_tile_the_skewed_cell_volume(shape):
+    """The two elements of every cell cover it: total volume = det(skew) (the skewed unit square / cube)."""
+    skew = np.array([[1.0, 0.2], [0.1, 1.0]]) if shape == C.TRI else \
+        np.array([[1.0, 0.2, 0.1], [0.0, 1.0, 0.15], [0.05, 0.0, 1.0]])
+    V = C.structured_vertices(shape, 3, skew)
+    m = C.CollapsedMesh(shape, V, 2)
+    assert np.all(m.detJ > 0)
+    assert abs(m.JW.sum() - np.linalg.det(skew)) < 1e-13

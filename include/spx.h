@@ -337,8 +337,9 @@ spx_status spx_helmholtz_adjoint(const spx_plan *plan, const double *u, const do
  * (then bit 2 of the plan's device status word is set).
  * The coefficients are as ill-conditioned as M_e (cond about 4e7 at P = 4 in
  * 3D in this basis); the projected function BwdTrans(c) only by the square
- * root: about sqrt(cond) x unit roundoff, i.e. ~1e-12 in FP64 but ~1e-4 in
- * FP32 (use FP64 where the projection must be accurate).
+ * root: about sqrt(cond) x unit roundoff, ~1e-12 in FP64.  In FP32 that
+ * would be ~1e-4, far from the FP32 operators' 1e-5, so SPX_F32 is refused
+ * (SPX_ERR_UNSUPPORTED): FwdTrans is FP64 only.
  * phys: device in [n_quad]; coef: device out [n_coef] (must not alias phys).
  * Needs geom. */
 spx_status spx_fwd_trans(const spx_plan *plan, spx_dtype dtype, const void *phys, void *coef, void *stream);

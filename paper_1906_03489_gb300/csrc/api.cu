@@ -546,6 +546,10 @@ spx_status spx_helmholtz_adjoint(const spx_plan* p, const double* u, const doubl
 }
 
 spx_status spx_fwd_trans(const spx_plan* p, spx_dtype dt, const void* phys, void* coef, void* stream) {
+  if (dt == SPX_F32)
+    return fail(SPX_ERR_UNSUPPORTED, "fwd_trans: FP32 is refused: the elemental mass matrix's condition number "
+                                     "(about 4e7 at P = 4 in 3D) exceeds FP32's 1 / epsilon, so no FP32 solve "
+                                     "reaches the FP32 operator tolerance; use SPX_F64");
   if (p && p->E && (!coef || !phys)) return fail(SPX_ERR_INVALID_ARG, "fwd_trans: NULL buffer");
   if (p && phys && phys == coef) return fail(SPX_ERR_INVALID_ARG, "fwd_trans: coef must not alias phys");
   const void* aux = !p ? nullptr : (dt == SPX_F64 ? static_cast<const void*>(p->d_aux64) : p->d_aux32);

@@ -240,7 +240,10 @@ spx_status spx_plan_set_geometry(spx_plan *plan, spx_dtype dtype, const void *ge
  * batch `eb` (1..64), threads per block `nthreads` (32..512, multiple of
  * 32) and pipeline depth `stages` (1..4).  order = -1 sets every order.
  * Two operators derive their block size from eb instead:
- *  - FP64 3D Helmholtz: eb * Q^2 threads;
+ *  - FP64 3D Helmholtz (and any precision with a collocation basis): eb * Q^2
+ *    threads; there stages 0 reads the geometric factors from L2 (the tile's
+ *    factors are prefetched when it starts) instead of staging them in shared
+ *    memory, which leaves room for larger tiles;
  *  - FP32 3D Helmholtz (element-pair kernel): ceil(eb / 2) * Q^2 threads;
  *    there `nthreads` (32..1024) is the number of threads per SM that the
  *    register budget must allow (<= 512: 128 registers per thread, <= 640:

@@ -460,10 +460,13 @@ spx_status spx_plan_set_tile(spx_plan* p, spx_op op, spx_dtype dt, int order, in
   if (op < 0 || op >= OP_KINDS || (dt != SPX_F64 && dt != SPX_F32))
     return fail(SPX_ERR_INVALID_ARG, "set_tile: bad operator or dtype");
   const int max_nt = uses_pair_kernel(p, op, dt) ? 1024 : 512;
-  const int min_st = uses_pair_kernel(p, op, dt) ? 0 : 1;
+  // stages 0: the FP32 3D pair kernel's L2 prefetch distance, or the other 3D
+  // Helmholtz bodies with Q^2 threads per element reading geometry from L2
+  const bool role3 = op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL && !p->shape;
+  const int min_st = (uses_pair_kernel(p, op, dt) || role3) ? 0 : 1;
   if (eb < 1 || eb > kMaxEB || nthreads < 32 || nthreads > max_nt || nthreads % 32 || stages < min_st || stages > 4)
     return fail(SPX_ERR_INVALID_ARG, "set_tile: eb 1..64, nthreads 32..512 (1024 for the FP32 3D Helmholtz), "
-                                     "multiple of 32, stages 1..4 (0..4 for the FP32 3D Helmholtz)");
+                                     "multiple of 32, stages 1..4 (0..4 for the 3D Helmholtz)");
   if (order != -1 && (order < 1 || order > kMaxP)) return fail(SPX_ERR_INVALID_ARG, "set_tile: order outside 1..8");
   LaunchCfg c = p->cfg[op][dt];
   c.nthreads = nthreads;
@@ -652,7 +655,7 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
   // register budget (threads per SM) and `stages` the L2 prefetch distance
   const std::vector<int> nts = pair ? std::vector<int>{512, 640, 768}
                                     : (role ? std::vector<int>{256} : std::vector<int>{64, 128, 192, 256, 384, 512});
-  const std::vector<int> sts = pair ? std::vector<int>{0, 1, 2} : std::vector<int>{1, 2, 3};
+  const std::vector<int> sts = (pair || role) ? std::vector<int>{0, 1, 2} : std::vector<int>{1, 2, 3};
   LaunchCfg best = p->cfg[op][dt];
   // Variable order: one launch serves every order, so its CTA is sized by the
   // largest order's tile (threads and shared memory); an order whose tile
@@ -711,27 +714,36 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
   for (int P = 1; P <= kMaxP; ++P) {
     if (!p->present[P]) continue;
     float bms = 1e30f;
-    int beb = best.order[P].eb;
+    int beb = best.order[P].eb, bsg = best.stages;
+    // bodies with Q^2 threads per element: the tile size and the staging depth
+    // decide the CTAs per SM together (staged geometry is most of the shared
+    // memory), so they are searched jointly
+    const std::vector<int> sgs = role ? sts : std::vector<int>{best.stages};
     for (int eb : ebs) {
-      LaunchCfg c = best;
-      c.order[P].eb = eb;
-      if (op_smem_bytes(p, op, dt, c) > p->max_smem) continue;
-      p->cfg[op][dt] = c;
-      p->tiles[op][dt].dirty = true;
-      spx_status s;
-      float ms = time_op(p, op, dt, in, out, reps, st, &s);
-      if (s != SPX_OK) {
-        p->cfg[op][dt] = best;
+      for (int sg : sgs) {
+        LaunchCfg c = best;
+        c.order[P].eb = eb;
+        c.stages = sg;
+        if (op_smem_bytes(p, op, dt, c) > p->max_smem) continue;
+        p->cfg[op][dt] = c;
         p->tiles[op][dt].dirty = true;
-        if (s == SPX_ERR_UNSUPPORTED) continue;
-        return s;
-      }
-      if (ms < bms) {
-        bms = ms;
-        beb = eb;
+        spx_status s;
+        float ms = time_op(p, op, dt, in, out, reps, st, &s);
+        if (s != SPX_OK) {
+          p->cfg[op][dt] = best;
+          p->tiles[op][dt].dirty = true;
+          if (s == SPX_ERR_UNSUPPORTED) continue;
+          return s;
+        }
+        if (ms < bms) {
+          bms = ms;
+          beb = eb;
+          bsg = sg;
+        }
       }
     }
     best.order[P].eb = beb;
+    best.stages = bsg;
     best_ms = bms;
   }
   for (int nt : nts) {

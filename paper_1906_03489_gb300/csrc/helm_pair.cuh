@@ -37,17 +37,6 @@
 
 namespace spx {
 
-// L2 prefetch of [g, g + bytes): the 16-byte aligned interior only.
-__device__ __forceinline__ void prefetch_l2(const void* g, uint64_t bytes) {
-  const uintptr_t a0 = (reinterpret_cast<uintptr_t>(g) + 15) & ~uintptr_t(15);
-  const uintptr_t a1 = (reinterpret_cast<uintptr_t>(g) + bytes) & ~uintptr_t(15);
-  for (uintptr_t a = a0; a < a1;) {
-    const uint32_t n = static_cast<uint32_t>(a1 - a > (1u << 20) ? (1u << 20) : a1 - a);
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
-    a += n;
-  }
-}
-
 template <int PLO, int PHI, int QOFF>
 struct PairParams {
   KParams<float, PLO, PHI, QOFF> k;

@@ -162,6 +162,7 @@ struct KParams {
   double lam;
   int n_tiles;
   int stages;
+  int geo_direct;          // 3D Helmholtz bodies: geometry read from global memory (L2-prefetched), not staged
   uint32_t slot_base;      // byte offset of slot 0
   uint32_t slot_bytes;
   uint32_t region_off[5];  // per stream, inside a slot

@@ -137,7 +137,9 @@ spx_status launch_impl(const LaunchReq& r) {
   p.skip = r.skip;
   p.lam = r.lam;
   p.n_tiles = tl.n;
-  p.stages = cfg.stages;
+  // stages 0 (3D Helmholtz with Q^2 threads per element): geometry read from L2, one slot for the rest
+  p.geo_direct = (OP == OP_HELM && DIM == 3 && BK != 1 && cfg.stages == 0) ? 1 : 0;
+  p.stages = cfg.stages < 1 ? 1 : cfg.stages;
   const SmemLayout L = smem_layout(plan, OP, sizeof(T), cfg, r.lam_f != nullptr, r.kap_f != nullptr);
   if (L.total > plan->max_smem)
     return fail(SPX_ERR_UNSUPPORTED, "operator tile needs " + std::to_string(L.total) +

@@ -50,7 +50,7 @@ __device__ __forceinline__ int op_streams(const Prm& p, int P, int Q, StreamDesc
       break;
     case OP_HELM:
       s[k++] = {p.in0, nd, 1, 0, false, true};
-      s[k++] = {p.geom, nf * qd, nf, 0, true, true};
+      s[k++] = {p.geo_direct ? nullptr : p.geom, nf * qd, nf, 0, true, true};
       s[k++] = {p.lam_f, qd, 1, 0, true, true};
       s[k++] = {p.kap_f, qd, 1, 0, true, true};
       break;
@@ -147,6 +147,7 @@ struct Ctx {
   int* status;            // the plan's device status word
   bool has_lam, has_kap;
   T lam;
+  const T* geom_g;        // geometry in global memory when it is not staged (geo_direct), else nullptr
   __device__ const T* staged(int s, int j) const { return reinterpret_cast<const T*>(sm) + soff[s * kMaxEB + j]; }
 };
 
@@ -567,7 +568,8 @@ __device__ __forceinline__ void helm_mid(const T* tab, const Ctx<T>& c, int el, 
   // S5: column (i, j) = (a, b): pointwise; g0 -> W3, g1 -> W4, g2 and lambda JW in
   // registers; then z = D^T g2 + lambda JW u along xi_3
   if (act) {
-    const T* G = c.staged(1, el) + b * Q + a;
+    // geometric factors: staged in shared memory, or read from L2 (prefetched at the tile's start)
+    const T* G = (c.geom_g ? c.geom_g + 7 * c.gquad[el] : c.staged(1, el)) + b * Q + a;
     const T* lf = c.has_lam ? c.staged(2, el) + b * Q + a : nullptr;
     const T* kf = c.has_kap ? c.staged(3, el) + b * Q + a : nullptr;
     T lj[Q];
@@ -1256,6 +1258,7 @@ __global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KPar
   c.has_lam = p.lam_f != nullptr;
   c.has_kap = p.kap_f != nullptr;
   c.lam = static_cast<T>(p.lam);
+  c.geom_g = (OP == OP_HELM && p.geo_direct) ? p.geom : nullptr;
   for (int k = 0;; ++k) {
     const int ti = blockIdx.x + k * gridDim.x;
     if (ti >= p.n_tiles) break;
@@ -1301,6 +1304,11 @@ __global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KPar
       if constexpr (OP == OP_SENSOR) gquad[j] = e;   // its output is one value per element
     }
     __syncthreads();
+    if (OP == OP_HELM && DIM == 3 && p.geo_direct && tid == 0) {   // this tile's geometry into L2 while S1..S4 run
+      if (t.contig) prefetch_l2(p.geom + 7 * gquad[0], uint64_t(t.count) * 7 * Q * Q * Q * sizeof(T));
+      else
+        for (int j = 0; j < t.count; ++j) prefetch_l2(p.geom + 7 * gquad[j], uint64_t(7) * Q * Q * Q * sizeof(T));
+    }
     bool released = false;
     auto rel = [&]() {
       if (!released) {

@@ -49,8 +49,15 @@ struct SmemLayout {
 
 inline uint32_t up128(uint64_t x) { return static_cast<uint32_t>((x + 127) & ~uint64_t(127)); }
 
+// stages 0 selects, for the 3D Helmholtz bodies with Q^2 threads per element,
+// geometry read from L2 instead of staged (no geometry region) and one slot.
+inline bool geo_direct(const spx_plan* plan, int op, const LaunchCfg& cfg) {
+  return op == OP_HELM && plan->dim == 3 && plan->bkind != BK_GENERAL && cfg.stages == 0;
+}
+
 inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const LaunchCfg& cfg, bool lam_f, bool kap_f) {
   SmemLayout L{};
+  const bool direct = geo_direct(plan, op, cfg);
   uint64_t region[5] = {0, 0, 0, 0, 0};
   uint64_t work = 0;
   for (int P = 1; P <= kMaxP; ++P) {
@@ -59,6 +66,7 @@ inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const Launch
     const int eb = cfg.order[P].eb;
     int64_t lens[5];
     stream_lens(op, plan->dim, P, Q, lam_f, kap_f, lens);
+    if (direct) lens[1] = 0;
     for (int s = 0; s < 5; ++s)
       if (lens[s]) region[s] = std::max<uint64_t>(region[s], uint64_t(eb) * (((lens[s] * sz + 15) & ~int64_t(15)) + 16));
     const int S1 = Q | 1;
@@ -77,7 +85,7 @@ inline SmemLayout smem_layout(const spx_plan* plan, int op, int sz, const Launch
     off += up128(region[s]);
   }
   L.slot_bytes = static_cast<uint32_t>(off);
-  L.work_base = L.slot_base + cfg.stages * L.slot_bytes;
+  L.work_base = L.slot_base + (cfg.stages < 1 ? 1 : cfg.stages) * L.slot_bytes;
   L.work_bytes = up128(work);
   L.meta_base = L.work_base + n_work_buffers(op) * L.work_bytes;
   L.total = L.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8 + 16 + (op == OP_FWD || op == OP_SENSOR ? kFwdExtra * sz : 0);

@@ -1,4 +1,4 @@
-"""Collapsed-coordinate elements: triangles and prisms (FP64, numpy).
+"""Collapsed-coordinate elements: triangles, prisms and tetrahedra (FP64, numpy).
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
@@ -136,7 +136,7 @@ def tri_basis(P, e1, e2):
 
 
 def n_modes(shape, P):
-    return n_tri(P) if shape == TRI else (P + 1) * n_tri(P)
+    return {TRI: n_tri(P), PRISM: (P + 1) * n_tri(P), TET: n_tet(P)}[shape]
 
 
 def dim_of(shape):
@@ -155,6 +155,14 @@ def quadrature(shape, Q):
         w = (W1 * W2).ravel() * 0.5 * (1.0 - eta[:, 1])
         xi = np.stack([0.5 * (1.0 + eta[:, 0]) * (1.0 - eta[:, 1]) - 1.0, eta[:, 1]], axis=-1)
         return eta, xi, w
+    if shape == TET:
+        E3, E2, E1 = np.meshgrid(r, r, g, indexing="ij")
+        W3, W2, W1 = np.meshgrid(wr, wr, wg, indexing="ij")
+        eta = np.stack([E1.ravel(), E2.ravel(), E3.ravel()], axis=-1)
+        w = (W1 * W2 * W3).ravel() * 0.5 * (1.0 - eta[:, 1]) * (0.5 * (1.0 - eta[:, 2])) ** 2
+        xi = np.stack([0.25 * (1.0 + eta[:, 0]) * (1.0 - eta[:, 1]) * (1.0 - eta[:, 2]) - 1.0,
+                       0.5 * (1.0 + eta[:, 1]) * (1.0 - eta[:, 2]) - 1.0, eta[:, 2]], axis=-1)
+        return eta, xi, w
     E3, E2, E1 = np.meshgrid(r, g, g, indexing="ij")
     W3, W2, W1 = np.meshgrid(wr, wg, wg, indexing="ij")
     eta = np.stack([E1.ravel(), E2.ravel(), E3.ravel()], axis=-1)
@@ -163,8 +171,41 @@ def quadrature(shape, Q):
     return eta, xi, w
 
 
+def _deta_dxi(shape, eta):
+    """K[q, a, c] = d eta_a / d xi_c of the collapse at the points eta."""
+    npt = eta.shape[0]
+    d = 2 if shape == TRI else 3
+    K = np.zeros((npt, d, d))
+    if shape == TRI:
+        s = 1.0 / (1.0 - eta[:, 1])
+        K[:, 0, 0] = 2.0 * s
+        K[:, 0, 1] = (1.0 + eta[:, 0]) * s
+        K[:, 1, 1] = 1.0
+    elif shape == PRISM:
+        s = 1.0 / (1.0 - eta[:, 2])
+        K[:, 0, 0] = 1.0
+        K[:, 1, 1] = 2.0 * s
+        K[:, 1, 2] = (1.0 + eta[:, 1]) * s
+        K[:, 2, 2] = 1.0
+    else:
+        s23 = 1.0 / ((1.0 - eta[:, 1]) * (1.0 - eta[:, 2]))
+        s3 = 1.0 / (1.0 - eta[:, 2])
+        K[:, 0, 0] = 4.0 * s23
+        K[:, 0, 1] = 2.0 * (1.0 + eta[:, 0]) * s23
+        K[:, 0, 2] = 2.0 * (1.0 + eta[:, 0]) * s23
+        K[:, 1, 1] = 2.0 * s3
+        K[:, 1, 2] = (1.0 + eta[:, 1]) * s3
+        K[:, 2, 2] = 1.0
+    return K
+
+
 def basis_at(shape, P, eta):
     """Phi (npts, nm) and [d Phi / d xi_a] at collapsed points, by the chain rule of the collapse."""
+    if shape == TET:
+        Phi, d1, d2, d3 = tet_basis(P, eta)
+        K = _deta_dxi(TET, eta)
+        dEta = [d1, d2, d3]
+        return Phi, [sum(K[:, a, c][:, None] * dEta[a] for a in range(3)) for c in range(3)]
     if shape == TRI:
         T, T1, T2 = tri_basis(P, eta[:, 0], eta[:, 1])
         s = 1.0 / (1.0 - eta[:, 1])
@@ -257,26 +298,15 @@ def collocation_matrices(shape, Q):
     from .geometry import tensor_matrix
     if shape == TRI:
         return [tensor_matrix(2, [Dg, I]), tensor_matrix(2, [I, Dr])]
+    if shape == TET:
+        return [tensor_matrix(3, [Dg, I, I]), tensor_matrix(3, [I, Dr, I]), tensor_matrix(3, [I, I, Dr])]
     return [tensor_matrix(3, [Dg, I, I]), tensor_matrix(3, [I, Dg, I]), tensor_matrix(3, [I, I, Dr])]
 
 
 def deta_dx(mesh):
     """d eta_a / d x_m at the quadrature points: (E, nq, d, d), by the chain
     rule d eta / d xi (the collapse) times d xi / d x (the affine map)."""
-    eta = mesh.eta
-    npt, d = eta.shape
-    K = np.zeros((npt, d, d))               # K[q, a, c] = d eta_a / d xi_c
-    if mesh.shape == TRI:
-        s = 1.0 / (1.0 - eta[:, 1])
-        K[:, 0, 0] = 2.0 * s
-        K[:, 0, 1] = (1.0 + eta[:, 0]) * s
-        K[:, 1, 1] = 1.0
-    else:
-        s = 1.0 / (1.0 - eta[:, 2])
-        K[:, 0, 0] = 1.0
-        K[:, 1, 1] = 2.0 * s
-        K[:, 1, 2] = (1.0 + eta[:, 1]) * s
-        K[:, 2, 2] = 1.0
+    K = _deta_dxi(mesh.shape, mesh.eta)     # K[q, a, c] = d eta_a / d xi_c
     return np.einsum("qac,ecm->eqam", K, mesh.Jinv)
 
 
@@ -313,6 +343,113 @@ def structured_vertices(shape, N, skew, jitter=None):
             i, j, k = c
             out.append([node(i, j, k), node(i + 1, j, k), node(i, j + 1, k), node(i, j, k + 1)])
             out.append([node(i, j + 1, k + 1), node(i + 1, j + 1, k + 1), node(i, j, k + 1), node(i, j + 1, k)])
+    V = np.array(out)
+    if jitter is not None:
+        V = V + np.asarray(jitter).reshape(V.shape)
+    return V
+
+
+# ---------------------------------------------------------------------------
+# Tetrahedra: A = {xi in [-1,1]^3 | xi1 + xi2 + xi3 <= -1} (Table t:refregions),
+# collapsed by  xi1 = (1 + eta1)(1 - eta2)(1 - eta3)/4 - 1,
+#               xi2 = (1 + eta2)(1 - eta3)/2 - 1,  xi3 = eta3.
+# At height eta3 the cross-section is the triangle of (eta1, eta2) scaled by
+# (1 - eta3)/2, so a triangle mode T_m of degree k_m (in the triangle's own
+# coordinates) times ((1 - eta3)/2)^k_m is a polynomial of degree k_m on the
+# tetrahedron.  Modes, in storage order: for every triangle mode m (its own
+# storage order), r = 0..P - k_m:
+#     T_m(eta1, eta2) ((1 - eta3)/2)^k_m                        r = 0
+#     T_m(eta1, eta2) ((1 - eta3)/2)^k_m (1 + eta3)/2 P^{(2 k_m - 1, 1)}_{r-1}(eta3)   r >= 1
+# then the apex (xi = (-1, -1, 1)) mode (1 + eta3)/2.  k_m: 1 for the three
+# triangle vertices, p + 1 (bottom edge), q + 1 (side edges), p + q + 1
+# (interior).  (P+1)(P+2)(P+3)/6 modes.  Quadrature: GLL in eta1, Gauss-Radau
+# in eta2 and eta3, weights times (1 - eta2)/2 ((1 - eta3)/2)^2.
+# ---------------------------------------------------------------------------
+TET = "tet"
+
+
+def tri_degree(P, p, q):
+    """Polynomial degree of triangle mode (p, q) in the triangle's coordinates."""
+    if (p, q) in ((0, 0), (P, 0), (0, P)):
+        return 1
+    if p == 0 or p == P:
+        return q + 1
+    if q == 0:
+        return p + 1
+    return p + q + 1
+
+
+def n_tet(P):
+    return (P + 1) * (P + 2) * (P + 3) // 6
+
+
+def tet_modes(P):
+    """Storage order: list of (triangle mode index m, r), then ('apex', 0)."""
+    out = []
+    for m, (p, q) in enumerate(tri_modes(P)):
+        k = tri_degree(P, p, q)
+        out += [(m, r) for r in range(P - k + 1)]
+    out.append(("apex", 0))
+    return out
+
+
+def psi_c(k, r, z, deriv=False):
+    """((1-z)/2)^k (r = 0) or ((1-z)/2)^k (1+z)/2 P^{(2k-1,1)}_{r-1}(z), or its derivative."""
+    z = np.atleast_1d(np.asarray(z, dtype=np.float64))
+    L, R = 0.5 * (1.0 - z), 0.5 * (1.0 + z)
+    if r == 0:
+        return -0.5 * k * L ** (k - 1) if deriv else L ** k
+    J = basis.jacobi(r - 1, 2 * k - 1, 1, z)
+    dJ = basis.jacobi_deriv(r - 1, 2 * k - 1, 1, z)
+    if not deriv:
+        return L ** k * R * J
+    dLk = -0.5 * k * L ** (k - 1) if k > 0 else np.zeros_like(z)
+    return dLk * R * J + L ** k * 0.5 * J + L ** k * R * dJ
+
+
+def tet_basis(P, eta):
+    """Tetrahedron modes at collapsed points eta (npts, 3): values and d/d eta_a (a = 1, 2, 3)."""
+    T, T1, T2 = tri_basis(P, eta[:, 0], eta[:, 1])
+    z = eta[:, 2]
+    modes = tri_modes(P)
+    out = np.empty((eta.shape[0], n_tet(P)))
+    d1, d2, d3 = np.empty_like(out), np.empty_like(out), np.empty_like(out)
+    for c, (m, r) in enumerate(tet_modes(P)):
+        if m == "apex":
+            out[:, c] = 0.5 * (1.0 + z)
+            d1[:, c] = d2[:, c] = 0.0
+            d3[:, c] = 0.5
+            continue
+        k = tri_degree(P, *modes[m])
+        g, dg = psi_c(k, r, z), psi_c(k, r, z, deriv=True)
+        out[:, c] = T[:, m] * g
+        d1[:, c] = T1[:, m] * g
+        d2[:, c] = T2[:, m] * g
+        d3[:, c] = T[:, m] * dg
+    return out, d1, d2, d3
+
+
+def kuhn_vertices(N, skew, jitter=None):
+    """Affine tetrahedra of a skewed N^3 grid, six per cube (Kuhn split along the
+    main diagonal): for the permutation (a, b, c) of the axes, the tet
+    (n0, n0 + e_a, n0 + e_a + e_b, n0 + e_a + e_b + e_c), listed as defining
+    vertices V0..V3 with V1 and V2 swapped where needed for a positive
+    orientation.  Cube c = i + N(j + N k) holds elements 6c..6c+5 in the order
+    of the permutations (0,1,2), (0,2,1), (1,0,2), (1,2,0), (2,0,1), (2,1,0)."""
+    S = np.asarray(skew, dtype=np.float64)
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    E = np.eye(3)
+    out = []
+    for k in range(N):
+        for j in range(N):
+            for i in range(N):
+                n0 = np.array([i, j, k], dtype=np.float64)
+                for (a, b, c) in perms:
+                    v = [n0, n0 + E[a], n0 + E[a] + E[b], n0 + E[a] + E[b] + E[c]]
+                    v = [S @ (x / N) for x in v]
+                    if np.linalg.det(np.stack([v[1] - v[0], v[2] - v[0], v[3] - v[0]], -1)) < 0:
+                        v[1], v[2] = v[2], v[1]
+                    out.append(v)
     V = np.array(out)
     if jitter is not None:
         V = V + np.asarray(jitter).reshape(V.shape)

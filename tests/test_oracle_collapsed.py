@@ -230,3 +230,113 @@ def test_structured_elements_tile_the_skewed_cell_volume(shape):
     m = C.CollapsedMesh(shape, V, 2)
     assert np.all(m.detJ > 0)
     assert abs(m.JW.sum() - np.linalg.det(skew)) < 1e-13
+
+
+def _tet_points(n, seed):
+    rng = np.random.default_rng(seed)
+    s = rng.uniform(0.02, 0.98, (n, 3))
+    s = s[s.sum(1) < 0.98]
+    xi = 2.0 * s - 1.0                       # inside A: xi1 + xi2 + xi3 <= -1
+    return xi, _tet_eta(xi)
+
+
+def _tet_eta(xi):
+    e1 = 2.0 * (1.0 + xi[:, 0]) / (-xi[:, 1] - xi[:, 2]) - 1.0
+    e2 = 2.0 * (1.0 + xi[:, 1]) / (1.0 - xi[:, 2]) - 1.0
+    return np.stack([e1, e2, xi[:, 2]], -1)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 5, 8])
+def test_tet_basis_spans_total_degree_p(P):
+    xi, eta = _tet_points(2500, P)
+    Phi, _ = C.basis_at(C.TET, P, eta)
+    assert Phi.shape[1] == (P + 1) * (P + 2) * (P + 3) // 6
+    Mono = np.stack([xi[:, 0] ** a * xi[:, 1] ** b * xi[:, 2] ** c for a in range(P + 1)
+                     for b in range(P + 1 - a) for c in range(P + 1 - a - b)], axis=-1)
+    coef, *_ = np.linalg.lstsq(Mono, Phi, rcond=None)
+    assert np.abs(Mono @ coef - Phi).max() < 1e-9
+    assert np.linalg.matrix_rank(Phi, tol=1e-10) == Phi.shape[1]
+
+
+@pytest.mark.parametrize("P", [1, 3, 6])
+def test_tet_vertex_modes_are_barycentric(P):
+    xi, eta = _tet_points(200, 9)
+    Phi, _ = C.basis_at(C.TET, P, eta)
+    modes, tm = C.tet_modes(P), C.tri_modes(P)
+    col = lambda tri: modes.index((tm.index(tri), 0))
+    np.testing.assert_allclose(Phi[:, col((0, 0))], -(1 + xi.sum(1)) / 2, atol=1e-14)
+    np.testing.assert_allclose(Phi[:, col((P, 0))], (1 + xi[:, 0]) / 2, atol=1e-14)
+    np.testing.assert_allclose(Phi[:, col((0, P))], (1 + xi[:, 1]) / 2, atol=1e-14)
+    np.testing.assert_allclose(Phi[:, modes.index(("apex", 0))], (1 + xi[:, 2]) / 2, atol=1e-14)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_tet_derivatives_match_finite_differences(P):
+    xi, eta = _tet_points(300, 12)
+    _, dPhi = C.basis_at(C.TET, P, eta)
+    h = 1e-6
+    for a in range(3):
+        dx = np.zeros(3)
+        dx[a] = h
+        num = (C.basis_at(C.TET, P, _tet_eta(xi + dx))[0] - C.basis_at(C.TET, P, _tet_eta(xi - dx))[0]) / (2 * h)
+        np.testing.assert_allclose(dPhi[a], num, atol=2e-7)
+
+
+def _tet_monomial_integral(a, b, c):
+    """int over A of xi1^a xi2^b xi3^c: s = 1 + xi on the simplex s1 + s2 + s3 <= 2,
+    int s^i s^j s^k = 2^(i+j+k+3) i! j! k! / (i+j+k+3)!, in exact arithmetic."""
+    from fractions import Fraction
+    tot = Fraction(0)
+    for i in range(a + 1):
+        for j in range(b + 1):
+            for k in range(c + 1):
+                co = math.comb(a, i) * math.comb(b, j) * math.comb(c, k) * (-1) ** (a - i + b - j + c - k)
+                tot += co * Fraction(2 ** (i + j + k + 3) * math.factorial(i) * math.factorial(j) * math.factorial(k),
+                                     math.factorial(i + j + k + 3))
+    return float(tot)
+
+
+@pytest.mark.parametrize("P", [1, 3])
+def test_tet_quadrature_integrates_degree_2p(P):
+    _, xi, w = C.quadrature(C.TET, P + 2)
+    assert abs(w.sum() - 4.0 / 3.0) < 1e-14
+    for a in range(2 * P + 1):
+        for b in range(2 * P + 1 - a):
+            for c in range(2 * P + 1 - a - b):
+                got = np.sum(w * xi[:, 0] ** a * xi[:, 1] ** b * xi[:, 2] ** c)
+                assert abs(got - _tet_monomial_integral(a, b, c)) < 1e-13, (a, b, c)
+
+
+def test_p1_tet_mass_and_stiffness_closed_forms():
+    V = np.array([[[0.1, 0.0, 0.2], [1.2, 0.1, 0.0], [0.2, 0.9, 0.1], [0.0, 0.2, 1.1]]])
+    m = C.CollapsedMesh(C.TET, V, 1)
+    modes, tm = C.tet_modes(1), C.tri_modes(1)
+    order = [modes.index((tm.index((0, 0)), 0)), modes.index((tm.index((1, 0)), 0)),
+             modes.index((tm.index((0, 1)), 0)), modes.index(("apex", 0))]
+    M = m.mass_matrix(0)[np.ix_(order, order)]
+    L = m.helmholtz_matrix(0, 0.0, 1.0)[np.ix_(order, order)]
+    X = V[0]
+    vol = abs(np.linalg.det(np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]], -1))) / 6.0
+    np.testing.assert_allclose(M, vol / 20.0 * (np.ones((4, 4)) + np.eye(4)), atol=1e-14)
+    # linear stiffness: grad lambda_i are the rows of the inverse of [1 x y z]
+    A = np.hstack([np.ones((4, 1)), X])
+    G = np.linalg.inv(A)[1:, :]          # column i = grad of barycentric lambda_i
+    np.testing.assert_allclose(L, vol * G.T @ G, atol=1e-12)
+
+
+def test_tet_constants_volume_and_kuhn_mesh():
+    skew = np.array([[1.0, 0.2, 0.1], [0.0, 1.0, 0.15], [0.05, 0.0, 1.0]])
+    V = C.kuhn_vertices(2, skew)
+    m = C.CollapsedMesh(C.TET, V, 3)
+    assert np.all(m.detJ > 0)
+    assert abs(m.JW.sum() - np.linalg.det(skew)) < 1e-13
+    one = np.linalg.lstsq(m.Phi, np.ones(m.nq), rcond=None)[0]
+    for e in range(0, m.E, 7):
+        L = m.helmholtz_matrix(e, 0.0, 1.0)
+        H = m.helmholtz_matrix(e)
+        np.testing.assert_allclose(L @ one, 0.0, atol=1e-11)
+        np.testing.assert_allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+    X = m.xq()
+    grads = C.phys_deriv(m, X[:, :, 1].reshape(-1))
+    np.testing.assert_allclose(grads[1], 1.0, atol=1e-11)
+    np.testing.assert_allclose(grads[0], 0.0, atol=1e-11)

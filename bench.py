@@ -703,17 +703,21 @@ def collapsed_flops_per_elem(shape, P):
     if shape == "tri":
         bwd = nt * Q + n * Q * Q
         return 2 * (2 * bwd + 2 * 2 * Q ** 3) + 14 * Q ** 2
-    bwd = n * nt * Q + n * n * Q * Q + n * Q ** 3
+    if shape == "tet":
+        ntet = n * (n + 1) * (n + 2) // 6
+        bwd = ntet * Q + nt * Q * Q + n * Q ** 3
+    else:
+        bwd = n * nt * Q + n * n * Q * Q + n * Q ** 3
     return 2 * (2 * bwd + 6 * Q ** 4) + 20 * Q ** 3
 
 
 def measure_collapsed(spx, mesh, synth, torch, stream, hbm_peak, fp64_peak, fp32_peak):
     """Helmholtz on the collapsed-element workloads (affine prisms / triangles of a skewed grid)."""
     out = {}
-    for name in ("prism3d_24_p4", "tri2d_128_p4"):
+    for name in ("prism3d_24_p4", "tet3d_16_p4", "tri2d_128_p4"):
         w = synth.WORKLOADS[name]
         N, P, shape, d = w["N"], w["P"], w["shape"], w["dim"]
-        plan = spx.Plan(d, 2 * N ** d, order=P, shape=shape)
+        plan = spx.Plan(d, (6 if shape == "tet" else 2) * N ** d, order=P, shape=shape)
         g = spx.geom_factors(plan, mesh.collapsed_vertices(shape, N), want_xq=False)
         plan.set_geometry(torch.float64, g["geom"], g["dxi"])
         plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])

@@ -175,7 +175,14 @@ typedef enum { SPX_MEM_HOST = 0, SPX_MEM_DEVICE = 1 } spx_memory;
  *     spx_basis_tables, psi^b_pq = psi^a_q for p = 0, P, ((1-z)/2)^(p+1) for
  *     q = 0 and ((1-z)/2)^(p+1) (1+z)/2 P^(2p+1,1)_(q-1)(z) otherwise; the mode
  *     (0, P) is the collapsed vertex, the function (1 + eta2)/2;
- *   prism modes a + (P+1) m: psi^a_a(xi1) times triangle mode m in (eta2, eta3).
+ *   prism modes a + (P+1) m: psi^a_a(xi1) times triangle mode m in (eta2, eta3);
+ *   tetrahedra A = {xi in [-1,1]^3 | xi1 + xi2 + xi3 <= -1}: xi1 = (1 + eta1)
+ *     (1 - eta2)(1 - eta3)/4 - 1, xi2 = (1 + eta2)(1 - eta3)/2 - 1, xi3 = eta3;
+ *     for every triangle mode m (storage order) of degree k_m (1 vertices,
+ *     p + 1 bottom edge, q + 1 side edges, p + q + 1 interior), r = 0..P - k_m:
+ *     T_m(eta1, eta2) ((1 - eta3)/2)^k_m times 1 (r = 0) or (1 + eta3)/2
+ *     P^(2 k_m - 1, 1)_(r-1)(eta3), then the apex mode (1 + eta3)/2
+ *     ((P+1)(P+2)(P+3)/6 per element); Gauss-Radau in eta2 and eta3.
  * Quadrature: Q = P + 2 points per direction, GLL in the uncollapsed
  * directions, Gauss-Radau (spx_gauss_radau; it omits the collapsed vertex) in
  * the collapsed one; point index i + Q j (+ Q^2 k) over (eta1, eta2[, eta3]).
@@ -186,7 +193,7 @@ typedef enum { SPX_MEM_HOST = 0, SPX_MEM_DEVICE = 1 } spx_memory;
  * operators BwdTrans, IProductWRTBase, PhysDeriv, Helmholtz (constant or
  * per-point lambda, kappa) and Integral (others: SPX_ERR_UNSUPPORTED);
  * spx_geom_factors takes straight-sided (affine) elements by their vertices. */
-typedef enum { SPX_SHAPE_TENSOR = 0, SPX_SHAPE_TRI = 1, SPX_SHAPE_PRISM = 2 } spx_shape;
+typedef enum { SPX_SHAPE_TENSOR = 0, SPX_SHAPE_TRI = 1, SPX_SHAPE_PRISM = 2, SPX_SHAPE_TET = 3 } spx_shape;
 
 typedef struct {
   int dim;                    /* 2 or 3 */

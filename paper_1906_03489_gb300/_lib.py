@@ -39,7 +39,7 @@ class PlanDesc(C.Structure):
                 ("basis", C.POINTER(BasisDesc)), ("basis_memory", C.c_int), ("shape", C.c_int)]
 
 
-SPX_SHAPE_TENSOR, SPX_SHAPE_TRI, SPX_SHAPE_PRISM = 0, 1, 2
+SPX_SHAPE_TENSOR, SPX_SHAPE_TRI, SPX_SHAPE_PRISM, SPX_SHAPE_TET = 0, 1, 2, 3
 
 
 class CgOpts(C.Structure):

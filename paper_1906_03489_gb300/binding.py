@@ -9,7 +9,8 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import (SPX_F32, SPX_F64, SPX_MEM_DEVICE, SPX_MEM_HOST, SPX_SHAPE_PRISM, SPX_SHAPE_TENSOR, SPX_SHAPE_TRI,
+from ._lib import (SPX_F32, SPX_F64, SPX_MEM_DEVICE, SPX_MEM_HOST, SPX_SHAPE_PRISM, SPX_SHAPE_TENSOR, SPX_SHAPE_TET,
+                   SPX_SHAPE_TRI,
                    OPS, BasisDesc, CgOpts, CgResult, PlanDesc, SpxError, check, lib)
 
 __all__ = ["Plan", "basis_tables", "nodal_basis_tables", "gauss_radau", "geom_factors", "bwd_trans", "iproduct", "phys_deriv", "helmholtz", "fwd_trans",
@@ -97,7 +98,8 @@ class Plan:
         self.shape = shape
         desc = PlanDesc()
         desc.dim, desc.n_elem, desc.q_offset = self.dim, self.E, self.q_offset
-        desc.shape = {"tensor": SPX_SHAPE_TENSOR, "tri": SPX_SHAPE_TRI, "prism": SPX_SHAPE_PRISM}[shape]
+        desc.shape = {"tensor": SPX_SHAPE_TENSOR, "tri": SPX_SHAPE_TRI, "prism": SPX_SHAPE_PRISM,
+                      "tet": SPX_SHAPE_TET}[shape]
         keep = None
         if basis:
             arr, mem, keep = _basis_descs(basis, self.q_offset)

@@ -44,7 +44,7 @@ def units():
                           [f"-DSPX_TN={tn}", f"-DSPX_DIM={dim}", f"-DSPX_OP={op}"]))
         for bk in (1, 2):   # 3D Helmholtz of the other basis kinds
             u.append((f"ops_{tn}_helm3_bk{bk}", "ops_inst.cu", [f"-DSPX_TN={tn}", f"-DSPX_BK={bk}"]))
-        for cs in (1, 2):   # triangles, prisms
+        for cs in (1, 2, 3):   # triangles, prisms, tetrahedra
             u.append((f"collapsed_{tn}_{cs}", "collapsed.cu", [f"-DSPX_CT={tn}", f"-DSPX_CS={cs}"]))
     u.append(("collapsed_geom", "collapsed.cu", ["-DSPX_CGEOM"]))
     return u

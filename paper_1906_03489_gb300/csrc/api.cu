@@ -250,11 +250,12 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
     return fail(SPX_ERR_INVALID_ARG, "plan_create: n_elem out of range");
   const int qoff = d->q_offset == 0 ? 2 : d->q_offset;
   if (qoff != 1 && qoff != 2) return fail(SPX_ERR_UNSUPPORTED, "plan_create: q_offset must be 1 or 2");
-  if (d->shape != SPX_SHAPE_TENSOR && d->shape != SPX_SHAPE_TRI && d->shape != SPX_SHAPE_PRISM)
+  if (d->shape != SPX_SHAPE_TENSOR && d->shape != SPX_SHAPE_TRI && d->shape != SPX_SHAPE_PRISM &&
+      d->shape != SPX_SHAPE_TET)
     return fail(SPX_ERR_INVALID_ARG, "plan_create: unknown element shape");
   if (d->shape != SPX_SHAPE_TENSOR) {
     if ((d->shape == SPX_SHAPE_TRI) != (d->dim == 2))
-      return fail(SPX_ERR_INVALID_ARG, "plan_create: triangles are 2D, prisms 3D");
+      return fail(SPX_ERR_INVALID_ARG, "plan_create: triangles are 2D, prisms and tetrahedra 3D");
     if (d->elem_order || qoff != 2 || d->n_basis)
       return fail(SPX_ERR_UNSUPPORTED, "plan_create: triangles / prisms take a uniform order, q_offset 2 and the "
                                        "library's basis");
@@ -294,16 +295,19 @@ spx_status spx_plan_create(spx_plan** out, const spx_plan_desc* d) {
   for (int64_t e = 0; e < p->E; ++e) {
     const int64_t n = p->orders[e] + 1, Q = p->orders[e] + qoff;
     const int64_t nt = n * (n + 1) / 2;   // triangle modes
-    const int64_t nm = p->shape == SPX_SHAPE_TRI ? nt : (p->shape == SPX_SHAPE_PRISM ? n * nt : (p->dim == 3 ? n * n * n : n * n));
+    const int64_t nm = p->shape == SPX_SHAPE_TRI     ? nt
+                       : p->shape == SPX_SHAPE_PRISM ? n * nt
+                       : p->shape == SPX_SHAPE_TET   ? n * (n + 1) * (n + 2) / 6
+                                                     : (p->dim == 3 ? n * n * n : n * n);
     p->coef_off[e + 1] = p->coef_off[e] + nm;
     p->quad_off[e + 1] = p->quad_off[e] + (p->dim == 3 ? Q * Q * Q : Q * Q);
   }
-  if (p->shape) {   // tables of the collapsed kernels: B1[Q][n], Bb[n][Q][n], D1[Q][Q], D2[Q][Q]
+  if (p->shape) {   // tables of the collapsed kernels: B1[Q][n], Bb[n][Q][n], D1[Q][Q], D2[Q][Q], Bc[n][Q][n]
     const int P = p->uP, n = P + 1, Q = P + 2;
-    p->ctab.assign(Q * n + n * Q * n + 2 * Q * Q, 0.0);
+    p->ctab.assign(Q * n + 2 * n * Q * n + 2 * Q * Q, 0.0);
     double* t = p->ctab.data();
     const spx_status cs = collapsed_tables(P, Q, t, t + Q * n, t + Q * n + n * Q * n, t + Q * n + n * Q * n + Q * Q,
-                                           nullptr, nullptr, nullptr, nullptr);
+                                           nullptr, nullptr, nullptr, nullptr, t + Q * n + n * Q * n + 2 * Q * Q);
     if (cs != SPX_OK) {
       delete p;
       return cs;

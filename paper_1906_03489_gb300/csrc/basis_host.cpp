@@ -211,9 +211,12 @@ spx_status gauss_radau(int Q, double* x, double* w) {
 //                ((1-z)/2)^(p+1) (1+z)/2 P^{(2p+1,1)}_{q-1}(z) for 0 < q < P - p),
 //                zero elsewhere;
 //   D1[Q][Q], D2[Q][Q]  collocation derivatives on the GLL / Gauss-Radau points;
-//   xg, wg, xr, wr      the two point sets and their weights.
+//   xg, wg, xr, wr      the two point sets and their weights;
+//   Bc[n][Q][n]  tetrahedra: ((1-z)/2)^k (r = 0) and ((1-z)/2)^k (1+z)/2
+//                P^{(2k-1,1)}_{r-1}(z) (0 < r <= P - k) at the Gauss-Radau
+//                points, [k][k3][r] for k = 1..P; [0][k3][0] = (1+z)/2 (apex).
 spx_status collapsed_tables(int P, int Q, double* B1, double* Bb, double* D1, double* D2, double* xg, double* wg,
-                            double* xr, double* wr) {
+                            double* xr, double* wr, double* Bc) {
   if (P < 1 || P > 8 || Q < P + 1 || Q > 16) return fail(SPX_ERR_INVALID_ARG, "collapsed tables: bad P or Q");
   std::vector<double> g, gw, r(Q), rw(Q);
   gll_points(Q, g, gw);
@@ -247,6 +250,18 @@ spx_status collapsed_tables(int P, int Q, double* B1, double* Bb, double* D1, do
             Bb[(p * Q + k) * n + q] = q == 0 ? Lp : Lp * R * jacobi_ab(q - 1, 2.0 * p + 1.0, 1.0, z);
         }
       }
+  }
+  if (Bc) {   // tetrahedra: [k][k3][r], k = 1..P, r <= P - k; [0][k3][0] = (1 + z)/2 (apex)
+    std::fill(Bc, Bc + n * Q * n, 0.0);
+    for (int k3 = 0; k3 < Q; ++k3) {
+      const double z = r[k3], L = 0.5 * (1.0 - z), R = 0.5 * (1.0 + z);
+      Bc[k3 * n] = R;
+      for (int k = 1; k <= P; ++k) {
+        const double Lk = std::pow(L, k);
+        for (int rr = 0; rr <= P - k; ++rr)
+          Bc[(k * Q + k3) * n + rr] = rr == 0 ? Lk : Lk * R * jacobi_ab(rr - 1, 2.0 * k - 1.0, 1.0, z);
+      }
+    }
   }
   if (D1) collocation(g, D1);
   if (D2) collocation(r, D2);

@@ -1,4 +1,4 @@
-// Collapsed-coordinate elements: triangles (2D) and prisms (3D), §2.1
+// Collapsed-coordinate elements: triangles (2D), prisms and tetrahedra (3D), §2.1
 // (Fig. f:duffy: the Duffy map from the square / cube onto the reference
 // shape, Table t:refregions) with the sum-factorisation of §3.3.
 //
@@ -10,6 +10,11 @@
 //   triangle  u(eta1_i, eta2_j) = sum_p psi^a_p(eta1_i) sum_q c_{pq} psi^b_{pq}(eta2_j)
 //   prism     u(xi1_i, eta2_j, eta3_k) = sum_a psi^a_a(xi1_i) sum_p psi^a_p(eta2_j)
 //                                         sum_q c_{a,pq} psi^b_{pq}(eta3_k)
+//   tetrahedron  u(eta1_i, eta2_j, eta3_k) = sum_p psi^a_p(eta1_i) sum_q psi^b_{pq}(eta2_j)
+//                sum_r c_{(pq),r} psi^c_{k(pq),r}(eta3_k)  (+ the apex (1 + eta3)/2):
+//                the eta3 factor of triangle mode m of degree k_m is
+//                ((1-z)/2)^k_m times 1 or (1+z)/2 P^{(2k_m-1,1)}_{r-1}(z), r <= P - k_m,
+//                and both eta2 and eta3 use Gauss-Radau points
 // Mode (p, q) = (0, P) is the collapsed vertex: its function (1 + z)/2 equals
 // psi^a_0 psi^a_P + psi^a_P psi^a_P, so its coefficient also enters the
 // p = P row of the collapsed-direction contraction (and, transposed, its
@@ -34,7 +39,7 @@
 namespace spx {
 namespace {
 
-constexpr int kTri = 1, kPrism = 2;
+constexpr int kTri = 1, kPrism = 2, kTet = 3;
 
 template <int P>
 struct Tri {
@@ -48,11 +53,14 @@ struct Tri {
 
 template <typename T, int P>
 struct CParams {
-  static constexpr int n = P + 1, Q = P + 2;
+  static constexpr int n = P + 1, Q = P + 2, nt = (P + 1) * (P + 2) / 2;
   T B1[Q * n];       // psi^a at the GLL points, [i][p]
   T Bb[n * Q * n];   // psi^b_{pq} at the Radau points, [p][k][q]
+  T Bc[n * Q * n];   // tetrahedra: psi^c_{k,r} at the Radau points, [k][k3][r]; [0][k3][0] = (1 + z)/2 (apex)
   T D1[Q * Q];       // collocation derivative, GLL points
   T D2[Q * Q];       // collocation derivative, Radau points
+  short toff[nt + 1];  // tetrahedra: first mode of triangle mode m (r = 0) and the apex at toff[nt]
+  short tdeg[nt];      // tetrahedra: degree k_m of triangle mode m
   const Tile* tiles;
   int n_tiles;
   int eb;            // elements per tile (buffer stride)
@@ -69,27 +77,34 @@ struct CParams {
 // shared-memory carve-up per element (values of T)
 template <int SHAPE, int P>
 struct CLayout {
-  static_assert(SHAPE == kTri || SHAPE == kPrism, "triangles and prisms");
+  static_assert(SHAPE == kTri || SHAPE == kPrism || SHAPE == kTet, "triangles, prisms and tetrahedra");
   static constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
   static constexpr int NQ = SHAPE == kTri ? Q * Q : Q * Q * Q;    // quadrature points
-  static constexpr int NM = SHAPE == kTri ? nt : n * nt;         // modes
-  static constexpr int NF = SHAPE == kTri ? n * Q : n * n * Q;   // after the collapsed-direction stage
-  static constexpr int NH = SHAPE == kTri ? 0 : n * Q * Q;       // prism: after the second stage
+  static constexpr int NM = SHAPE == kTri ? nt : (SHAPE == kPrism ? n * nt : (P + 1) * (P + 2) * (P + 3) / 6);
+  // after the first (collapsed-direction) stage: tri [p][k], prism [a][p][k], tet [m][k3]
+  static constexpr int NF = SHAPE == kTri ? n * Q : (SHAPE == kPrism ? n * n * Q : nt * Q);
+  static constexpr int NH = SHAPE == kTri ? 0 : n * Q * Q;       // after the second stage
   // buffers: C (modes), F, H, U, G0, G1, G2, V
   static constexpr int per_elem = NM + NF + NH + 5 * NQ;
-  static constexpr int tables = Q * n + n * Q * n + 2 * Q * Q;
+  // tables: B1, Bb, Bc, D1, D2 (values of T), then the tet mode tables (ints, rounded up)
+  static constexpr int tables = Q * n + 2 * n * Q * n + 2 * Q * Q + (2 * nt + 2);
 };
 
 template <typename T, int SHAPE, int P>
 struct Bufs {
   using L = CLayout<SHAPE, P>;
-  T *B1, *Bb, *D1, *D2, *C, *F, *H, *U, *G0, *G1, *G2, *V;
+  T *B1, *Bb, *Bc, *D1, *D2, *C, *F, *H, *U, *G0, *G1, *G2, *V;
+  int* toff;   // [nt + 1]
+  int* tdeg;   // [nt]
   __device__ Bufs(T* sm, int eb) {
     B1 = sm;
     Bb = B1 + L::Q * L::n;
-    D1 = Bb + L::n * L::Q * L::n;
+    Bc = Bb + L::n * L::Q * L::n;
+    D1 = Bc + L::n * L::Q * L::n;
     D2 = D1 + L::Q * L::Q;
-    C = D2 + L::Q * L::Q;
+    toff = reinterpret_cast<int*>(D2 + L::Q * L::Q);
+    tdeg = toff + L::nt + 1;
+    C = D2 + L::Q * L::Q + (2 * L::nt + 2);
     F = C + eb * L::NM;
     H = F + eb * L::NF;
     U = H + eb * L::NH;
@@ -150,6 +165,101 @@ __device__ __forceinline__ void stage_b_bwd(const T* F, T* out, int64_t e_base, 
   }
 }
 
+// ---- tetrahedra: the eta3 stage over the triangle modes ---------------------
+// forward: F[e][m][k3] = sum_r C[e][toff[m] + r] Bc[k_m][k3][r]
+//          (+ the apex coefficient for the three triangle vertex modes, whose sum is 1)
+template <typename T, int P>
+__device__ __forceinline__ void stage_c_fwd(const T* C, T* F, const T* Bc, const int* toff, const int* tdeg, int ne,
+                                            int tid, int nthr) {
+  constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm, NM = (P + 1) * (P + 2) * (P + 3) / 6;
+  constexpr int items = nt * Q;
+  for (int w = tid; w < ne * items; w += nthr) {
+    const int e = w / items, r0 = w - e * items;
+    const int m = r0 % nt, k3 = r0 / nt;
+    const int k = tdeg[m], o = toff[m];
+    const T* c = C + e * NM;
+    const T* b = Bc + (k * Q + k3) * n;
+    T acc = T(0);
+#pragma unroll
+    for (int r = 0; r < n; ++r)
+      if (r <= P - k) acc = fma(c[o + r], b[r], acc);
+    if (m == 0 || m == P || m == Tri<P>::off(P)) acc = fma(c[NM - 1], Bc[k3 * n], acc);   // apex
+    F[e * nt * Q + m + nt * k3] = acc;
+  }
+}
+
+// forward, eta2: H[e][p][j][k3] = sum_q F[e][(p, q)][k3] Bb[p][j][q] (+ row P for the triangle's collapsed vertex)
+template <typename T, int P>
+__device__ __forceinline__ void stage_tb_fwd(const T* F, T* H, const T* Bb, int ne, int tid, int nthr) {
+  constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
+  constexpr int items = n * Q * Q;
+  for (int w = tid; w < ne * items; w += nthr) {
+    const int e = w / items, r0 = w - e * items;
+    const int p = r0 % n, j = (r0 / n) % Q, k3 = r0 / (n * Q);
+    const T* f = F + e * nt * Q + nt * k3;
+    const T* b = Bb + (p * Q + j) * n;
+    const int o = Tri<P>::off(p), mc = Tri<P>::cnt(p);
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < n; ++q)
+      if (q < mc) acc = fma(f[o + q], b[q], acc);
+    if (p == P) acc = fma(f[P], Bb[j * n + P], acc);
+    H[e * n * Q * Q + r0] = acc;
+  }
+}
+
+// transposed, eta2: F[e][(p, q)][k3] = sum_j Bb[p][j][q] H[e][p][j][k3] (+ row P into (0, P))
+template <typename T, int P>
+__device__ __forceinline__ void stage_tb_bwd(const T* H, T* F, const T* Bb, int ne, int tid, int nthr) {
+  constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
+  constexpr int items = nt * Q;
+  for (int w = tid; w < ne * items; w += nthr) {
+    const int e = w / items, r0 = w - e * items;
+    const int mi = r0 % nt, k3 = r0 / nt;
+    int p = 0;
+#pragma unroll
+    for (int pp = 1; pp <= P; ++pp)
+      if (mi >= Tri<P>::off(pp)) p = pp;
+    const int q = mi - Tri<P>::off(p);
+    const T* h = H + e * n * Q * Q + p + n * Q * k3;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) acc = fma(Bb[(p * Q + j) * n + q], h[n * j], acc);
+    if (p == 0 && q == P) {
+      const T* hP = H + e * n * Q * Q + P + n * Q * k3;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) acc = fma(Bb[j * n + P], hP[n * j], acc);
+    }
+    F[e * nt * Q + mi + nt * k3] = acc;
+  }
+}
+
+// transposed, eta3: out[e][toff[m] + r] = sum_k3 Bc[k_m][k3][r] F[e][m][k3]; the apex
+// collects the three triangle vertex modes against (1 + z)/2
+template <typename T, int P>
+__device__ __forceinline__ void stage_c_bwd(const T* F, T* out, int64_t e_base, const T* Bc, const int* toff,
+                                            const int* tdeg, int ne, int tid, int nthr) {
+  constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm, NM = (P + 1) * (P + 2) * (P + 3) / 6;
+  for (int w = tid; w < ne * NM; w += nthr) {
+    const int e = w / NM, mi = w - e * NM;
+    const T* f = F + e * nt * Q;
+    T acc = T(0);
+    if (mi == NM - 1) {
+      const int v1 = P, v2 = Tri<P>::off(P);
+#pragma unroll
+      for (int k3 = 0; k3 < Q; ++k3) acc = fma(Bc[k3 * n], f[nt * k3] + f[v1 + nt * k3] + f[v2 + nt * k3], acc);
+    } else {
+      int m = 0;
+      for (int mm = 1; mm < nt; ++mm)
+        if (mi >= toff[mm]) m = mm;
+      const int r = mi - toff[m], k = tdeg[m];
+#pragma unroll
+      for (int k3 = 0; k3 < Q; ++k3) acc = fma(Bc[(k * Q + k3) * n + r], f[m + nt * k3], acc);
+    }
+    out[(e_base + e) * NM + mi] = acc;
+  }
+}
+
 // ---- dense 1D stages on the tensor part ------------------------------------
 // y[e][.. i along axis ..] = sum_c A[i][c] x[e][.. c ..] (TR: A[c][i]); extents
 // (N0, N1, N2) in and the same with axis AX resized to M out, axis 0 fastest.
@@ -194,11 +304,16 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
   Bufs<T, SHAPE, P> b(reinterpret_cast<T*>(csm), p.eb);
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int i = tid; i < Q * n; i += nthr) b.B1[i] = p.B1[i];
-  for (int i = tid; i < n * Q * n; i += nthr) b.Bb[i] = p.Bb[i];
+  for (int i = tid; i < n * Q * n; i += nthr) {
+    b.Bb[i] = p.Bb[i];
+    b.Bc[i] = p.Bc[i];
+  }
   for (int i = tid; i < Q * Q; i += nthr) {
     b.D1[i] = p.D1[i];
     b.D2[i] = p.D2[i];
   }
+  for (int i = tid; i <= nt; i += nthr) b.toff[i] = p.toff[i];
+  for (int i = tid; i < nt; i += nthr) b.tdeg[i] = p.tdeg[i];
   __syncthreads();
   for (int ti = blockIdx.x; ti < p.n_tiles; ti += gridDim.x) {
     const Tile t = p.tiles[ti];
@@ -214,6 +329,12 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
         stage_b_fwd<T, P, 1>(b.C, b.F, b.Bb, ne, tid, nthr);
         __syncthreads();
         stage_dense<0, n, Q, 1, Q, false, false>(b.F, dst, b.B1, ne, tid, nthr, NQ, dbase);   // F[p][j] -> u[i][j]
+      } else if constexpr (SHAPE == kTet) {
+        stage_c_fwd<T, P>(b.C, b.F, b.Bc, b.toff, b.tdeg, ne, tid, nthr);                     // F[m][k3]
+        __syncthreads();
+        stage_tb_fwd<T, P>(b.F, b.H, b.Bb, ne, tid, nthr);                                     // H[p][j][k3]
+        __syncthreads();
+        stage_dense<0, n, Q, Q, Q, false, false>(b.H, dst, b.B1, ne, tid, nthr, NQ, dbase);   // u[i][j][k3]
       } else {
         stage_b_fwd<T, P, n>(b.C, b.F, b.Bb, ne, tid, nthr);                                 // F[a][p][k]
         __syncthreads();
@@ -231,9 +352,9 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
       if constexpr (SHAPE == kTri) {
         stage_dense<0, Q, Q, 1, Q, false, false>(b.U, b.G0, b.D1, ne, tid, nthr, NQ, 0);
         stage_dense<1, Q, Q, 1, Q, false, false>(b.U, b.G1, b.D2, ne, tid, nthr, NQ, 0);
-      } else {
+      } else {   // eta2 on GLL points (prism) or Gauss-Radau points (tetrahedron)
         stage_dense<0, Q, Q, Q, Q, false, false>(b.U, b.G0, b.D1, ne, tid, nthr, NQ, 0);
-        stage_dense<1, Q, Q, Q, Q, false, false>(b.U, b.G1, b.D1, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, Q, Q, false, false>(b.U, b.G1, SHAPE == kTet ? b.D2 : b.D1, ne, tid, nthr, NQ, 0);
         stage_dense<2, Q, Q, Q, Q, false, false>(b.U, b.G2, b.D2, ne, tid, nthr, NQ, 0);
       }
       __syncthreads();
@@ -290,7 +411,7 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
       } else {
         stage_dense<0, Q, Q, Q, Q, true, true>(b.G0, b.V, b.D1, ne, tid, nthr, NQ, 0);
         __syncthreads();
-        stage_dense<1, Q, Q, Q, Q, true, true>(b.G1, b.V, b.D1, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, Q, Q, true, true>(b.G1, b.V, SHAPE == kTet ? b.D2 : b.D1, ne, tid, nthr, NQ, 0);
         __syncthreads();
         stage_dense<2, Q, Q, Q, Q, true, true>(b.G2, b.V, b.D2, ne, tid, nthr, NQ, 0);
       }
@@ -309,6 +430,12 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
         stage_dense<0, Q, Q, 1, n, true, false>(b.V, b.F, b.B1, ne, tid, nthr, n * Q, 0);   // F[p][k]
         __syncthreads();
         stage_b_bwd<T, P, 1>(b.F, p.out0, e0, b.Bb, ne, tid, nthr);
+      } else if constexpr (SHAPE == kTet) {
+        stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, b.B1, ne, tid, nthr, n * Q * Q, 0);  // H[p][j][k3]
+        __syncthreads();
+        stage_tb_bwd<T, P>(b.H, b.F, b.Bb, ne, tid, nthr);                                    // F[m][k3]
+        __syncthreads();
+        stage_c_bwd<T, P>(b.F, p.out0, e0, b.Bc, b.toff, b.tdeg, ne, tid, nthr);
       } else {
         stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, b.B1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
         __syncthreads();
@@ -348,12 +475,29 @@ spx_status launch_c(const LaunchReq& r) {
   if (tl.n == 0) return SPX_OK;
   Prm prm{};
   constexpr int n = P + 1, Q = P + 2;
-  const std::vector<double>& ct = plan->ctab;   // B1, Bb, D1, D2 (FP64)
+  const std::vector<double>& ct = plan->ctab;   // B1, Bb, D1, D2, Bc (FP64)
   int o = 0;
   for (int i = 0; i < Q * n; ++i) prm.B1[i] = static_cast<T>(ct[o++]);
   for (int i = 0; i < n * Q * n; ++i) prm.Bb[i] = static_cast<T>(ct[o++]);
   for (int i = 0; i < Q * Q; ++i) prm.D1[i] = static_cast<T>(ct[o++]);
   for (int i = 0; i < Q * Q; ++i) prm.D2[i] = static_cast<T>(ct[o++]);
+  for (int i = 0; i < n * Q * n; ++i) prm.Bc[i] = static_cast<T>(ct[o++]);
+  // tetrahedra: first mode and degree of every triangle mode (storage order p outer, q inner)
+  constexpr int nt = (P + 1) * (P + 2) / 2;
+  int m = 0, acc = 0;
+  for (int pp = 0; pp <= P; ++pp) {
+    const int cnt = pp == 0 ? P + 1 : (pp == P ? P : P - pp);
+    for (int q = 0; q < cnt; ++q, ++m) {
+      int k;
+      if ((pp == 0 && (q == 0 || q == P)) || (pp == P && q == 0)) k = 1;
+      else if (pp == 0 || pp == P) k = q + 1;
+      else k = q == 0 ? pp + 1 : pp + q + 1;
+      prm.tdeg[m] = static_cast<short>(k);
+      prm.toff[m] = static_cast<short>(acc);
+      acc += P - k + 1;
+    }
+  }
+  prm.toff[nt] = static_cast<short>(acc);   // the apex
   prm.tiles = tl.d;
   prm.n_tiles = tl.n;
   prm.eb = cfg.order[P].eb;
@@ -439,6 +583,7 @@ size_t collapsed_smem_bytes(const spx_plan* plan, int dtype, int eb) {
   case S * 16 + Pv: return dtype == 0 ? collapsed_smem_t<double, S, Pv>(eb) : collapsed_smem_t<float, S, Pv>(eb);
     SPX_CSM(1, 1) SPX_CSM(1, 2) SPX_CSM(1, 3) SPX_CSM(1, 4) SPX_CSM(1, 5) SPX_CSM(1, 6) SPX_CSM(1, 7) SPX_CSM(1, 8)
     SPX_CSM(2, 1) SPX_CSM(2, 2) SPX_CSM(2, 3) SPX_CSM(2, 4) SPX_CSM(2, 5) SPX_CSM(2, 6) SPX_CSM(2, 7) SPX_CSM(2, 8)
+    SPX_CSM(3, 1) SPX_CSM(3, 2) SPX_CSM(3, 3) SPX_CSM(3, 4) SPX_CSM(3, 5) SPX_CSM(3, 6) SPX_CSM(3, 7) SPX_CSM(3, 8)
 #undef SPX_CSM
     default: return SIZE_MAX;
   }
@@ -446,13 +591,16 @@ size_t collapsed_smem_bytes(const spx_plan* plan, int dtype, int eb) {
 
 spx_status launch_collapsed_f64_1(const LaunchReq& r);
 spx_status launch_collapsed_f64_2(const LaunchReq& r);
+spx_status launch_collapsed_f64_3(const LaunchReq& r);
 spx_status launch_collapsed_f32_1(const LaunchReq& r);
 spx_status launch_collapsed_f32_2(const LaunchReq& r);
+spx_status launch_collapsed_f32_3(const LaunchReq& r);
 
 spx_status launch_collapsed(const LaunchReq& r) {
-  const bool tri = r.plan->shape == kTri;
-  if (r.dtype == 0) return tri ? launch_collapsed_f64_1(r) : launch_collapsed_f64_2(r);
-  return tri ? launch_collapsed_f32_1(r) : launch_collapsed_f32_2(r);
+  const int sh = r.plan->shape;
+  if (r.dtype == 0) return sh == kTri ? launch_collapsed_f64_1(r) : (sh == kPrism ? launch_collapsed_f64_2(r)
+                                                                                  : launch_collapsed_f64_3(r));
+  return sh == kTri ? launch_collapsed_f32_1(r) : (sh == kPrism ? launch_collapsed_f32_2(r) : launch_collapsed_f32_3(r));
 }
 
 // ---- geometric factors of affine collapsed elements (FP64) ------------------
@@ -468,6 +616,7 @@ struct CGeomParams {
   float* dxi32;
   int64_t E;
   int d, Q;
+  int tet;                 // 3D: tetrahedra (else prisms)
   double xg[16], wg[16], xr[16], wr[16];
 };
 
@@ -512,6 +661,23 @@ __global__ void collapsed_geom_kernel(const __grid_constant__ CGeomParams g) {
       K[0][1] = (1.0 + eta[0]) * s;
       K[1][1] = 1.0;
       wt = g.wg[i] * g.wr[j] * 0.5 * (1.0 - eta[1]);
+    } else if (g.tet) {
+      const int i = q % Q, j = (q / Q) % Q, k = q / (Q * Q);
+      eta[0] = g.xg[i];
+      eta[1] = g.xr[j];
+      eta[2] = g.xr[k];
+      const double s23 = 1.0 / ((1.0 - eta[1]) * (1.0 - eta[2])), s3 = 1.0 / (1.0 - eta[2]);
+      xi[0] = 0.25 * (1.0 + eta[0]) * (1.0 - eta[1]) * (1.0 - eta[2]) - 1.0;
+      xi[1] = 0.5 * (1.0 + eta[1]) * (1.0 - eta[2]) - 1.0;
+      xi[2] = eta[2];
+      K[0][0] = 4.0 * s23;
+      K[0][1] = 2.0 * (1.0 + eta[0]) * s23;
+      K[0][2] = 2.0 * (1.0 + eta[0]) * s23;
+      K[1][1] = 2.0 * s3;
+      K[1][2] = (1.0 + eta[1]) * s3;
+      K[2][2] = 1.0;
+      const double h3 = 0.5 * (1.0 - eta[2]);
+      wt = g.wg[i] * g.wr[j] * g.wr[k] * 0.5 * (1.0 - eta[1]) * h3 * h3;
     } else {
       const int i = q % Q, j = (q / Q) % Q, k = q / (Q * Q);
       eta[0] = g.xg[i];
@@ -579,6 +745,7 @@ spx_status collapsed_geom(const spx_plan* plan, const double* verts, double* geo
   g.E = plan->E;
   g.d = plan->dim;
   g.Q = plan->uP + 2;
+  g.tet = plan->shape == kTet ? 1 : 0;
   spx_status s = collapsed_tables(plan->uP, g.Q, nullptr, nullptr, nullptr, nullptr, g.xg, g.wg, g.xr, g.wr);
   if (s != SPX_OK) return s;
   const int64_t total = plan->E * (plan->dim == 2 ? g.Q * g.Q : g.Q * g.Q * g.Q);

@@ -145,7 +145,7 @@ spx_status basis_tables(int P, int Q, double* xi, double* w, double* B, double* 
 spx_status gauss_radau(int Q, double* x, double* w);
 // Tables of the collapsed-coordinate kernels (basis_host.cpp).
 spx_status collapsed_tables(int P, int Q, double* B1, double* Bb, double* D1, double* D2, double* xg, double* wg,
-                            double* xr, double* wr);
+                            double* xr, double* wr, double* Bc = nullptr);
 
 // Nodal (Lagrange through the P + 1 GLL points) basis at the Q GLL points.
 spx_status nodal_basis_tables(int P, int Q, double* B, double* dB);

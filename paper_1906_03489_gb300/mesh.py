@@ -68,8 +68,9 @@ def periodic_l2g(dim, N, P, device="cuda"):
 
 
 def collapsed_vertices(shape, N, jitter=None, device="cuda"):
-    """Defining vertices V0..Vd of affine triangles ("tri", 2 N^2) or prisms
-    ("prism", 2 N^3): FP64 tensor (E, d+1, d) in the library's vertex layout.
+    """Defining vertices V0..Vd of affine triangles ("tri", 2 N^2), prisms
+    ("prism", 2 N^3) or tetrahedra ("tet", 6 N^3, the Kuhn split of every cube
+    along its main diagonal): FP64 tensor (E, d+1, d), the library's vertex layout.
 
     Grid nodes (i, j[, k]) / N pass through the skew synth.SKEW2 / SKEW3.  Each
     square (cube) holds two elements, element 2 c + t for cell c = ex + N(ey
@@ -95,8 +96,29 @@ def collapsed_vertices(shape, N, jitter=None, device="cuda"):
         node = lambda a, b, c: (np.stack([a, b, c], -1) * h) @ S.T
         lo = np.stack([node(i, j, k), node(i + 1, j, k), node(i, j + 1, k), node(i, j, k + 1)], 1)
         up = np.stack([node(i, j + 1, k + 1), node(i + 1, j + 1, k + 1), node(i, j, k + 1), node(i, j + 1, k)], 1)
+    elif shape == "tet":
+        # six tetrahedra per cube along its main diagonal: for the axis order
+        # (a, b, c), n0, n0 + e_a, n0 + e_a + e_b, n0 + e_a + e_b + e_c; the
+        # second and third vertex swapped where that gives a positive volume
+        S = np.array(synth.SKEW3)
+        ez, ey, ex = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+        n0 = np.stack([ex.ravel(), ey.ravel(), ez.ravel()], -1).astype(np.float64)
+        E3 = np.eye(3)
+        tets = []
+        for a, b, c in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+            v = [n0, n0 + E3[a], n0 + E3[a] + E3[b], n0 + E3[a] + E3[b] + E3[c]]
+            v = [(x * h) @ S.T for x in v]
+            det = np.linalg.det(np.stack([v[1] - v[0], v[2] - v[0], v[3] - v[0]], -1))
+            swap = det < 0
+            v1 = np.where(swap[:, None], v[2], v[1])
+            v2 = np.where(swap[:, None], v[1], v[2])
+            tets.append(np.stack([v[0], v1, v2, v[3]], 1))
+        V = np.stack(tets, 1).reshape(-1, 4, 3)
+        if jitter is not None:
+            V = V + np.asarray(jitter).reshape(V.shape)
+        return torch.tensor(V, dtype=torch.float64, device=device).contiguous()
     else:
-        raise ValueError("shape must be 'tri' or 'prism'")
+        raise ValueError("shape must be 'tri', 'prism' or 'tet'")
     V = np.stack([lo, up], 1).reshape(-1, lo.shape[1], lo.shape[2])
     if jitter is not None:
         V = V + np.asarray(jitter).reshape(V.shape)

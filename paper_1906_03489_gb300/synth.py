@@ -31,6 +31,9 @@ WORKLOADS = {
     "prism3d_24_p4": dict(dim=3, N=24, P=4, Q=6, shape="prism", seed=6),
     # 2 N^2 affine triangles of a skewed N^2 grid, P=4, Q=6 (GLL, Gauss-Radau)
     "tri2d_128_p4": dict(dim=2, N=128, P=4, Q=6, shape="tri", seed=7),
+    # 6 N^3 affine tetrahedra (Kuhn split of every cube of a skewed N^3 grid),
+    # P=4, Q=6 (GLL, Gauss-Radau, Gauss-Radau)
+    "tet3d_16_p4": dict(dim=3, N=16, P=4, Q=6, shape="tet", seed=8),
 }
 
 # Skew of the collapsed-element grids (node (i, j[, k]) h maps to SKEW applied

@@ -1,4 +1,4 @@
-"""GPU parity of the collapsed-coordinate elements (triangles, prisms) against the FP64 oracle.
+"""GPU parity of the collapsed-coordinate elements (triangles, prisms, tetrahedra) against the FP64 oracle.
 
 Affine elements of a skewed grid with a seeded jitter of every vertex (so
 that no two elements share a Jacobian), orders 1..8 on ragged tiles, both
@@ -31,19 +31,21 @@ def built():
 
 def make(shape, N, P, seed=60, jit=0.02):
     d = 2 if shape == "tri" else 3
-    E = 2 * N ** d
+    E = (6 if shape == "tet" else 2) * N ** d
     jitter = jit / N * synth.uniform(synth.rng(seed), E * (d + 1) * d).reshape(E, d + 1, d)
     plan = spx.Plan(d, E, order=P, shape=shape)
     g = spx.geom_factors(plan, mesh.collapsed_vertices(shape, N, jitter))
     plan.set_geometry(torch.float64, g["geom"], g["dxi"])
     plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])
     skew = synth.SKEW2 if shape == "tri" else synth.SKEW3
-    om = C.CollapsedMesh(shape, C.structured_vertices(shape, N, skew, jitter), P)
+    V = C.kuhn_vertices(N, skew, jitter) if shape == "tet" else C.structured_vertices(shape, N, skew, jitter)
+    om = C.CollapsedMesh(shape, V, P)
     return plan, g, om
 
 
 CASES = [("tri", 3, 1), ("tri", 3, 2), ("tri", 3, 4), ("tri", 2, 6), ("tri", 2, 8),
-         ("prism", 2, 1), ("prism", 2, 2), ("prism", 2, 4), ("prism", 2, 6), ("prism", 1, 8)]
+         ("prism", 2, 1), ("prism", 2, 2), ("prism", 2, 4), ("prism", 2, 6), ("prism", 1, 8),
+         ("tet", 1, 1), ("tet", 2, 2), ("tet", 2, 3), ("tet", 2, 4), ("tet", 1, 6), ("tet", 1, 8)]
 
 
 @pytest.mark.parametrize("shape,N,P", CASES)
@@ -118,6 +120,27 @@ def test_prism_full_workload_sampled(dtype):
     ids = np.concatenate([[0, plan.E - 1], np.sort(np.random.default_rng(0).choice(plan.E, 30, replace=False))])
     Vall = C.structured_vertices("prism", N, synth.SKEW3)
     om = C.CollapsedMesh("prism", Vall[ids], P)
+    nm = om.nm
+    ref = np.concatenate([om.helmholtz_matrix(t) @ u[e * nm:(e + 1) * nm] for t, e in enumerate(ids)])
+    got = np.concatenate([y[e * nm:(e + 1) * nm] for e in ids])
+    assert rel_err(got, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_tet_full_workload_sampled(dtype):
+    w = synth.WORKLOADS["tet3d_16_p4"]
+    N, P = w["N"], w["P"]
+    plan = spx.Plan(3, 6 * N ** 3, order=P, shape="tet")
+    g = spx.geom_factors(plan, mesh.collapsed_vertices("tet", N))
+    plan.set_geometry(torch.float64, g["geom"], g["dxi"])
+    plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])
+    u = synth.uniform(synth.rng(w["seed"]), plan.n_coef)
+    ut = torch.tensor(u, device="cuda", dtype=dtype)
+    y = torch.empty_like(ut)
+    plan.autotune("helmholtz", dtype, ut, y, reps=1)
+    y = spx.helmholtz(plan, ut).cpu().double().numpy()
+    ids = np.concatenate([[0, plan.E - 1], np.sort(np.random.default_rng(0).choice(plan.E, 30, replace=False))])
+    om = C.CollapsedMesh("tet", C.kuhn_vertices(N, synth.SKEW3)[ids], P)
     nm = om.nm
     ref = np.concatenate([om.helmholtz_matrix(t) @ u[e * nm:(e + 1) * nm] for t, e in enumerate(ids)])
     got = np.concatenate([y[e * nm:(e + 1) * nm] for e in ids])

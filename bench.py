@@ -148,9 +148,12 @@ def fp_peaks(torch, sampler_index=0):
     return out
 
 
-# Sources of the Helmholtz kernels and their launcher (what their ncu counters depend on).
+# Sources of the Helmholtz kernels and their launcher (what their ncu counters depend on):
+# the FP32 pair kernel (helm_pair.cuh and what it builds on) and the FP64 role body.
 HELM_SOURCES = ("helm_pair.cuh", "op_kernel.cuh", "lanes.cuh", "kernel_params.h", "device_common.cuh",
                 "launch_ops.cuh", "smem_layout.h")
+HELM64_SOURCES = ("op_kernel.cuh", "lanes.cuh", "kernel_params.h", "device_common.cuh", "launch_ops.cuh",
+                  "smem_layout.h")
 
 
 def kernel_digest(names=None):
@@ -167,7 +170,7 @@ def kernel_digest(names=None):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name):
+def profiled_traffic(name, sources=HELM_SOURCES):
     """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", name)
     try:
@@ -176,7 +179,7 @@ def profiled_traffic(name):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_digest") == kernel_digest(HELM_SOURCES):
+        if kv.get("kernel_digest") == kernel_digest(sources):
             return float(kv["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -459,7 +462,7 @@ def run_ours(a):
                        "parallelism": f"replica per GPU x{world}"},
             "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": round(achieved / fp64_peak, 4) if fp64_peak else None,
-                         "traffic": profiled_traffic("helmholtz_f64_hex32.txt"),
+                         "traffic": profiled_traffic("helmholtz_f64_hex32.txt", HELM64_SOURCES),
                          "peak_kind": "measured: fastest FP64 probe kind on this GPU in this run (fp_peaks)",
                          "algorithmic_flops_per_launch": fl_launch,
                          "flops_model": "per element 2 (2 (n^3 Q + n^2 Q^2 + n Q^3) + 6 Q^4) + 20 Q^3 "

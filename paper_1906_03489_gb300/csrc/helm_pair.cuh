@@ -246,7 +246,6 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
     const float* G0 = geo_staged(p.geom, dsm + ctl.offs[3], t, j0, q0, Q) + b * Q + a;
     const float* G1 = geo_staged(p.geom, dsm + ctl.offs[3], t, two ? j1 : j0, two ? q1 : q0, Q) + b * Q + a;
     const float lam = static_cast<float>(p.lam);
-    V ljk[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       const int w0 = a + Q * b + US * k, w1 = a + Q * b + GS * k;
@@ -268,21 +267,28 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
         r1 = Vt::mul(kk, r1);
         r2 = Vt::mul(kk, r2);
       }
-      V lj;
-      if (p.lam_f) {
-        const V ll = Vt::ldcs2(p.lam_f + q0 + o + b * Q + a, p.lam_f + q1 + o + b * Q + a);
-        lj = Vt::mul(ll, jw);
-      } else {
-        lj = Vt::mul(Vt::bcast(lam), jw);
-      }
       A[w0] = r0;
       F[w1] = r1;
       g2[k] = r2;
-      ljk[k] = lj;
+      (void)jw;
     }
     eo_d<P, Q, true>(tab, g2, z);
+    // mass term: lambda JW u, with JW read again from the staged slot (holding
+    // lambda JW in registers across the D^T contraction made the combined
+    // variable-order kernel spill)
 #pragma unroll
-    for (int k = 0; k < Q; ++k) z[k] = Vt::fmav(ljk[k], u[k], z[k]);
+    for (int k = 0; k < Q; ++k) {
+      const int o = k * Q2 + 6 * Q3;
+      const V jw = Vt::pair(G0[o], G1[o]);
+      V lj;
+      if (p.lam_f) {
+        const int oq = k * Q2 + b * Q + a;
+        lj = Vt::mul(Vt::ldcs2(p.lam_f + q0 + oq, p.lam_f + q1 + oq), jw);
+      } else {
+        lj = Vt::mul(Vt::bcast(lam), jw);
+      }
+      z[k] = Vt::fmav(lj, u[k], z[k]);
+    }
   }
   ctl.sync();
   // every thread is done with the geometry slot
@@ -339,7 +345,9 @@ __device__ __forceinline__ bool helm_pair_tile(const Prm& p, Ctl& ctl, const flo
 }
 
 // Body of order P, selected at run time from the tile (orders <= THR packed
-// two elements per thread).
+// two elements per thread).  (Bodies called out of line, each with its own
+// register allocation, measured 40% slower on the variable-order workload:
+// the calls' register saves cost more than the spills of the union.)
 template <int PLO, int PHI, int QOFF, int THR, class Prm, class Ctl>
 __device__ __forceinline__ bool pair_dispatch(int P, const Prm& p, Ctl& ctl, const Tile& t) {
   if constexpr (PLO <= PHI) {

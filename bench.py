@@ -630,6 +630,10 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
     uu = torch.tensor(ca, device="cuda", requires_grad=True)
     ff = torch.tensor(synth.uniform(synth.rng(41), pa.n_coef), device="cuda")
     lp, kp = lam.clone().requires_grad_(True), kap.clone().requires_grad_(True)
+    # the forward / backward Helmholtz and the adjoint kernel on autotuned tiles
+    scratch = torch.empty(2 * pa.n_quad, dtype=torch.float64, device="cuda")
+    pa.autotune("helmholtz", torch.float64, uu.detach(), torch.empty_like(ff), reps=2)
+    pa.autotune("helmholtz_adjoint", torch.float64, uu.detach(), scratch, reps=2)
 
     def fwd_bwd():
         y = spx.helmholtz_ad(pa, uu, lp, kp)

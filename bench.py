@@ -304,6 +304,32 @@ def timed(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
+def timed_rotating(torch, call, k, launches, stream):
+    """Mean device time of one launch of a streaming operator: `call(i)` runs
+    it on buffer copy i of k (inputs, outputs and the geometric factors it
+    reads; k copies hold over twice the L2, so no launch finds its operands
+    there).  The k calls are captured once in a CUDA graph and the graph is
+    replayed between CUDA events on `stream`, so host time between launches
+    is not counted."""
+    for i in range(k):   # warm-up: launch tiles built before the capture
+        call(i)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        for i in range(k):
+            call(i)
+    rounds = max(2, -(-launches // k))
+    with torch.cuda.stream(stream):
+        g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(rounds):
+            g.replay()
+        e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / (rounds * k)
+
+
 def apply_steps(spx, torch, plans, ins, outs, steps, stream, local):
     """Times `steps` Helmholtz applies alternating between the two copies of
     the workload (inputs of both copies exceed the L2), CUDA events on the
@@ -547,23 +573,44 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
     n3 = (P + 1) ** 3
     reps = 30
     ops = {}
+    geo0 = geoms[0]
     for dt, sz in ((torch.float32, 4), (torch.float64, 8)):
         fp64 = dt == torch.float64
         pk = fp64_peak if fp64 else fp32_peak
+        gk = ("geom", "dxi") if fp64 else ("geom32", "dxi32")
         c = torch.tensor(coef, device="cuda", dtype=dt)
         f = spx.bwd_trans(plan, c)
-        outs = [torch.empty_like(f) for _ in range(3)]
         tag = "f32" if dt == torch.float32 else "f64"
-        packed = torch.empty(3 * plan.n_quad, dtype=dt, device="cuda")
-        for op, fn, nbytes, tin, tout in (
-                ("phys_deriv", lambda: spx.phys_deriv(plan, f, outs), E * 13 * Q ** 3 * sz, f, packed),
-                ("bwd_trans", lambda: spx.bwd_trans(plan, c, f), E * (n3 + Q ** 3) * sz, c, f),
-                ("iproduct", lambda: spx.iproduct(plan, f, c), E * (2 * Q ** 3 + n3) * sz, f, c)):
-            plan.autotune(op, dt, tin, tout, reps=5)
-            fn()
-            ms = timed(fn, reps, stream)
-            ops[f"{op}_{tag}"] = roof(ms, nbytes, E * op_flops_per_elem(op, P, Q), fp64, hbm_peak, pk)
-            ops[f"{op}_{tag}"]["tile_eb_threads_stages"] = list(plan.get_tile(op, dt, P))
+        # streaming operators, each over k copies of its operands (> 2 x L2 in all)
+        for op, nbytes, nq_out in (("phys_deriv", E * 13 * Q ** 3 * sz, 3), ("bwd_trans", E * (n3 + Q ** 3) * sz, 1),
+                                   ("iproduct", E * (2 * Q ** 3 + n3) * sz, 0)):
+            k = max(2, -(-2 * L2_BYTES // nbytes))
+            src = c if op == "bwd_trans" else f
+            ins = [src.clone() for _ in range(k)]
+            outs = [torch.empty(nq_out * plan.n_quad if nq_out else plan.n_coef, dtype=dt, device="cuda")
+                    for _ in range(k)]
+            geos = [(geo0[gk[0]].clone(), geo0[gk[1]].clone()) for _ in range(k)] if op != "bwd_trans" else None
+
+            def call(i, op=op, ins=ins, outs=outs, geos=geos):
+                if geos:
+                    plan.set_geometry(dt, *geos[i])
+                if op == "phys_deriv":
+                    spx.phys_deriv(plan, ins[i], list(outs[i].view(3, -1)))
+                elif op == "bwd_trans":
+                    spx.bwd_trans(plan, ins[i], outs[i])
+                else:
+                    spx.iproduct(plan, ins[i], outs[i])
+            if geos:
+                plan.set_geometry(dt, *geos[0])
+            plan.autotune(op, dt, ins[0], outs[0], reps=5)
+            ms = timed_rotating(torch, call, k, 60, stream)
+            plan.set_geometry(dt, geo0[gk[0]], geo0[gk[1]])
+            r = roof(ms, nbytes, E * op_flops_per_elem(op, P, Q), fp64, hbm_peak, pk)
+            r["tile_eb_threads_stages"] = list(plan.get_tile(op, dt, P))
+            r["timing"] = (f"{k} copies of the operands ({k * nbytes / 1e6:.0f} MB, > 2 x L2) launched in turn "
+                           "from a CUDA graph, CUDA events around the replays")
+            ops[f"{op}_{tag}"] = r
+            del ins, outs, geos
         # FwdTrans (elemental preconditioned CG in one launch; reads f and JW, writes the coefficients)
         # and Integral (reads f and JW)
         f = spx.bwd_trans(plan, torch.tensor(coef, device="cuda", dtype=dt))
@@ -584,11 +631,21 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
             ops["sensor_f64"] = roof(ms, E * (n3 + Q ** 3 + 1) * sz, E * op_flops_per_elem("sensor", P, Q), True,
                                      hbm_peak, pk)
             ops["sensor_f64"]["tile_eb_threads_stages"] = list(plan.get_tile("sensor", dt, P))
-        res = torch.empty((), dtype=torch.float64, device="cuda")
-        ms = timed(lambda: spx.integral(plan, f, res), reps, stream)
         # a reduction streaming 2 Q^3 values per element: HBM bound in both precisions
-        ops[f"integral_{tag}"] = roof(ms, E * 2 * Q ** 3 * sz, E * op_flops_per_elem("integral", P, Q), False,
-                                      hbm_peak, pk)
+        nbytes = E * 2 * Q ** 3 * sz
+        k = max(2, -(-2 * L2_BYTES // nbytes))
+        ins = [f.clone() for _ in range(k)]
+        geos = [(geo0[gk[0]].clone(), geo0[gk[1]].clone()) for _ in range(k)]
+        res = torch.empty(k, dtype=torch.float64, device="cuda")
+
+        def call_int(i):
+            plan.set_geometry(dt, *geos[i])
+            spx.integral(plan, ins[i], res[i])
+        ms = timed_rotating(torch, call_int, k, 60, stream)
+        plan.set_geometry(dt, geo0[gk[0]], geo0[gk[1]])
+        ops[f"integral_{tag}"] = roof(ms, nbytes, E * op_flops_per_elem("integral", P, Q), False, hbm_peak, pk)
+        ops[f"integral_{tag}"]["timing"] = f"{k} copies of the operands launched in turn from a CUDA graph"
+        del ins, geos
     ex["ops_hex32"] = ops
     # variable order workload
     wv, pv, gv, cv = make_workload("hex3d_24_varp", spx, mesh, synth, torch)
@@ -872,6 +929,24 @@ def run_case(a):
         ms = timed(lambda: spx.helmholtz(plan, u, out=y), max(1, a.steps), stream)
         print(json.dumps({"case": "helm", "workload": a.workload, "dtype": str(dt), "ms": round(ms, 4),
                           "tile": plan.get_tile("helmholtz", dt, P)}), flush=True)
+    elif a.case == "ops":
+        # BwdTrans then IProductWRTBase of the workload, each with the same fixed tile (--tile / --tile64)
+        w, plans, _, coef = make_workload(a.workload, spx, mesh, synth, torch)
+        plan = plans[0]
+        P = w["P"]
+        dt = torch.float64 if a.precision == "f64" else torch.float32
+        c = torch.tensor(coef, device="cuda", dtype=dt)
+        f = torch.empty(plan.n_quad, dtype=dt, device="cuda")
+        tile = a.tile64 if dt == torch.float64 else a.tile
+        res = {"case": "ops", "workload": a.workload, "dtype": str(dt)}
+        for op, fn in (("bwd_trans", lambda: spx.bwd_trans(plan, c, f)), ("iproduct", lambda: spx.iproduct(plan, f, c))):
+            if tile:
+                eb, nt, st = (int(x) for x in tile.split(","))
+                plan.set_tile(op, dt, eb, nt, st)
+            fn()   # warm-up (module load, tile lists)
+            res[op + "_ms"] = round(timed(fn, max(1, a.steps), stream), 4)
+            res[op + "_tile"] = plan.get_tile(op, dt, P)
+        print(json.dumps(res), flush=True)
     elif a.case == "peaks":
         print(json.dumps({"case": "peaks", "fp_peaks": fp_peaks(torch)}), flush=True)
     elif a.case == "varp":
@@ -979,8 +1054,8 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--case", default="bench", choices=["bench", "cg", "varp", "helm", "peaks"],
-                    help="bench: the benchmark line; cg / varp / helm / peaks: one short run for profiling")
+    ap.add_argument("--case", default="bench", choices=["bench", "cg", "varp", "helm", "ops", "peaks"],
+                    help="bench: the benchmark line; cg / varp / helm / ops / peaks: one short run for profiling")
     ap.add_argument("--precision", default="f32_reliable",
                     help="cg: f64 | f32_refine | f32_reliable; varp, helm: f32 | f64")
     ap.add_argument("--cg-maxit", type=int, default=30)

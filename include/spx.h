@@ -246,15 +246,22 @@ spx_status spx_plan_set_geometry(spx_plan *plan, spx_dtype dtype, const void *ge
  * Overrides the launch tile of one operator/precision/order: elements per
  * batch `eb` (1..64), threads per block `nthreads` (32..512, multiple of
  * 32) and pipeline depth `stages` (1..4).  order = -1 sets every order.
- * Two operators derive their block size from eb instead:
+ * Three kinds of kernel derive their block size from eb instead:
  *  - FP64 3D Helmholtz (and any precision with a collocation basis): eb * Q^2
  *    threads; there stages 0 reads the geometric factors from L2 (the tile's
  *    factors are prefetched when it starts) instead of staging them in shared
- *    memory, which leaves room for larger tiles;
+ *    memory, which leaves room for larger tiles, and `nthreads` (32..1024)
+ *    picks the register budget of a uniform-order plan (<= 512: 128
+ *    registers per thread, above: 72, for more CTAs per SM);
  *  - FP32 3D Helmholtz (element-pair kernel): ceil(eb / 2) * Q^2 threads;
  *    there `nthreads` (32..1024) is the number of threads per SM that the
  *    register budget must allow (<= 512: 128 registers per thread, <= 640:
- *    96, else 80) and `stages` (0..4) the L2 prefetch distance in tiles. */
+ *    96, else 80) and `stages` (0..4) the L2 prefetch distance in tiles;
+ *  - FP32 3D BwdTrans and IProductWRTBase of a uniform-order plan with the
+ *    modified basis (the same element-pair layout): ceil(eb / 2) * Q^2
+ *    threads, `nthreads` (32..2048) the threads per SM of the register budget
+ *    (<= 768: 80 registers, <= 1024: 64, <= 1280: 48, else 40), `stages`
+ *    (0..4) the L2 prefetch distance in tiles. */
 spx_status spx_plan_set_tile(spx_plan *plan, spx_op op, spx_dtype dtype, int order, int eb, int nthreads,
                              int stages);
 

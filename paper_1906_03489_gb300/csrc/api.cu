@@ -31,8 +31,8 @@ static int default_eb(int dim, int Q) {
 size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& cfg) {
   if (plan->shape) return collapsed_smem_bytes(plan, dtype, cfg.order[plan->uP].eb);
   if (uses_pair_kernel(plan, op, dtype)) {
-    const PairShape s = pair_shape(plan, cfg, pair_threshold(plan));
-    return s.nthreads > 512 ? SIZE_MAX : s.smem;
+    const PairShape s = pair_shape(plan, cfg, pair_threshold(plan), op);
+    return s.nthreads > (op == OP_HELM ? 512 : 1024) ? SIZE_MAX : s.smem;
   }
   // worst case: coefficient fields present
   return smem_layout(plan, op, dtype == 0 ? 8 : 4, cfg, true, true).total;
@@ -463,14 +463,16 @@ spx_status spx_plan_set_tile(spx_plan* p, spx_op op, spx_dtype dt, int order, in
   if (!p) return fail(SPX_ERR_INVALID_ARG, "set_tile: NULL plan");
   if (op < 0 || op >= OP_KINDS || (dt != SPX_F64 && dt != SPX_F32))
     return fail(SPX_ERR_INVALID_ARG, "set_tile: bad operator or dtype");
-  const int max_nt = uses_pair_kernel(p, op, dt) ? 1024 : 512;
+  // pair kernels: nthreads is the threads-per-SM class of the register budget
   // stages 0: the FP32 3D pair kernel's L2 prefetch distance, or the other 3D
   // Helmholtz bodies with Q^2 threads per element reading geometry from L2
   const bool role3 = op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL && !p->shape;
+  const int max_nt = uses_pair_kernel(p, op, dt) ? (op == OP_HELM ? 1024 : 2048) : (role3 ? 1024 : 512);
   const int min_st = (uses_pair_kernel(p, op, dt) || role3) ? 0 : 1;
   if (eb < 1 || eb > kMaxEB || nthreads < 32 || nthreads > max_nt || nthreads % 32 || stages < min_st || stages > 4)
-    return fail(SPX_ERR_INVALID_ARG, "set_tile: eb 1..64, nthreads 32..512 (1024 for the FP32 3D Helmholtz), "
-                                     "multiple of 32, stages 1..4 (0..4 for the 3D Helmholtz)");
+    return fail(SPX_ERR_INVALID_ARG, "set_tile: eb 1..64, nthreads 32..512 (3D Helmholtz: 1024; FP32 BwdTrans / "
+                                     "IProductWRTBase pair kernels of one order: 2048), multiple of 32, stages 1..4 "
+                                     "(0..4 for the 3D Helmholtz and the pair kernels)");
   if (order != -1 && (order < 1 || order > kMaxP)) return fail(SPX_ERR_INVALID_ARG, "set_tile: order outside 1..8");
   LaunchCfg c = p->cfg[op][dt];
   c.nthreads = nthreads;
@@ -595,8 +597,45 @@ spx_status spx_helmholtz_diag(const spx_plan* p, spx_dtype dt, double lambda, vo
 // ---------------------------------------------------------------------------
 // Autotuning (§3.3: the fastest strategy is picked at start-up).
 // ---------------------------------------------------------------------------
+// Reads a buffer larger than the L2 (16-byte words, cached in L2 only), so
+// that the next launch finds none of its operands there; the lines it leaves
+// are clean (no write-back charged to the timed launch).  The buffer is
+// zeroed, so the sink is never written.
+__global__ void l2_evict_kernel(const uint4* __restrict__ buf, size_t n, unsigned* sink) {
+  unsigned x = 0;
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    const uint4 v = __ldcg(buf + i);
+    x ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (x == 0x9e3779b9u) *sink = x;
+}
+
+// Device buffer of twice the L2 for l2_evict_kernel, held for one autotune call.
+struct EvictBuf {
+  uint4* d = nullptr;
+  size_t n = 0;
+  ~EvictBuf() {
+    if (d) cudaFree(d);
+  }
+  spx_status init(cudaStream_t st) {
+    int dev = 0, l2 = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune: L2 size");
+    n = 2 * size_t(std::max(l2, 1 << 20)) / sizeof(uint4);
+    if ((e = cudaMalloc(&d, (n + 1) * sizeof(uint4))) != cudaSuccess) return cuda_fail(e, "cudaMalloc(evict)");
+    if ((e = cudaMemsetAsync(d, 0, (n + 1) * sizeof(uint4), st)) != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    return SPX_OK;
+  }
+  void evict(int num_sms, cudaStream_t st) const {
+    l2_evict_kernel<<<num_sms * 4, 512, 0, st>>>(d, n, reinterpret_cast<unsigned*>(d + n));
+  }
+};
+
+// Mean time of one launch with the L2 evicted before each (the operands of
+// a streaming operator then come from HBM, as on a mesh larger than the L2).
 static float time_op(spx_plan* p, int op, spx_dtype dt, const void* in, void* out, int reps, cudaStream_t st,
-                     spx_status* err) {
+                     const EvictBuf& ev, spx_status* err) {
   void* o[3] = {out, nullptr, nullptr};
   const void* in1 = nullptr;
   size_t qbytes = (dt == SPX_F64 ? 8 : 4) * static_cast<size_t>(p->n_quad);
@@ -609,21 +648,29 @@ static float time_op(spx_plan* p, int op, spx_dtype dt, const void* in, void* ou
     in1 = in;
     o[1] = static_cast<char*>(out) + qbytes;
   }
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  std::vector<cudaEvent_t> ev0(reps), ev1(reps);
+  for (int i = 0; i < reps; ++i) {
+    cudaEventCreate(&ev0[i]);
+    cudaEventCreate(&ev1[i]);
+  }
   *err = run_op(p, op, dt, in, in1, nullptr, nullptr, o[0], o[1], o[2], 1.0, st);  // warm-up
-  cudaEventRecord(e0, st);
-  for (int i = 0; i < reps && *err == SPX_OK; ++i)
+  for (int i = 0; i < reps && *err == SPX_OK; ++i) {
+    ev.evict(p->num_sms, st);
+    cudaEventRecord(ev0[i], st);
     *err = run_op(p, op, dt, in, in1, nullptr, nullptr, o[0], o[1], o[2], 1.0, st);
-  cudaEventRecord(e1, st);
-  cudaError_t ce = cudaEventSynchronize(e1);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+    cudaEventRecord(ev1[i], st);
+  }
+  cudaError_t ce = cudaEventSynchronize(ev1[reps - 1]);
+  float total = 0.f;
+  for (int i = 0; i < reps; ++i) {
+    float ms = 0.f;
+    if (ce == cudaSuccess && *err == SPX_OK) cudaEventElapsedTime(&ms, ev0[i], ev1[i]);
+    total += ms;
+    cudaEventDestroy(ev0[i]);
+    cudaEventDestroy(ev1[i]);
+  }
   if (ce != cudaSuccess && *err == SPX_OK) *err = cuda_fail(ce, "autotune timing");
-  return ms / std::max(1, reps);
+  return total / reps;
 }
 
 // Threads (compute threads plus the producer warp of the variable-order FP32
@@ -636,7 +683,7 @@ static void tile_footprint(const spx_plan* p, int op, int dt, const LaunchCfg& b
   c.order[P].eb = eb;
   const int Q = P + p->qoff;
   if (uses_pair_kernel(p, op, dt)) {
-    const PairShape s = pair_shape(p, c, pair_threshold(p));
+    const PairShape s = pair_shape(p, c, pair_threshold(p), op);
     *thr = s.nthreads + (p->uniform ? 0 : 32);
     *smem = s.smem;
   } else {
@@ -651,15 +698,22 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
     return fail(SPX_ERR_INVALID_ARG, "autotune: bad argument");
   if (p->E == 0) return SPX_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  EvictBuf ev;
+  if (spx_status es = ev.init(st); es != SPX_OK) return es;
   const int ebs[] = {1, 2, 3, 4, 5, 6, 7, 8, 12, 16, 24, 32};
   const bool pair = uses_pair_kernel(p, op, dt);
   // bodies with Q^2 threads per element take their block size from eb
   const bool role = op == OP_HELM && p->dim == 3 && p->bkind != BK_GENERAL && !pair && !p->shape;
-  // the pair kernel derives its CTA size from eb: there `nthreads` picks the
+  // the pair kernels derive their CTA size from eb: there `nthreads` picks the
   // register budget (threads per SM) and `stages` the L2 prefetch distance
-  const std::vector<int> nts = pair ? std::vector<int>{512, 640, 768}
-                                    : (role ? std::vector<int>{256} : std::vector<int>{64, 128, 192, 256, 384, 512});
-  const std::vector<int> sts = (pair || role) ? std::vector<int>{0, 1, 2} : std::vector<int>{1, 2, 3};
+  const bool sf = pair && (op == OP_BWD || op == OP_IPROD);
+  const std::vector<int> nts = sf     ? std::vector<int>{768, 1024, 1280, 1536}
+                               : pair ? std::vector<int>{512, 640, 768}
+                                      : (role ? (p->uniform ? std::vector<int>{512, 896} : std::vector<int>{512})
+                                              : std::vector<int>{64, 128, 192, 256, 384, 512});
+  // (BwdTrans / IProductWRTBase pair kernels: slots of the input ring, 0 = registers)
+  const std::vector<int> sts = sf ? std::vector<int>{0, 2, 3}
+                                  : ((pair || role) ? std::vector<int>{0, 1, 2} : std::vector<int>{1, 2, 3});
   LaunchCfg best = p->cfg[op][dt];
   // Variable order: one launch serves every order, so its CTA is sized by the
   // largest order's tile (threads and shared memory); an order whose tile
@@ -697,7 +751,7 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
         p->cfg[op][dt] = c;
         p->tiles[op][dt].dirty = true;
         spx_status s;
-        const float ms = time_op(p, op, dt, in, out, reps, st, &s);
+        const float ms = time_op(p, op, dt, in, out, reps, st, ev, &s);
         if (s != SPX_OK) {
           p->cfg[op][dt] = best;
           p->tiles[op][dt].dirty = true;
@@ -719,20 +773,24 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
     if (!p->present[P]) continue;
     float bms = 1e30f;
     int beb = best.order[P].eb, bsg = best.stages;
-    // bodies with Q^2 threads per element: the tile size and the staging depth
-    // decide the CTAs per SM together (staged geometry is most of the shared
-    // memory), so they are searched jointly
+    // bodies with Q^2 threads per element: the tile size, the staging depth
+    // and the register class decide the CTAs per SM together (staged geometry
+    // is most of the shared memory), so they are searched jointly
     const std::vector<int> sgs = role ? sts : std::vector<int>{best.stages};
+    const std::vector<int> ntl = role ? nts : std::vector<int>{best.nthreads};
+    int bnt = best.nthreads;
+    for (int nt : ntl)
     for (int eb : ebs) {
       for (int sg : sgs) {
         LaunchCfg c = best;
         c.order[P].eb = eb;
         c.stages = sg;
+        c.nthreads = nt;
         if (op_smem_bytes(p, op, dt, c) > p->max_smem) continue;
         p->cfg[op][dt] = c;
         p->tiles[op][dt].dirty = true;
         spx_status s;
-        float ms = time_op(p, op, dt, in, out, reps, st, &s);
+        float ms = time_op(p, op, dt, in, out, reps, st, ev, &s);
         if (s != SPX_OK) {
           p->cfg[op][dt] = best;
           p->tiles[op][dt].dirty = true;
@@ -743,14 +801,16 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
           bms = ms;
           beb = eb;
           bsg = sg;
+          bnt = nt;
         }
       }
     }
     best.order[P].eb = beb;
     best.stages = bsg;
+    best.nthreads = bnt;
     best_ms = bms;
   }
-  for (int nt : nts) {
+  for (int nt : role ? std::vector<int>{} : nts) {
     for (int sg : sts) {
       LaunchCfg c = best;
       c.nthreads = nt;
@@ -759,7 +819,7 @@ spx_status spx_autotune(spx_plan* p, spx_op op, spx_dtype dt, const void* in, vo
       p->cfg[op][dt] = c;
       p->tiles[op][dt].dirty = true;
       spx_status s;
-      float ms = time_op(p, op, dt, in, out, reps, st, &s);
+      float ms = time_op(p, op, dt, in, out, reps, st, ev, &s);
       if (s != SPX_OK) {
         if (s == SPX_ERR_UNSUPPORTED) continue;
         p->cfg[op][dt] = best;

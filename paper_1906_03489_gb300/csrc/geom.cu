@@ -337,7 +337,17 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(const T* __restri
     const int64_t qd = quad_off ? quad_off[e + 1] - q0 : qd_uniform;
     const T* jw = geom + int64_t(nf) * q0 + int64_t(nf - 1) * qd;
     const T* fe = f + q0;
-    for (int64_t q = lane; q < qd; q += 32) part.add(jw[q], fe[q]);
+    // four terms per lane in flight (loads first), added in the lane's order
+    int64_t q = lane;
+    for (; q + 96 < qd; q += 128) {
+      const T a0 = jw[q], a1 = jw[q + 32], a2 = jw[q + 64], a3 = jw[q + 96];
+      const T b0 = fe[q], b1 = fe[q + 32], b2 = fe[q + 64], b3 = fe[q + 96];
+      part.add(a0, b0);
+      part.add(a1, b1);
+      part.add(a2, b2);
+      part.add(a3, b3);
+    }
+    for (; q < qd; q += 32) part.add(jw[q], fe[q]);
   }
   double acc = part.value();
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);

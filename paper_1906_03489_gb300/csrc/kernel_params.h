@@ -93,6 +93,10 @@ struct PairLayout {
   static constexpr int WA = upm(mx((n - 1) + Q * (n - 1) + XS * (Q - 1) + 1, Q * Q + US * (Q - 1)), Q * Q, M);
   static constexpr int WC = upm((Q - 1) + Q * (n - 1) + YS * (Q - 1) + 1, Q * Q, M);
   static constexpr int WF = upm(mx(Q * Q + GS * (Q - 1), (Q - 1) + Q * (n - 1) + ZS * (n - 1) + 1), Q * Q, M);
+  // group strides of the streaming operators (pair_ops.cuh): X alone in A
+  // (BwdTrans), Y2 alone in F (IProductWRTBase)
+  static constexpr int WX = upm((n - 1) + Q * (n - 1) + XS * (Q - 1) + 1, Q * Q, M);
+  static constexpr int WZ = upm((Q - 1) + Q * (n - 1) + ZS * (n - 1) + 1, Q * Q, M);
 };
 
 // Orders packed two elements per thread in a variable-order launch (measured:
@@ -115,6 +119,23 @@ inline void pair_ws_bytes(int P, int QOFF, int lanes, uint64_t w[3]) {
     SPX_PWS(1) SPX_PWS(2) SPX_PWS(3) SPX_PWS(4) SPX_PWS(5) SPX_PWS(6) SPX_PWS(7) SPX_PWS(8)
 #undef SPX_PWS
 #undef SPX_PWS_
+    default: break;
+  }
+}
+
+// Group strides in bytes of the streaming pair kernels (pair_ops.cuh, two
+// elements per thread): {WX, WC, WZ}.
+inline void pair_sf_bytes(int P, int QOFF, uint64_t w[3]) {
+  w[0] = w[1] = w[2] = 0;
+  switch (P * 4 + QOFF) {
+#define SPX_PSF_(p, q) \
+  case p * 4 + (q - p): \
+    w[0] = 8u * PairLayout<p, q, 16>::WX; w[1] = 8u * PairLayout<p, q, 16>::WC; w[2] = 8u * PairLayout<p, q, 16>::WZ; \
+    break;
+#define SPX_PSF(p) SPX_PSF_(p, p + 1) SPX_PSF_(p, p + 2)
+    SPX_PSF(1) SPX_PSF(2) SPX_PSF(3) SPX_PSF(4) SPX_PSF(5) SPX_PSF(6) SPX_PSF(7) SPX_PSF(8)
+#undef SPX_PSF
+#undef SPX_PSF_
     default: break;
   }
 }

@@ -7,6 +7,7 @@
 
 #include "helm_pair.cuh"
 #include "op_kernel.cuh"
+#include "pair_ops.cuh"
 #include "smem_layout.h"
 #include "spx_internal.h"
 
@@ -27,11 +28,11 @@ spx_status launch_pair_kernel(K kern, const Prm& pp, int nthreads, uint32_t smem
   int nb = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthreads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-  if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile does not fit on an SM");
+  if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "pair-kernel tile does not fit on an SM");
   const int grid = std::min<int64_t>(n_tiles, int64_t(nb) * plan->num_sms);
   kern<<<grid, nthreads, smem, stream>>>(pp);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "Helmholtz kernel launch");
+  if (e != cudaSuccess) return cuda_fail(e, "pair kernel launch");
   return SPX_OK;
 }
 
@@ -107,6 +108,54 @@ spx_status launch_pair(const LaunchReq& r) {
   }
 }
 
+template <int OP, int P, int QOFF, int REG>
+spx_status launch_sf_reg(const SfParams<P, QOFF>& pp, const PairShape& s, const spx_plan* plan, int n_tiles,
+                         cudaStream_t stream) {
+  static std::mutex mu;
+  static bool configured = false;
+  return launch_pair_kernel(sf_pair_kernel<OP, P, QOFF, REG>, pp, s.nthreads, s.smem, plan, n_tiles, stream,
+                            &configured, &mu);
+}
+
+// FP32 BwdTrans / IProductWRTBase on hexahedra of one order in the pair
+// layout (pair_ops.cuh).  `nthreads` of the launch configuration is the
+// number of threads per SM the register budget must allow (80 registers up
+// to 768, 64 up to 1024, 48 up to 1280, else 40); `stages` the slots of the
+// shared-memory input ring (0: inputs carried in registers).
+template <int OP, int P, int QOFF>
+spx_status launch_sf_pair(const LaunchReq& r) {
+  const spx_plan* plan = r.plan;
+  const LaunchCfg& cfg = plan->cfg[OP][1];
+  const TileList& tl = plan->tiles[OP][1];
+  if (tl.n == 0) return SPX_OK;
+  SfParams<P, QOFF> pp{};
+  auto& p = pp.k;
+  const std::vector<double>& t = plan->tab[P];
+  for (int i = 0; i < tab_len(P, QOFF); ++i) p.tab[i] = static_cast<float>(t[i]);
+  p.tiles = tl.d;
+  p.in0 = static_cast<const float*>(r.in0);
+  p.geom = static_cast<const float*>(r.geom);
+  p.out0 = static_cast<float*>(r.out0);
+  p.status = plan->d_status;
+  p.skip = r.skip;
+  p.n_tiles = tl.n;
+  const PairShape s = pair_shape(plan, cfg, kMaxP, OP);
+  if (s.nthreads > 1024) return fail(SPX_ERR_UNSUPPORTED, "operator tile needs more than 1024 threads");
+  if (s.smem > plan->max_smem) return fail(SPX_ERR_UNSUPPORTED, "operator tile does not fit in shared memory");
+  pp.stages = cfg.stages;
+  pp.eb = cfg.order[P].eb;
+  pp.off_a = s.off_a;
+  pp.off_c = s.off_c;
+  pp.off_f = s.off_f;
+  pp.off_ring = s.off_geo;
+  pp.slot_bytes = s.slot_bytes;
+  const int budget = cfg.nthreads;
+  if (budget <= 768) return launch_sf_reg<OP, P, QOFF, 80>(pp, s, plan, tl.n, r.stream);
+  if (budget <= 1024) return launch_sf_reg<OP, P, QOFF, 64>(pp, s, plan, tl.n, r.stream);
+  if (budget <= 1280) return launch_sf_reg<OP, P, QOFF, 48>(pp, s, plan, tl.n, r.stream);
+  return launch_sf_reg<OP, P, QOFF, 40>(pp, s, plan, tl.n, r.stream);
+}
+
 template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0>
 spx_status launch_impl(const LaunchReq& r) {
   const spx_plan* plan = r.plan;
@@ -150,17 +199,24 @@ spx_status launch_impl(const LaunchReq& r) {
   p.work_base = L.work_base;
   p.work_bytes = L.work_bytes;
   p.meta_base = L.meta_base;
+  // 3D Helmholtz bodies with Q^2 threads per element, one order: `nthreads`
+  // above 512 selects the 72-register class (more CTAs per SM)
+  constexpr bool kRole = OP == OP_HELM && DIM == 3 && BK != 1 && PLO == PHI;
+  const bool low_regs = kRole && cfg.nthreads > 512;
   auto kern = op_kernel<T, DIM, OP, PLO, PHI, QOFF, BK>;
-  // raise the dynamic shared-memory limit once per instantiation
+  if constexpr (kRole) {
+    if (low_regs) kern = op_kernel<T, DIM, OP, PLO, PHI, QOFF, BK, 72>;
+  }
+  // raise the dynamic shared-memory limit once per kernel
   static std::mutex mu;
-  static size_t configured = 0;
+  static size_t configured[2] = {0, 0};
   {
     std::lock_guard<std::mutex> g(mu);
-    if (L.total > configured) {
+    if (L.total > configured[low_regs]) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(plan->max_smem));
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-      configured = plan->max_smem;
+      configured[low_regs] = plan->max_smem;
     }
   }
   int nthr = cfg.nthreads;
@@ -187,6 +243,8 @@ spx_status launch_impl(const LaunchReq& r) {
 template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0>
 spx_status launch_any(const LaunchReq& r) {
   if constexpr (std::is_same_v<T, float> && DIM == 3 && OP == OP_HELM && BK == 0) return launch_pair<PLO, PHI, QOFF>(r);
+  else if constexpr (std::is_same_v<T, float> && DIM == 3 && (OP == OP_BWD || OP == OP_IPROD) && BK == 0 && PLO == PHI)
+    return r.plan->bkind == BK_PARITY ? launch_sf_pair<OP, PLO, QOFF>(r) : launch_impl<T, DIM, OP, PLO, PHI, QOFF, BK>(r);
   else return launch_impl<T, DIM, OP, PLO, PHI, QOFF, BK>(r);
 }
 

@@ -1221,8 +1221,11 @@ __device__ __forceinline__ void dispatch_order(int P, const Prm& p, const Ctx<T>
   }
 }
 
-template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0>
-__global__ void __launch_bounds__(512, 1) op_kernel(const __grid_constant__ KParams<T, PLO, PHI, QOFF> p) {
+// REG: register budget per thread (128 lets a 512-thread block run; the 3D
+// Helmholtz bodies with Q^2 threads per element also come with 72, for more
+// CTAs per SM).
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0, int REG = 128>
+__global__ void __maxnreg__(REG) op_kernel(const __grid_constant__ KParams<T, PLO, PHI, QOFF> p) {
   extern __shared__ __align__(128) char sm[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
   uint32_t* soff = reinterpret_cast<uint32_t*>(sm + p.meta_base);

@@ -102,6 +102,7 @@ struct PairShape {
   uint32_t off_a, off_c, off_f;  // byte offsets of the work buffers
   uint32_t off_geo;              // byte offset of the geometry slot
   uint32_t off_meta;             // byte offset of the two tile-metadata buffers (variable order)
+  uint32_t slot_bytes;           // BwdTrans / IProductWRTBase: bytes per input-ring slot (at off_geo)
   uint32_t smem;
 };
 
@@ -109,24 +110,42 @@ struct PairShape {
 // coefficient and quadrature offsets of up to kMaxEB elements).
 constexpr uint32_t kTileMetaBytes = 16 + 2 * 8 * kMaxEB;
 
-inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg, int thr) {
+// BwdTrans / IProductWRTBase in the pair layout (pair_ops.cuh, uniform
+// order): the work buffers of their phases, then `stages` input-ring slots
+// (SfSlot) in place of the geometry slot.
+inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg, int thr, int op = OP_HELM) {
   PairShape s{};
   uint64_t wa = 0, wc = 0, wf = 0, geo = 0;
+  const bool sf = op == OP_BWD || op == OP_IPROD;
   for (int P = 1; P <= kMaxP; ++P) {
     if (!plan->present[P]) continue;
     const int Q = P + plan->qoff;
     const int eb = cfg.order[P].eb;
-    const int lanes = pair_lanes(P, thr);
+    const int lanes = sf ? 2 : pair_lanes(P, thr);
     const int groups = (eb + lanes - 1) / lanes;
     uint64_t w[3];
-    pair_ws_bytes(P, plan->qoff, lanes, w);
+    if (sf) {
+      pair_sf_bytes(P, plan->qoff, w);
+      if (op == OP_BWD) w[2] = 0;   // A (X) and C (Y)
+      else w[0] = 0;                // C (Y3) and F (Y2)
+    } else {
+      pair_ws_bytes(P, plan->qoff, lanes, w);
+    }
     s.nthreads = std::max(s.nthreads, groups * Q * Q);
     wa = std::max<uint64_t>(wa, groups * w[0]);
     wc = std::max<uint64_t>(wc, groups * w[1]);
     wf = std::max<uint64_t>(wf, groups * w[2]);
-    geo = std::max<uint64_t>(geo, uint64_t(eb) * geo_erb(Q));   // per element regions
+    if (!sf) geo = std::max<uint64_t>(geo, uint64_t(eb) * geo_erb(Q));   // per element regions
   }
   s.nthreads = (s.nthreads + 31) / 32 * 32;
+  if (sf) {
+    const int P = plan->uP, Q = P + plan->qoff, eb = cfg.order[P].eb;
+    const uint64_t nv = op == OP_BWD ? uint64_t(P + 1) * (P + 1) * (P + 1) : uint64_t(Q) * Q * Q;
+    const uint64_t f_rb = ((eb * nv * 4 + 15) & ~uint64_t(15)) + 16;
+    const uint64_t jw_rb = ((uint64_t(Q) * Q * Q * 4 + 15) & ~uint64_t(15)) + 16;
+    s.slot_bytes = static_cast<uint32_t>(up128(op == OP_BWD ? f_rb : f_rb + eb * jw_rb));
+    geo = uint64_t(cfg.stages) * s.slot_bytes;
+  }
   s.off_a = 128;
   s.off_c = s.off_a + up128(wa);
   s.off_f = s.off_c + up128(wc);
@@ -142,6 +161,9 @@ inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg, int thr)
 inline int pair_threshold(const spx_plan* plan) { return plan->uniform ? kMaxP : kPairThrVar; }
 
 inline bool uses_pair_kernel(const spx_plan* plan, int op, int dtype) {
+  if ((op == OP_BWD || op == OP_IPROD) && dtype == 1 && plan->dim == 3 && plan->bkind == BK_PARITY && !plan->shape &&
+      plan->uniform)
+    return true;
   return op == OP_HELM && dtype == 1 && plan->dim == 3 && plan->bkind == BK_PARITY && !plan->shape;
 }
 

@@ -195,6 +195,71 @@ def test_pair_kernel_tiles_do_not_change_results(eb, budget, pf):
     assert rel_err(spx.helmholtz(c.plan, ut), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("P,q_offset", [(4, 2), (4, 1), (8, 2), (2, 1)])
+@pytest.mark.parametrize("eb,budget,pf", [(1, 768, 0), (2, 1024, 1), (7, 1280, 2), (13, 1536, 3), (24, 1024, 4),
+                                           (64, 1536, 1)])
+def test_streaming_pair_tiles_do_not_change_results(P, q_offset, eb, budget, pf):
+    """FP32 3D BwdTrans and IProductWRTBase in the element-pair layout: odd and
+    even tile sizes, a ragged last tile (3^3 elements), every register class
+    (the smallest spills at high orders), inputs carried in registers (0) or
+    staged through a ring of 1..4 shared-memory slots, Q = P+1 and P+2.  A
+    tile over 1024 threads or the shared memory is refused, not run."""
+    c = _case(3, 3, P, 0.05, q_offset)
+    u, ut = c.coef(22, torch.float32)
+    f, ft = c.quad(23, torch.float32)
+    for op in ("bwd_trans", "iproduct"):
+        try:
+            c.plan.set_tile(op, torch.float32, eb, budget, pf)
+        except spx.SpxError as e:
+            assert e.status == 2 and not (P <= 4 and eb <= 7)   # refused as too large; small tiles fit
+            return
+        assert c.plan.get_tile(op, torch.float32, P) == (eb, budget, pf)
+    assert rel_err(spx.bwd_trans(c.plan, ut), operators.bwd_trans(c.om, u)) <= 1e-5
+    assert rel_err(spx.iproduct(c.plan, ft), operators.iproduct(c.om, f)) <= 1e-5
+
+
+@pytest.mark.parametrize("P,q_offset", [(2, 2), (4, 2), (4, 1), (8, 2)])
+@pytest.mark.parametrize("nthreads,stages", [(896, 0), (1024, 1), (512, 0)])
+def test_role_register_classes(P, q_offset, nthreads, stages):
+    """FP64 3D Helmholtz with Q^2 threads per element: the 72-register class
+    (nthreads > 512; it spills at the highest orders) and the 128-register
+    class give the oracle's result, on the largest tile that fits (512
+    threads, the shared memory) and on a ragged tile of at most 3 elements."""
+    c = _case(3, 3, P, 0.05, q_offset)
+    u, ut = c.coef(26)
+    ref = operators.helmholtz(c.om, u)
+    Q = P + q_offset
+    for top in (max(1, 512 // Q ** 2), 3):
+        for eb in range(top, 0, -1):
+            try:
+                c.plan.set_tile("helmholtz", torch.float64, eb, nthreads, stages)
+                break
+            except spx.SpxError as e:
+                assert e.status == 2 and eb > 1   # too large for the shared memory; one element always fits
+        assert rel_err(spx.helmholtz(c.plan, ut), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("stages", [0, 2])
+def test_streaming_pair_unaligned_views(stages):
+    """FP32 3D BwdTrans and IProductWRTBase on 4-byte-offset views: every
+    staged range then has ragged head and tail words."""
+    c = _case(3, 3, 4, 0.05)
+    u, _ = c.coef(24)
+    f, _ = c.quad(25)
+
+    def view(x, off):
+        big = torch.zeros(x.size + off + 1, dtype=torch.float32, device="cuda")
+        big[off:off + x.size] = torch.tensor(x, device="cuda", dtype=torch.float32)
+        return big[off:off + x.size]
+
+    for op in ("bwd_trans", "iproduct"):
+        c.plan.set_tile(op, torch.float32, 5, 1024, stages)
+    y = spx.bwd_trans(c.plan, view(u, 1), out=view(np.zeros(c.plan.n_quad), 3))
+    assert rel_err(y, operators.bwd_trans(c.om, u)) <= 1e-5
+    z = spx.iproduct(c.plan, view(f, 2), out=view(np.zeros(c.plan.n_coef), 1))
+    assert rel_err(z, operators.iproduct(c.om, f)) <= 1e-5
+
+
 def test_pair_kernel_tile_too_large_is_refused():
     c = _case(3, 2, 4, 0.05)
     with pytest.raises(spx.SpxError) as e:

@@ -663,6 +663,7 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
         r["gdofs"] = round(pv.n_coef / ms / 1e6, 3)
         r["tiles_eb_by_order"] = {int(p_): pv.get_tile("helmholtz", dt, int(p_))[0]
                                   for p_ in sorted(set(pv.orders.tolist()))}
+        r["threads_stages"] = list(pv.get_tile("helmholtz", dt, int(pv.orders.min()))[1:])
         var[tag] = r
     var["flops_model"] = "sum over elements of the per-order Helmholtz flops (P_e, Q_e = P_e + 2)"
     ex["varp_hex24"] = var
@@ -940,8 +941,9 @@ def run_case(a):
         tile = a.tile64 if dt == torch.float64 else a.tile
         res = {"case": "ops", "workload": a.workload, "dtype": str(dt)}
         for op, fn in (("bwd_trans", lambda: spx.bwd_trans(plan, c, f)), ("iproduct", lambda: spx.iproduct(plan, f, c))):
-            if tile:
-                eb, nt, st = (int(x) for x in tile.split(","))
+            t_op = a.tile_iprod if (op == "iproduct" and a.tile_iprod) else tile
+            if t_op:
+                eb, nt, st = (int(x) for x in t_op.split(","))
                 plan.set_tile(op, dt, eb, nt, st)
             fn()   # warm-up (module load, tile lists)
             res[op + "_ms"] = round(timed(fn, max(1, a.steps), stream), 4)
@@ -956,15 +958,20 @@ def run_case(a):
         u = torch.tensor(coef, device="cuda", dtype=dt)
         y = torch.empty_like(u)
         if a.varp_tiles:   # elements per tile of orders 2..8 (no autotuning: a reproducible launch)
-            for P, eb in zip(range(2, 9), (int(x) for x in a.varp_tiles.split(","))):
-                plan.set_tile("helmholtz", dt, eb, 512, 0 if dt == torch.float32 else 2, order=P)
+            # optional 8th and 9th fields: threads class (FP32: the highest paired order) and stages
+            f = [int(x) for x in a.varp_tiles.split(",")]
+            nt = f[7] if len(f) > 7 else 512
+            st = f[8] if len(f) > 8 else (0 if dt == torch.float32 else 2)
+            for P, eb in zip(range(2, 9), f[:7]):
+                plan.set_tile("helmholtz", dt, eb, nt, st, order=P)
         else:
             plan.autotune("helmholtz", dt, u, y, reps=2)
         spx.helmholtz(plan, u, out=y)   # warm-up (module load, tile lists)
         ms = timed(lambda: spx.helmholtz(plan, u, out=y), max(1, a.steps), stream)
+        orders = sorted(set(plan.orders.tolist()))
         print(json.dumps({"case": "varp", "workload": "hex3d_24_varp", "dtype": str(dt), "ms": round(ms, 4),
-                          "tiles": {int(P): plan.get_tile("helmholtz", dt, int(P))[0]
-                                    for P in sorted(set(plan.orders.tolist()))}}), flush=True)
+                          "tiles": {int(P): plan.get_tile("helmholtz", dt, int(P))[0] for P in orders},
+                          "threads_stages": plan.get_tile("helmholtz", dt, int(orders[0]))[1:]}), flush=True)
 
 
 def oracle_sample_rate(name, n_elem_sample, seconds, repeat=None):
@@ -1051,6 +1058,8 @@ def main():
     ap.add_argument("--workload", default="hex3d_32_p4")
     ap.add_argument("--tile", default=None, help="FP32 apply: eb,threads,stages (skips autotuning)")
     ap.add_argument("--tile64", default=None, help="FP64 apply: eb,threads,stages (skips autotuning)")
+    ap.add_argument("--tile-iprod", dest="tile_iprod", default=None,
+                    help="--case ops: IProductWRTBase tile when it differs from BwdTrans's")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -31,7 +31,7 @@ static int default_eb(int dim, int Q) {
 size_t op_smem_bytes(const spx_plan* plan, int op, int dtype, const LaunchCfg& cfg) {
   if (plan->shape) return collapsed_smem_bytes(plan, dtype, cfg.order[plan->uP].eb);
   if (uses_pair_kernel(plan, op, dtype)) {
-    const PairShape s = pair_shape(plan, cfg, pair_threshold(plan), op);
+    const PairShape s = pair_shape(plan, cfg, pair_threshold(plan, cfg), op);
     return s.nthreads > (op == OP_HELM ? 512 : 1024) ? SIZE_MAX : s.smem;
   }
   // worst case: coefficient fields present
@@ -50,10 +50,17 @@ spx_status ensure_tiles(spx_plan* plan, int op, int dtype) {
                            static_cast<int32_t>(e0), 1});
   } else {
     // heaviest orders first: round-robin assignment then balances the CTAs
+    tl.grp_P.clear();
+    tl.grp_tile.clear();
+    tl.grp_bytes.clear();
     for (int P = kMaxP; P >= 1; --P) {
       if (!plan->present[P]) continue;
       const int eb = cfg.order[P].eb;
       const int64_t b0 = plan->bucket_start[P], b1 = plan->bucket_start[P + 1];
+      const double n = P + 1, Q = P + plan->qoff;
+      tl.grp_P.push_back(P);
+      tl.grp_tile.push_back(static_cast<int>(tiles.size()));
+      tl.grp_bytes.push_back(double(b1 - b0) * (2 * n * n * n + 7 * Q * Q * Q));
       for (int64_t s = b0; s < b1; s += eb) {
         const int cnt = static_cast<int>(std::min<int64_t>(eb, b1 - s));
         bool contig = true;
@@ -62,6 +69,7 @@ spx_status ensure_tiles(spx_plan* plan, int op, int dtype) {
         tiles.push_back(Tile{P, cnt, static_cast<int32_t>(s), contig ? 1 : 0});
       }
     }
+    tl.grp_tile.push_back(static_cast<int>(tiles.size()));
   }
   if (tl.d) cudaFree(tl.d);
   tl.d = nullptr;
@@ -683,7 +691,7 @@ static void tile_footprint(const spx_plan* p, int op, int dt, const LaunchCfg& b
   c.order[P].eb = eb;
   const int Q = P + p->qoff;
   if (uses_pair_kernel(p, op, dt)) {
-    const PairShape s = pair_shape(p, c, pair_threshold(p), op);
+    const PairShape s = pair_shape(p, c, pair_threshold(p, c), op);
     *thr = s.nthreads + (p->uniform ? 0 : 32);
     *smem = s.smem;
   } else {

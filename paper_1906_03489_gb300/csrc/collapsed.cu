@@ -263,27 +263,52 @@ __device__ __forceinline__ void stage_c_bwd(const T* F, T* out, int64_t e_base, 
 // ---- dense 1D stages on the tensor part ------------------------------------
 // y[e][.. i along axis ..] = sum_c A[i][c] x[e][.. c ..] (TR: A[c][i]); extents
 // (N0, N1, N2) in and the same with axis AX resized to M out, axis 0 fastest.
+// One thread per pencil along AX: its NA inputs are read once into registers
+// and every output of the pencil is formed from them, with A at compile-time
+// indices.  FP32 kernels pass A in the kernel's parameter block (a
+// constant-bank operand of the FMA, no load per multiply-add); FP64 kernels
+// pass the shared-memory copy (a broadcast load per multiply-add, hidden by
+// the FP64 pipe; constant-bank FP64 operands made the compiler hold many
+// table values in registers and spill).
 template <int AX, int N0, int N1, int N2, int M, bool TR, bool ACC, typename T>
-__device__ __forceinline__ void stage_dense(const T* x, T* y, const T* A, int ne, int tid, int nthr, int64_t ystride,
-                                            int64_t ybase) {
+__device__ __forceinline__ void stage_dense(const T* x, T* y, const T* A, int ne, int tid, int nthr,
+                                            int64_t ystride, int64_t ybase) {
   constexpr int NA = AX == 0 ? N0 : (AX == 1 ? N1 : N2);
   constexpr int O0 = AX == 0 ? M : N0, O1 = AX == 1 ? M : N1, O2 = AX == 2 ? M : N2;
-  constexpr int XS = N0 * N1 * N2, YS = O0 * O1 * O2;
+  constexpr int XS = N0 * N1 * N2;
   constexpr int SA = AX == 0 ? 1 : (AX == 1 ? N0 : N0 * N1);
   constexpr int SO = AX == 0 ? 1 : (AX == 1 ? O0 : O0 * O1);
-  for (int w = tid; w < ne * YS; w += nthr) {
-    const int e = w / YS, r = w - e * YS;
-    const int i0 = r % O0, i1 = (r / O0) % O1, i2 = r / (O0 * O1);
-    const int m = AX == 0 ? i0 : (AX == 1 ? i1 : i2);
-    const int xb = (AX == 0 ? 0 : i0) + (AX == 1 ? 0 : i1 * N0) + (AX == 2 ? 0 : i2 * N0 * N1);
-    const T* xe = x + e * XS + xb;
-    T acc = T(0);
+  constexpr int NP = XS / NA;   // pencils per element
+  for (int w = tid; w < ne * NP; w += nthr) {
+    const int e = w / NP, r = w - e * NP;
+    // the pencil's two other coordinates (the same extents in x and y), fastest first
+    const int i0 = AX == 0 ? 0 : r % N0;
+    const int i1 = AX == 1 ? 0 : (AX == 0 ? r % N1 : (r / N0) % N1);
+    const int i2 = AX == 2 ? 0 : (AX == 0 ? r / N1 : r / N0);
+    const T* xe = x + e * XS + i0 + N0 * (i1 + N1 * i2);
+    T* yo = y + ybase + e * ystride + i0 + O0 * (i1 + O1 * i2);
+    T v[NA];
 #pragma unroll
-    for (int c = 0; c < NA; ++c) acc = fma(TR ? A[c * M + m] : A[m * NA + c], xe[c * SA], acc);
-    T* yo = y + ybase + e * ystride + r;
-    if (ACC) *yo += acc;
-    else *yo = acc;
-    (void)SO;
+    for (int c = 0; c < NA; ++c) v[c] = xe[c * SA];
+    if constexpr (sizeof(T) == 4) {   // A in the parameter block: every index a constant
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        T acc = (TR ? A[m] : A[m * NA]) * v[0];
+#pragma unroll
+        for (int c = 1; c < NA; ++c) acc = fma(TR ? A[c * M + m] : A[m * NA + c], v[c], acc);
+        if (ACC) yo[m * SO] += acc;
+        else yo[m * SO] = acc;
+      }
+    } else {   // A in shared memory: one output at a time keeps the table loads few
+#pragma unroll 1
+      for (int m = 0; m < M; ++m) {
+        T acc = (TR ? A[m] : A[m * NA]) * v[0];
+#pragma unroll
+        for (int c = 1; c < NA; ++c) acc = fma(TR ? A[c * M + m] : A[m * NA + c], v[c], acc);
+        if (ACC) yo[m * SO] += acc;
+        else yo[m * SO] = acc;
+      }
+    }
   }
 }
 
@@ -303,6 +328,11 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
   extern __shared__ __align__(16) unsigned char csm[];
   Bufs<T, SHAPE, P> b(reinterpret_cast<T*>(csm), p.eb);
   const int tid = threadIdx.x, nthr = blockDim.x;
+  // tables of the dense stages (see stage_dense)
+  constexpr bool kParamTab = sizeof(T) == 4;
+  const T* tB1 = kParamTab ? p.B1 : b.B1;
+  const T* tD1 = kParamTab ? p.D1 : b.D1;
+  const T* tD2 = kParamTab ? p.D2 : b.D2;
   for (int i = tid; i < Q * n; i += nthr) b.B1[i] = p.B1[i];
   for (int i = tid; i < n * Q * n; i += nthr) {
     b.Bb[i] = p.Bb[i];
@@ -328,19 +358,19 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
       if constexpr (SHAPE == kTri) {
         stage_b_fwd<T, P, 1>(b.C, b.F, b.Bb, ne, tid, nthr);
         __syncthreads();
-        stage_dense<0, n, Q, 1, Q, false, false>(b.F, dst, b.B1, ne, tid, nthr, NQ, dbase);   // F[p][j] -> u[i][j]
+        stage_dense<0, n, Q, 1, Q, false, false>(b.F, dst, tB1, ne, tid, nthr, NQ, dbase);   // F[p][j] -> u[i][j]
       } else if constexpr (SHAPE == kTet) {
         stage_c_fwd<T, P>(b.C, b.F, b.Bc, b.toff, b.tdeg, ne, tid, nthr);                     // F[m][k3]
         __syncthreads();
         stage_tb_fwd<T, P>(b.F, b.H, b.Bb, ne, tid, nthr);                                     // H[p][j][k3]
         __syncthreads();
-        stage_dense<0, n, Q, Q, Q, false, false>(b.H, dst, b.B1, ne, tid, nthr, NQ, dbase);   // u[i][j][k3]
+        stage_dense<0, n, Q, Q, Q, false, false>(b.H, dst, tB1, ne, tid, nthr, NQ, dbase);   // u[i][j][k3]
       } else {
         stage_b_fwd<T, P, n>(b.C, b.F, b.Bb, ne, tid, nthr);                                 // F[a][p][k]
         __syncthreads();
-        stage_dense<1, n, n, Q, Q, false, false>(b.F, b.H, b.B1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
+        stage_dense<1, n, n, Q, Q, false, false>(b.F, b.H, tB1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
         __syncthreads();
-        stage_dense<0, n, Q, Q, Q, false, false>(b.H, dst, b.B1, ne, tid, nthr, NQ, dbase);     // u[i][j][k]
+        stage_dense<0, n, Q, Q, Q, false, false>(b.H, dst, tB1, ne, tid, nthr, NQ, dbase);     // u[i][j][k]
       }
       __syncthreads();
     } else {
@@ -350,12 +380,12 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
     if constexpr (OP == OP_DERIV || OP == OP_HELM) {
       // gradient along the collapsed directions: G0, G1 (, G2)
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, Q, false, false>(b.U, b.G0, b.D1, ne, tid, nthr, NQ, 0);
-        stage_dense<1, Q, Q, 1, Q, false, false>(b.U, b.G1, b.D2, ne, tid, nthr, NQ, 0);
+        stage_dense<0, Q, Q, 1, Q, false, false>(b.U, b.G0, tD1, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, 1, Q, false, false>(b.U, b.G1, tD2, ne, tid, nthr, NQ, 0);
       } else {   // eta2 on GLL points (prism) or Gauss-Radau points (tetrahedron)
-        stage_dense<0, Q, Q, Q, Q, false, false>(b.U, b.G0, b.D1, ne, tid, nthr, NQ, 0);
-        stage_dense<1, Q, Q, Q, Q, false, false>(b.U, b.G1, SHAPE == kTet ? b.D2 : b.D1, ne, tid, nthr, NQ, 0);
-        stage_dense<2, Q, Q, Q, Q, false, false>(b.U, b.G2, b.D2, ne, tid, nthr, NQ, 0);
+        stage_dense<0, Q, Q, Q, Q, false, false>(b.U, b.G0, tD1, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, Q, Q, false, false>(b.U, b.G1, SHAPE == kTet ? tD2 : tD1, ne, tid, nthr, NQ, 0);
+        stage_dense<2, Q, Q, Q, Q, false, false>(b.U, b.G2, tD2, ne, tid, nthr, NQ, 0);
       }
       __syncthreads();
     }
@@ -405,15 +435,15 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
       __syncthreads();
       // transposed gradient added to V
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, Q, true, true>(b.G0, b.V, b.D1, ne, tid, nthr, NQ, 0);
+        stage_dense<0, Q, Q, 1, Q, true, true>(b.G0, b.V, tD1, ne, tid, nthr, NQ, 0);
         __syncthreads();
-        stage_dense<1, Q, Q, 1, Q, true, true>(b.G1, b.V, b.D2, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, 1, Q, true, true>(b.G1, b.V, tD2, ne, tid, nthr, NQ, 0);
       } else {
-        stage_dense<0, Q, Q, Q, Q, true, true>(b.G0, b.V, b.D1, ne, tid, nthr, NQ, 0);
+        stage_dense<0, Q, Q, Q, Q, true, true>(b.G0, b.V, tD1, ne, tid, nthr, NQ, 0);
         __syncthreads();
-        stage_dense<1, Q, Q, Q, Q, true, true>(b.G1, b.V, SHAPE == kTet ? b.D2 : b.D1, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, Q, Q, true, true>(b.G1, b.V, SHAPE == kTet ? tD2 : tD1, ne, tid, nthr, NQ, 0);
         __syncthreads();
-        stage_dense<2, Q, Q, Q, Q, true, true>(b.G2, b.V, b.D2, ne, tid, nthr, NQ, 0);
+        stage_dense<2, Q, Q, Q, Q, true, true>(b.G2, b.V, tD2, ne, tid, nthr, NQ, 0);
       }
       __syncthreads();
     }
@@ -427,19 +457,19 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
     if constexpr (OP == OP_IPROD || OP == OP_HELM) {
       // transposed tensor directions, then the collapsed direction -> HBM
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, n, true, false>(b.V, b.F, b.B1, ne, tid, nthr, n * Q, 0);   // F[p][k]
+        stage_dense<0, Q, Q, 1, n, true, false>(b.V, b.F, tB1, ne, tid, nthr, n * Q, 0);   // F[p][k]
         __syncthreads();
         stage_b_bwd<T, P, 1>(b.F, p.out0, e0, b.Bb, ne, tid, nthr);
       } else if constexpr (SHAPE == kTet) {
-        stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, b.B1, ne, tid, nthr, n * Q * Q, 0);  // H[p][j][k3]
+        stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, tB1, ne, tid, nthr, n * Q * Q, 0);  // H[p][j][k3]
         __syncthreads();
         stage_tb_bwd<T, P>(b.H, b.F, b.Bb, ne, tid, nthr);                                    // F[m][k3]
         __syncthreads();
         stage_c_bwd<T, P>(b.F, p.out0, e0, b.Bc, b.toff, b.tdeg, ne, tid, nthr);
       } else {
-        stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, b.B1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
+        stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, tB1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
         __syncthreads();
-        stage_dense<1, n, Q, Q, n, true, false>(b.H, b.F, b.B1, ne, tid, nthr, n * n * Q, 0);  // F[a][p][k]
+        stage_dense<1, n, Q, Q, n, true, false>(b.H, b.F, tB1, ne, tid, nthr, n * n * Q, 0);  // F[a][p][k]
         __syncthreads();
         stage_b_bwd<T, P, n>(b.F, p.out0, e0, b.Bb, ne, tid, nthr);
       }

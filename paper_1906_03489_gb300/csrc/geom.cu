@@ -332,22 +332,31 @@ __global__ void __launch_bounds__(kIntThreads) integral_kernel(const T* __restri
   const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   DotAcc<T> part;   // FP64, or a compensated float pair for FP32 data (no FP64 instruction per term)
-  for (int64_t e = gw; e < E; e += nw) {
-    const int64_t q0 = quad_off ? quad_off[e] : e * qd_uniform;
-    const int64_t qd = quad_off ? quad_off[e + 1] - q0 : qd_uniform;
-    const T* jw = geom + int64_t(nf) * q0 + int64_t(nf - 1) * qd;
-    const T* fe = f + q0;
-    // four terms per lane in flight (loads first), added in the lane's order
-    int64_t q = lane;
-    for (; q + 96 < qd; q += 128) {
-      const T a0 = jw[q], a1 = jw[q + 32], a2 = jw[q + 64], a3 = jw[q + 96];
-      const T b0 = fe[q], b1 = fe[q + 32], b2 = fe[q + 64], b3 = fe[q + 96];
-      part.add(a0, b0);
-      part.add(a1, b1);
-      part.add(a2, b2);
-      part.add(a3, b3);
+  if (!quad_off) {
+    // uniform order: a warp takes four elements at a time (e, e + nw, e + 2 nw,
+    // e + 3 nw), with the loads of all four issued before their terms are added
+    const int64_t qd = qd_uniform;
+    for (int64_t e = gw; e < E; e += 4 * nw) {
+      for (int64_t q = lane; q < qd; q += 32) {
+        T a[4], b[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int64_t ej = e + j * nw;
+          a[j] = ej < E ? geom[int64_t(nf) * ej * qd + int64_t(nf - 1) * qd + q] : T(0);
+          b[j] = ej < E ? f[ej * qd + q] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) part.add(a[j], b[j]);
+      }
     }
-    for (; q < qd; q += 32) part.add(jw[q], fe[q]);
+  } else {
+    for (int64_t e = gw; e < E; e += nw) {
+      const int64_t q0 = quad_off[e];
+      const int64_t qd = quad_off[e + 1] - q0;
+      const T* jw = geom + int64_t(nf) * q0 + int64_t(nf - 1) * qd;
+      const T* fe = f + q0;
+      for (int64_t q = lane; q < qd; q += 32) part.add(jw[q], fe[q]);
+    }
   }
   double acc = part.value();
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);

@@ -26,7 +26,9 @@
 //    S1 coefficients are loaded into registers during S6..S9;
 //  * helm_varp_kernel (several orders, elements of one order scattered
 //    through the mesh): a producer warp outside the compute barriers writes
-//    each tile's element offsets into shared memory and stages its geometry.
+//    each tile's element offsets into shared memory and stages its geometry;
+//    every CTA keeps to the tiles of one order, so that each order's body
+//    runs in a loop of its own.
 // Coefficients are read straight from HBM (coalesced, read once), outputs
 // stored straight to HBM.
 #pragma once
@@ -44,6 +46,13 @@ struct PairParams {
   uint32_t off_a, off_c, off_f;    // byte offsets of the work buffers
   uint32_t off_geo;                // byte offset of the geometry slot
   uint32_t off_meta;               // byte offset of the tile metadata (variable order)
+  // variable order: the tile list is one run of tiles per order; CTAs
+  // [grp_cta[g], grp_cta[g + 1]) walk run g (order grp_P[g], tiles
+  // [grp_tile[g], grp_tile[g + 1])) and nothing else
+  int ngrp;
+  int grp_P[kMaxP];
+  int grp_tile[kMaxP + 1];
+  int grp_cta[kMaxP + 1];
 };
 
 // L2 prefetch of every input range of tile `ti`.
@@ -588,6 +597,47 @@ __device__ __forceinline__ void produce_geo(const Prm& p, const TileMeta* m, cha
   }
 }
 
+// Compute warps of a CTA that keeps to order P: its tiles t0, t0 + G, ...
+// below t1.  The loop sits inside the order's branch: a loop around the
+// dispatch over all orders made the compiler keep values of every body live
+// across it (spills that no single body has).
+template <int P, int QOFF, int THR, class Prm>
+__device__ __forceinline__ void varp_compute(const Prm& pp, ProducerCtl& ctl, uint64_t* mbar, TileMeta* meta, int t0,
+                                             int t1, int G) {
+  using V = typename std::conditional<pair_lanes(P, THR) == 2, float2, float>::type;
+  const auto& p = pp.k;
+  const int tid = ctl.tid, nc = ctl.nthr;
+  for (int k = 0;; ++k) {
+    const int ti = t0 + k * G;
+    if (ti >= t1) break;
+    const bool ok = mbar_wait(&mbar[k & 1], (k >> 1) & 1);
+    if (named_sync_or(1, nc, !ok)) {
+      if (tid == 0) {
+        *ctl.abort = 1;
+        atomicOr(p.status, kStatusTimeout);
+      }
+      named_arrive(2, nc + 32);
+      return;
+    }
+    ctl.meta = &meta[k & 1];
+    ctl.parity = k & 1;
+    const Tile t = ctl.meta->t;
+    if (!helm_pair_tile<P, P + QOFF, V>(p, ctl, p.tab + std::decay_t<decltype(p)>::Layout::off(P), t)) {
+      if (tid == 0) atomicOr(p.status, kStatusTimeout);
+      return;
+    }
+  }
+}
+
+template <int PLO, int PHI, int QOFF, int THR, class Prm>
+__device__ __forceinline__ void varp_dispatch(int P, const Prm& pp, ProducerCtl& ctl, uint64_t* mbar, TileMeta* meta,
+                                              int t0, int t1, int G) {
+  if constexpr (PLO <= PHI) {
+    if (P == PLO) varp_compute<PLO, QOFF, THR>(pp, ctl, mbar, meta, t0, t1, G);
+    else varp_dispatch<PLO + 1, PHI, QOFF, THR>(P, pp, ctl, mbar, meta, t0, t1, G);
+  }
+}
+
 template <int PLO, int PHI, int QOFF, int REG, int THR>
 __global__ void __maxnreg__(REG) helm_varp_kernel(const __grid_constant__ PairParams<PLO, PHI, QOFF> pp) {
   extern __shared__ __align__(128) char sm[];
@@ -598,8 +648,12 @@ __global__ void __maxnreg__(REG) helm_varp_kernel(const __grid_constant__ PairPa
   TileMeta* meta = reinterpret_cast<TileMeta*>(sm + pp.off_meta);
   const int tid = threadIdx.x;
   const int nc = blockDim.x - 32;                          // compute threads
-  const int G = gridDim.x;
   if (p.skip && *p.skip) return;   // uniform across the grid: nothing started yet
+  // this CTA's run of tiles (one order): tiles t0 + r, t0 + r + G, ... below t1
+  int g = 0;
+  while (g + 1 < pp.ngrp && int(blockIdx.x) >= pp.grp_cta[g + 1]) ++g;
+  const int G = pp.grp_cta[g + 1] - pp.grp_cta[g];
+  const int t0 = pp.grp_tile[g] + int(blockIdx.x) - pp.grp_cta[g], t1 = pp.grp_tile[g + 1];
   if (tid == 0) {
     mbar_init(bar, 1);
     mbar_init(&mbar[0], 1);
@@ -610,43 +664,23 @@ __global__ void __maxnreg__(REG) helm_varp_kernel(const __grid_constant__ PairPa
   __syncthreads();
   if (tid >= nc) {   // producer warp
     const int lane = tid - nc;
-    const int t0 = blockIdx.x;
-    if (t0 < p.n_tiles) {
+    if (t0 < t1) {
       produce_meta<QOFF>(p, &meta[0], &mbar[0], t0, lane);
       produce_geo<QOFF>(p, &meta[0], sm + pp.off_geo, bar, lane);
-      if (t0 + G < p.n_tiles) produce_meta<QOFF>(p, &meta[1], &mbar[1], t0 + G, lane);
+      if (t0 + G < t1) produce_meta<QOFF>(p, &meta[1], &mbar[1], t0 + G, lane);
     }
     for (int k = 0;; ++k) {
       const int ti = t0 + k * G;
-      if (ti >= p.n_tiles) break;
+      if (ti >= t1) break;
       named_sync(2, nc + 32);   // compute warps are past S5 of tile k
       if (*reinterpret_cast<volatile int*>(abort)) break;
-      if (ti + G < p.n_tiles) produce_geo<QOFF>(p, &meta[(k + 1) & 1], sm + pp.off_geo, bar, lane);
-      if (ti + 2 * G < p.n_tiles) produce_meta<QOFF>(p, &meta[k & 1], &mbar[k & 1], ti + 2 * G, lane);
+      if (ti + G < t1) produce_geo<QOFF>(p, &meta[(k + 1) & 1], sm + pp.off_geo, bar, lane);
+      if (ti + 2 * G < t1) produce_meta<QOFF>(p, &meta[k & 1], &mbar[k & 1], ti + 2 * G, lane);
     }
     return;
   }
   ProducerCtl ctl{sm, {pp.off_a, pp.off_c, pp.off_f, pp.off_geo}, bar, 0u, tid, nc, nullptr, abort};
-  for (int k = 0;; ++k) {
-    const int ti = blockIdx.x + k * G;
-    if (ti >= p.n_tiles) break;
-    const bool ok = mbar_wait(&mbar[k & 1], (k >> 1) & 1);
-    if (named_sync_or(1, nc, !ok)) {
-      if (tid == 0) {
-        *abort = 1;
-        atomicOr(p.status, kStatusTimeout);
-      }
-      named_arrive(2, nc + 32);
-      return;
-    }
-    ctl.meta = &meta[k & 1];
-    ctl.parity = k & 1;
-    const Tile t = ctl.meta->t;
-    if (!pair_dispatch<PLO, PHI, QOFF, THR>(t.P, p, ctl, t)) {
-      if (tid == 0) atomicOr(p.status, kStatusTimeout);
-      return;
-    }
-  }
+  varp_dispatch<PLO, PHI, QOFF, THR>(pp.grp_P[g], pp, ctl, mbar, meta, t0, t1, G);
 }
 
 }  // namespace spx

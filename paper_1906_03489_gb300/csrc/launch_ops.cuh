@@ -45,22 +45,83 @@ spx_status launch_pair_reg(const PairParams<PLO, PHI, QOFF>& pp, const PairShape
                             stream, &configured, &mu);
 }
 
-// variable order: compute threads + one producer warp
+// Splits `grid` CTAs among the runs of a variable-order tile list in
+// proportion to their algorithmic bytes (every run gets at least one CTA and
+// no more than its tiles), into grp_cta.
+inline int varp_split_ctas(const TileList& tl, int grid, int* grp_cta) {
+  const int ng = static_cast<int>(tl.grp_P.size());
+  double W = 0.0;
+  for (double b : tl.grp_bytes) W += b;
+  std::vector<int> cnt(ng);
+  int used = 0;
+  for (int g = 0; g < ng; ++g) {
+    const int nt = tl.grp_tile[g + 1] - tl.grp_tile[g];
+    cnt[g] = std::max(1, std::min(nt, static_cast<int>(grid * tl.grp_bytes[g] / std::max(W, 1.0))));
+    used += cnt[g];
+  }
+  // hand out what rounding left over to the runs with the most bytes per CTA
+  while (used < grid) {
+    int best = -1;
+    double bw = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      const int nt = tl.grp_tile[g + 1] - tl.grp_tile[g];
+      if (cnt[g] >= nt) continue;
+      const double w = tl.grp_bytes[g] / cnt[g];
+      if (w > bw) {
+        bw = w;
+        best = g;
+      }
+    }
+    if (best < 0) break;
+    ++cnt[best];
+    ++used;
+  }
+  grp_cta[0] = 0;
+  for (int g = 0; g < ng; ++g) grp_cta[g + 1] = grp_cta[g] + cnt[g];
+  return grp_cta[ng];
+}
+
+// variable order: compute threads + one producer warp; the grid is split
+// among the orders' runs of tiles (PairParams::grp_*)
 template <int PLO, int PHI, int QOFF, int REG, int THR>
-spx_status launch_varp_reg(const PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, const spx_plan* plan,
-                           int n_tiles, cudaStream_t stream) {
+spx_status launch_varp_reg(PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, const spx_plan* plan,
+                           const TileList& tl, cudaStream_t stream) {
   static std::mutex mu;
   static bool configured = false;
-  if (s.nthreads + 32 > 1024) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile needs too many threads");
-  return launch_pair_kernel(helm_varp_kernel<PLO, PHI, QOFF, REG, THR>, pp, s.nthreads + 32, s.smem, plan,
-                            n_tiles, stream, &configured, &mu);
+  auto kern = helm_varp_kernel<PLO, PHI, QOFF, REG, THR>;
+  const int nthreads = s.nthreads + 32;
+  if (nthreads > 1024) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile needs too many threads");
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(plan->max_smem));
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      configured = true;
+    }
+  }
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthreads, s.smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "pair-kernel tile does not fit on an SM");
+  const int ng = static_cast<int>(tl.grp_P.size());
+  if (ng < 1 || ng > kMaxP) return fail(SPX_ERR_UNSUPPORTED, "variable-order tile list has no order runs");
+  pp.ngrp = ng;
+  for (int g = 0; g < ng; ++g) pp.grp_P[g] = tl.grp_P[g];
+  for (int g = 0; g <= ng; ++g) pp.grp_tile[g] = tl.grp_tile[g];
+  const int grid = varp_split_ctas(tl, std::max<int>(ng, nb * plan->num_sms), pp.grp_cta);
+  kern<<<grid, nthreads, s.smem, stream>>>(pp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "Helmholtz kernel launch");
+  return SPX_OK;
 }
 
 // FP32 Helmholtz on hexahedra (helm_pair.cuh).  `stages` of the launch
 // configuration is its L2 prefetch distance in tiles; `nthreads` the number
 // of threads per SM that the register budget must allow: 128 registers up to
 // 512, 96 up to 640, else 80 (uniform order).  Variable-order launches run the
-// producer-warp kernel at 128 registers, orders <= kPairThrVar in pairs.
+// producer-warp kernel at 128 registers; there `nthreads` picks the highest
+// order run in pairs (pair_threshold).
 template <int PLO, int PHI, int QOFF>
 spx_status launch_pair(const LaunchReq& r) {
   const spx_plan* plan = r.plan;
@@ -88,7 +149,7 @@ spx_status launch_pair(const LaunchReq& r) {
   p.skip = r.skip;
   p.lam = r.lam;
   p.n_tiles = tl.n;
-  const int thr = pair_threshold(plan);
+  const int thr = pair_threshold(plan, cfg);
   const PairShape s = pair_shape(plan, cfg, thr);
   if (s.nthreads > 512) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile needs more than 512 threads");
   if (s.smem > plan->max_smem) return fail(SPX_ERR_UNSUPPORTED, "Helmholtz tile does not fit in shared memory");
@@ -104,7 +165,9 @@ spx_status launch_pair(const LaunchReq& r) {
     return launch_pair_reg<PLO, PHI, QOFF, 80, kMaxP>(pp, s, plan, tl.n, r.stream);
   } else {
     pp.off_meta = s.off_meta;
-    return launch_varp_reg<PLO, PHI, QOFF, 128, kPairThrVar>(pp, s, plan, tl.n, r.stream);
+    if (thr == kPairThrVar) return launch_varp_reg<PLO, PHI, QOFF, 128, kPairThrVar>(pp, s, plan, tl, r.stream);
+    if (thr == 6) return launch_varp_reg<PLO, PHI, QOFF, 128, 6>(pp, s, plan, tl, r.stream);
+    return launch_varp_reg<PLO, PHI, QOFF, 128, 8>(pp, s, plan, tl, r.stream);
   }
 }
 

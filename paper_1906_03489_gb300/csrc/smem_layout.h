@@ -157,8 +157,13 @@ inline PairShape pair_shape(const spx_plan* plan, const LaunchCfg& cfg, int thr,
 
 // Orders packed two per thread: all of them in a uniform-order plan; in a
 // variable-order launch (one kernel for every order, registers allocated for
-// the largest body) only the low orders, so that no body spills.
-inline int pair_threshold(const spx_plan* plan) { return plan->uniform ? kMaxP : kPairThrVar; }
+// the largest body) the launch's `nthreads` class picks the highest packed
+// order: <= 512: 5, <= 640: 6, else 8 (pairs of P = 7, 8 spill a little at
+// 128 registers).
+inline int pair_threshold(const spx_plan* plan, const LaunchCfg& cfg) {
+  if (plan->uniform) return kMaxP;
+  return cfg.nthreads <= 512 ? kPairThrVar : (cfg.nthreads <= 640 ? 6 : 8);
+}
 
 inline bool uses_pair_kernel(const spx_plan* plan, int op, int dtype) {
   if ((op == OP_BWD || op == OP_IPROD) && dtype == 1 && plan->dim == 3 && plan->bkind == BK_PARITY && !plan->shape &&

@@ -28,6 +28,11 @@ struct TileList {
   Tile* d = nullptr;   // device
   int n = 0;
   bool dirty = true;
+  // variable order: the list holds one contiguous run of tiles per order
+  // (heaviest order first); run g has order grp_P[g], tiles
+  // [grp_tile[g], grp_tile[g + 1]) and grp_bytes[g] algorithmic bytes
+  std::vector<int> grp_P, grp_tile;
+  std::vector<double> grp_bytes;
 };
 
 }  // namespace spx

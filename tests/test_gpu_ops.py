@@ -127,6 +127,20 @@ def test_variable_order(dim, N, dtype):
         assert np.abs(o.cpu().double().numpy() - r).max() / scale <= TOL[dtype]
 
 
+@pytest.mark.parametrize("nthreads", [512, 640, 768])
+@pytest.mark.parametrize("eb,stages", [(1, 0), (2, 1), (3, 2)])
+def test_variable_order_pair_classes(nthreads, eb, stages):
+    """FP32 variable-order Helmholtz with element pairs up to P = 5, 6 and 8
+    (the launch's threads class), several tile sizes and prefetch depths; each
+    CTA keeps to one order's run of tiles (here runs of a few tiles, fewer
+    than the CTAs an SM's share would give them)."""
+    orders = synth.orders(synth.rng(27), 5 ** 3, 1, 8)
+    c = Case(3, 5, orders=orders, amp=0.05)
+    u, ut = c.coef(28, torch.float32)
+    c.plan.set_tile("helmholtz", torch.float32, eb, nthreads, stages)
+    assert rel_err(spx.helmholtz(c.plan, ut), operators.helmholtz(c.om, u)) <= 1e-5
+
+
 def test_variable_order_equals_uniform_launches():
     """One variable-order launch gives, element by element, what uniform launches give."""
     dim, N = 3, 4

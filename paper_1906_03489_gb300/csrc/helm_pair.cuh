@@ -46,13 +46,6 @@ struct PairParams {
   uint32_t off_a, off_c, off_f;    // byte offsets of the work buffers
   uint32_t off_geo;                // byte offset of the geometry slot
   uint32_t off_meta;               // byte offset of the tile metadata (variable order)
-  // variable order: the tile list is one run of tiles per order; CTAs
-  // [grp_cta[g], grp_cta[g + 1]) walk run g (order grp_P[g], tiles
-  // [grp_tile[g], grp_tile[g + 1])) and nothing else
-  int ngrp;
-  int grp_P[kMaxP];
-  int grp_tile[kMaxP + 1];
-  int grp_cta[kMaxP + 1];
 };
 
 // L2 prefetch of every input range of tile `ti`.
@@ -649,11 +642,9 @@ __global__ void __maxnreg__(REG) helm_varp_kernel(const __grid_constant__ PairPa
   const int tid = threadIdx.x;
   const int nc = blockDim.x - 32;                          // compute threads
   if (p.skip && *p.skip) return;   // uniform across the grid: nothing started yet
-  // this CTA's run of tiles (one order): tiles t0 + r, t0 + r + G, ... below t1
-  int g = 0;
-  while (g + 1 < pp.ngrp && int(blockIdx.x) >= pp.grp_cta[g + 1]) ++g;
-  const int G = pp.grp_cta[g + 1] - pp.grp_cta[g];
-  const int t0 = pp.grp_tile[g] + int(blockIdx.x) - pp.grp_cta[g], t1 = pp.grp_tile[g + 1];
+  // this CTA's run of tiles (one order)
+  const TileRun run = tile_run(p);
+  const int G = run.G, t0 = run.t0, t1 = run.t1;
   if (tid == 0) {
     mbar_init(bar, 1);
     mbar_init(&mbar[0], 1);
@@ -680,7 +671,7 @@ __global__ void __maxnreg__(REG) helm_varp_kernel(const __grid_constant__ PairPa
     return;
   }
   ProducerCtl ctl{sm, {pp.off_a, pp.off_c, pp.off_f, pp.off_geo}, bar, 0u, tid, nc, nullptr, abort};
-  varp_dispatch<PLO, PHI, QOFF, THR>(pp.grp_P[g], pp, ctl, mbar, meta, t0, t1, G);
+  varp_dispatch<PLO, PHI, QOFF, THR>(run.P, pp, ctl, mbar, meta, t0, t1, G);
 }
 
 }  // namespace spx

@@ -99,9 +99,9 @@ struct PairLayout {
   static constexpr int WZ = upm((Q - 1) + Q * (n - 1) + ZS * (n - 1) + 1, Q * Q, M);
 };
 
-// Orders packed two elements per thread in a variable-order launch (measured:
-// with the higher orders in pairs the single kernel's register budget makes
-// their bodies spill; 4 and 5 time alike, 6 and 8 slower).
+// Highest order packed two elements per thread in a variable-order launch by
+// default (measured on 24^3, P = 2..8: pairs up to 5 0.070 ms, up to 6 or 8
+// 0.081 ms; the launch's threads class selects the others).
 constexpr int kPairThrVar = 5;
 
 // Elements per thread of order P in a kernel that packs orders <= thr in pairs.
@@ -190,7 +190,28 @@ struct KParams {
   uint32_t work_base;
   uint32_t work_bytes;     // per work buffer
   uint32_t meta_base;
+  // runs of the tile list, one order each (a uniform plan has one): CTAs
+  // [grp_cta[g], grp_cta[g + 1]) walk run g (order grp_P[g], tiles
+  // [grp_tile[g], grp_tile[g + 1])) and nothing else
+  int ngrp;
+  int grp_P[kMaxP];
+  int grp_tile[kMaxP + 1];
+  int grp_cta[kMaxP + 1];
   T tab[Layout::total];
 };
+
+// This CTA's run of tiles: tiles t0, t0 + G, ... below t1, all of order P.
+struct TileRun {
+  int P, t0, t1, G;
+};
+#ifdef __CUDACC__
+template <class Prm>
+__device__ __forceinline__ TileRun tile_run(const Prm& p) {
+  int g = 0;
+  while (g + 1 < p.ngrp && int(blockIdx.x) >= p.grp_cta[g + 1]) ++g;
+  return TileRun{p.grp_P[g], p.grp_tile[g] + int(blockIdx.x) - p.grp_cta[g], p.grp_tile[g + 1],
+                 p.grp_cta[g + 1] - p.grp_cta[g]};
+}
+#endif
 
 }  // namespace spx

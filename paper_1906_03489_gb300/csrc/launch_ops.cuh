@@ -49,6 +49,11 @@ spx_status launch_pair_reg(const PairParams<PLO, PHI, QOFF>& pp, const PairShape
 // proportion to their algorithmic bytes (every run gets at least one CTA and
 // no more than its tiles), into grp_cta.
 inline int varp_split_ctas(const TileList& tl, int grid, int* grp_cta) {
+  if (tl.grp_P.empty()) {   // uniform order: one run over the whole list
+    grp_cta[0] = 0;
+    grp_cta[1] = std::max(1, std::min(grid, tl.n));
+    return grp_cta[1];
+  }
   const int ng = static_cast<int>(tl.grp_P.size());
   double W = 0.0;
   for (double b : tl.grp_bytes) W += b;
@@ -81,8 +86,29 @@ inline int varp_split_ctas(const TileList& tl, int grid, int* grp_cta) {
   return grp_cta[ng];
 }
 
+// The runs of a launch's tile list into the kernel parameters (one per order
+// present, or one for a uniform plan) and the grid split among them; returns
+// the grid size (0 if the list is malformed).
+template <class KP>
+int set_runs(KP& k, const spx_plan* plan, const TileList& tl, int grid) {
+  if (tl.grp_P.empty()) {
+    k.ngrp = 1;
+    k.grp_P[0] = plan->uP;
+    k.grp_tile[0] = 0;
+    k.grp_tile[1] = tl.n;
+  } else {
+    const int ng = static_cast<int>(tl.grp_P.size());
+    if (ng > kMaxP) return 0;
+    k.ngrp = ng;
+    for (int g = 0; g < ng; ++g) k.grp_P[g] = tl.grp_P[g];
+    for (int g = 0; g <= ng; ++g) k.grp_tile[g] = tl.grp_tile[g];
+    grid = std::max(grid, ng);
+  }
+  return varp_split_ctas(tl, grid, k.grp_cta);
+}
+
 // variable order: compute threads + one producer warp; the grid is split
-// among the orders' runs of tiles (PairParams::grp_*)
+// among the orders' runs of tiles (KParams::grp_*)
 template <int PLO, int PHI, int QOFF, int REG, int THR>
 spx_status launch_varp_reg(PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, const spx_plan* plan,
                            const TileList& tl, cudaStream_t stream) {
@@ -104,12 +130,8 @@ spx_status launch_varp_reg(PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, c
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthreads, s.smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "pair-kernel tile does not fit on an SM");
-  const int ng = static_cast<int>(tl.grp_P.size());
-  if (ng < 1 || ng > kMaxP) return fail(SPX_ERR_UNSUPPORTED, "variable-order tile list has no order runs");
-  pp.ngrp = ng;
-  for (int g = 0; g < ng; ++g) pp.grp_P[g] = tl.grp_P[g];
-  for (int g = 0; g <= ng; ++g) pp.grp_tile[g] = tl.grp_tile[g];
-  const int grid = varp_split_ctas(tl, std::max<int>(ng, nb * plan->num_sms), pp.grp_cta);
+  const int grid = set_runs(pp.k, plan, tl, nb * plan->num_sms);
+  if (grid < 1) return fail(SPX_ERR_UNSUPPORTED, "tile list has no order runs");
   kern<<<grid, nthreads, s.smem, stream>>>(pp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "Helmholtz kernel launch");
@@ -294,7 +316,8 @@ spx_status launch_impl(const LaunchReq& r) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthr, L.total);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "operator tile does not fit on an SM");
-  const int grid = std::min<int64_t>(tl.n, int64_t(nb) * plan->num_sms);
+  const int grid = set_runs(p, plan, tl, nb * plan->num_sms);   // variable order: one order per CTA
+  if (grid < 1) return fail(SPX_ERR_UNSUPPORTED, "tile list has no order runs");
   kern<<<grid, nthr, L.total, r.stream>>>(p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "operator kernel launch");

@@ -1213,58 +1213,20 @@ __device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel)
   else body_diag<T, DIM, P, Q>(tab, c, p.out0, rel);
 }
 
-template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK, class Prm, class Rel>
-__device__ __forceinline__ void dispatch_order(int P, const Prm& p, const Ctx<T>& c, Rel rel) {
-  if constexpr (PLO <= PHI) {
-    if (P == PLO) run_body<T, DIM, OP, PLO, PLO + QOFF, BK>(p, c, rel);
-    else dispatch_order<T, DIM, OP, PLO + 1, PHI, QOFF, BK>(P, p, c, rel);
-  }
-}
-
-// REG: register budget per thread (128 lets a 512-thread block run; the 3D
-// Helmholtz bodies with Q^2 threads per element also come with 72, for more
-// CTAs per SM).
-template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0, int REG = 128>
-__global__ void __maxnreg__(REG) op_kernel(const __grid_constant__ KParams<T, PLO, PHI, QOFF> p) {
-  extern __shared__ __align__(128) char sm[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
-  uint32_t* soff = reinterpret_cast<uint32_t*>(sm + p.meta_base);
-  int64_t* gcoef = reinterpret_cast<int64_t*>(sm + p.meta_base + 5 * kMaxEB * 4);
-  int64_t* gquad = gcoef + kMaxEB;
-  int* tab_order = reinterpret_cast<int*>(gquad + kMaxEB);
-  const int tid = threadIdx.x, nthr = blockDim.x;
+// The tiles of this CTA's run (order P, compile time): tiles t0, t0 + G, ...
+// below t1, through the staging ring.  The loop sits inside the order's
+// branch (op_dispatch): a loop around a dispatch over every order made the
+// compiler keep values of all the bodies live across it (spills that no
+// single body has).
+template <typename T, int DIM, int OP, int P, int QOFF, int BK, class Prm>
+__device__ __forceinline__ void op_run(const Prm& p, char* sm, uint64_t* bars, uint32_t* soff, int64_t* gcoef,
+                                       int64_t* gquad, Ctx<T>& c, int t0, int t1, int G) {
+  constexpr int Q = P + QOFF;
+  const int tid = c.tid, nthr = c.nthr;
   const int S = p.stages;
-  if (p.skip && *p.skip) return;   // uniform across the grid: nothing started yet
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-    fence_barrier_init();
-    *tab_order = -1;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      const int ti = blockIdx.x + s * gridDim.x;
-      if (ti < p.n_tiles) issue_tile<T, DIM, OP, QOFF>(p, sm, bars, s, ti);
-    }
-  }
-  Ctx<T> c;
-  c.sm = sm;
-  for (int w = 0; w < 8; ++w) c.work[w] = reinterpret_cast<T*>(sm + p.work_base + size_t(w) * p.work_bytes);
-  c.soff = soff;
-  c.tab_order = tab_order;
-  c.extra = reinterpret_cast<T*>(sm + p.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8 + 16);
-  c.status = p.status;
-  c.gcoef = gcoef;
-  c.gquad = gquad;
-  c.tid = tid;
-  c.nthr = nthr;
-  c.has_lam = p.lam_f != nullptr;
-  c.has_kap = p.kap_f != nullptr;
-  c.lam = static_cast<T>(p.lam);
-  c.geom_g = (OP == OP_HELM && p.geo_direct) ? p.geom : nullptr;
   for (int k = 0;; ++k) {
-    const int ti = blockIdx.x + k * gridDim.x;
-    if (ti >= p.n_tiles) break;
+    const int ti = t0 + k * G;
+    if (ti >= t1) break;
     const int slot = k % S;
     const bool ok = mbar_wait(&bars[slot], (k / S) & 1);
     if (__syncthreads_or(!ok)) {
@@ -1272,7 +1234,6 @@ __global__ void __maxnreg__(REG) op_kernel(const __grid_constant__ KParams<T, PL
       return;
     }
     const Tile t = p.tiles[ti];
-    const int P = t.P, Q = t.P + QOFF;
     c.ne = t.count;
     // per-tile metadata: element offsets and staged-data offsets
     StreamDesc<T> sd[5];
@@ -1316,16 +1277,70 @@ __global__ void __maxnreg__(REG) op_kernel(const __grid_constant__ KParams<T, PL
     auto rel = [&]() {
       if (!released) {
         released = true;
-        if (tid == 0 && ti + S * gridDim.x < p.n_tiles) {
+        if (tid == 0 && ti + S * G < t1) {
           fence_proxy_async();
-          issue_tile<T, DIM, OP, QOFF>(p, sm, bars, slot, ti + S * gridDim.x);
+          issue_tile<T, DIM, OP, QOFF>(p, sm, bars, slot, ti + S * G);
         }
       }
     };
-    dispatch_order<T, DIM, OP, PLO, PHI, QOFF, BK>(P, p, c, rel);
+    run_body<T, DIM, OP, P, Q, BK>(p, c, rel);
     __syncthreads();
     rel();
   }
+}
+
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK, class Prm>
+__device__ __forceinline__ void op_dispatch(int P, const Prm& p, char* sm, uint64_t* bars, uint32_t* soff,
+                                            int64_t* gcoef, int64_t* gquad, Ctx<T>& c, int t0, int t1, int G) {
+  if constexpr (PLO <= PHI) {
+    if (P == PLO) op_run<T, DIM, OP, PLO, QOFF, BK>(p, sm, bars, soff, gcoef, gquad, c, t0, t1, G);
+    else op_dispatch<T, DIM, OP, PLO + 1, PHI, QOFF, BK>(P, p, sm, bars, soff, gcoef, gquad, c, t0, t1, G);
+  }
+}
+
+// REG: register budget per thread (128 lets a 512-thread block run; the 3D
+// Helmholtz bodies with Q^2 threads per element also come with 72, for more
+// CTAs per SM).  Each CTA walks one run of the tile list (one order).
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK = 0, int REG = 128>
+__global__ void __maxnreg__(REG) op_kernel(const __grid_constant__ KParams<T, PLO, PHI, QOFF> p) {
+  extern __shared__ __align__(128) char sm[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
+  uint32_t* soff = reinterpret_cast<uint32_t*>(sm + p.meta_base);
+  int64_t* gcoef = reinterpret_cast<int64_t*>(sm + p.meta_base + 5 * kMaxEB * 4);
+  int64_t* gquad = gcoef + kMaxEB;
+  int* tab_order = reinterpret_cast<int*>(gquad + kMaxEB);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int S = p.stages;
+  if (p.skip && *p.skip) return;   // uniform across the grid: nothing started yet
+  const TileRun run = tile_run(p);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+    *tab_order = -1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      const int ti = run.t0 + s * run.G;
+      if (ti < run.t1) issue_tile<T, DIM, OP, QOFF>(p, sm, bars, s, ti);
+    }
+  }
+  Ctx<T> c;
+  c.sm = sm;
+  for (int w = 0; w < 8; ++w) c.work[w] = reinterpret_cast<T*>(sm + p.work_base + size_t(w) * p.work_bytes);
+  c.soff = soff;
+  c.tab_order = tab_order;
+  c.extra = reinterpret_cast<T*>(sm + p.meta_base + 5 * kMaxEB * 4 + 2 * kMaxEB * 8 + 16);
+  c.status = p.status;
+  c.gcoef = gcoef;
+  c.gquad = gquad;
+  c.tid = tid;
+  c.nthr = nthr;
+  c.has_lam = p.lam_f != nullptr;
+  c.has_kap = p.kap_f != nullptr;
+  c.lam = static_cast<T>(p.lam);
+  c.geom_g = (OP == OP_HELM && p.geo_direct) ? p.geom : nullptr;
+  op_dispatch<T, DIM, OP, PLO, PHI, QOFF, BK>(run.P, p, sm, bars, soff, gcoef, gquad, c, run.t0, run.t1, run.G);
 }
 
 }  // namespace spx

@@ -90,7 +90,16 @@ inline int varp_split_ctas(const TileList& tl, int grid, int* grp_cta) {
 // present, or one for a uniform plan) and the grid split among them; returns
 // the grid size (0 if the list is malformed).
 template <class KP>
-int set_runs(KP& k, const spx_plan* plan, const TileList& tl, int grid) {
+int set_runs(KP& k, const spx_plan* plan, const TileList& tl, int grid, bool one_run = false) {
+  if (one_run) {   // every CTA walks the whole list (orders mixed, heaviest first)
+    k.ngrp = 1;
+    k.grp_P[0] = 0;
+    k.grp_tile[0] = 0;
+    k.grp_tile[1] = tl.n;
+    k.grp_cta[0] = 0;
+    k.grp_cta[1] = std::max(1, std::min(grid, tl.n));
+    return k.grp_cta[1];
+  }
   if (tl.grp_P.empty()) {
     k.ngrp = 1;
     k.grp_P[0] = plan->uP;
@@ -316,7 +325,8 @@ spx_status launch_impl(const LaunchReq& r) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthr, L.total);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "operator tile does not fit on an SM");
-  const int grid = set_runs(p, plan, tl, nb * plan->num_sms);   // variable order: one order per CTA
+  // variable order: one order per CTA, except FP64 (one run over the mixed list; op_kernel.cuh body_of_order)
+  const int grid = set_runs(p, plan, tl, nb * plan->num_sms, std::is_same_v<T, double> && PLO < PHI);
   if (grid < 1) return fail(SPX_ERR_UNSUPPORTED, "tile list has no order runs");
   kern<<<grid, nthr, L.total, r.stream>>>(p);
   e = cudaGetLastError();

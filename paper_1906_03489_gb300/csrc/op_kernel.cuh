@@ -1218,10 +1218,21 @@ __device__ __forceinline__ void run_body(const Prm& p, const Ctx<T>& c, Rel rel)
 // branch (op_dispatch): a loop around a dispatch over every order made the
 // compiler keep values of all the bodies live across it (spills that no
 // single body has).
-template <typename T, int DIM, int OP, int P, int QOFF, int BK, class Prm>
+// P == 0 (FP64 variable order): the run is the whole tile list, every order
+// in it, and each tile's body is chosen at run time.  The FP64 bodies are
+// bound by the FP64 pipe: there the balance of every CTA walking every order
+// (heaviest first) measured 3-7% faster than one order per CTA, spills and all.
+template <typename T, int DIM, int OP, int PLO, int PHI, int QOFF, int BK, class Prm, class Rel>
+__device__ __forceinline__ void body_of_order(int P, const Prm& p, const Ctx<T>& c, Rel rel) {
+  if constexpr (PLO <= PHI) {
+    if (P == PLO) run_body<T, DIM, OP, PLO, PLO + QOFF, BK>(p, c, rel);
+    else body_of_order<T, DIM, OP, PLO + 1, PHI, QOFF, BK>(P, p, c, rel);
+  }
+}
+
+template <typename T, int DIM, int OP, int P, int QOFF, int BK, class Prm, int PLO = P, int PHI = P>
 __device__ __forceinline__ void op_run(const Prm& p, char* sm, uint64_t* bars, uint32_t* soff, int64_t* gcoef,
                                        int64_t* gquad, Ctx<T>& c, int t0, int t1, int G) {
-  constexpr int Q = P + QOFF;
   const int tid = c.tid, nthr = c.nthr;
   const int S = p.stages;
   for (int k = 0;; ++k) {
@@ -1234,14 +1245,15 @@ __device__ __forceinline__ void op_run(const Prm& p, char* sm, uint64_t* bars, u
       return;
     }
     const Tile t = p.tiles[ti];
+    const int TP = P ? P : t.P, Q = TP + QOFF;   // this tile's order
     c.ne = t.count;
     // per-tile metadata: element offsets and staged-data offsets
     StreamDesc<T> sd[5];
-    const int ns = op_streams<T, DIM, OP>(p, P, Q, sd);
+    const int ns = op_streams<T, DIM, OP>(p, TP, Q, sd);
     char* slotp = sm + p.slot_base + slot * p.slot_bytes;
     for (int j = tid; j < t.count; j += nthr) {
       const int64_t e = elem_id(p, t, j);
-      gcoef[j] = coef_off_of<DIM>(p, e, P);
+      gcoef[j] = coef_off_of<DIM>(p, e, TP);
       gquad[j] = quad_off_of<DIM>(p, e, Q);
 #pragma unroll
       for (int s = 0; s < 5; ++s) {
@@ -1252,7 +1264,7 @@ __device__ __forceinline__ void op_run(const Prm& p, char* sm, uint64_t* bars, u
         char* at;
         if (t.contig && sd[s].whole) {
           const int64_t e0 = elem_id(p, t, 0);
-          const int64_t off0 = sd[s].quad ? quad_off_of<DIM>(p, e0, Q) : coef_off_of<DIM>(p, e0, P);
+          const int64_t off0 = sd[s].quad ? quad_off_of<DIM>(p, e0, Q) : coef_off_of<DIM>(p, e0, TP);
           const T* g0 = sd[s].base + sd[s].mult * off0 + sd[s].boff;
           at = region + (reinterpret_cast<uintptr_t>(g0) & 15) + (g - g0) * sizeof(T);
           // head / tail words of the whole-tile range
@@ -1283,7 +1295,8 @@ __device__ __forceinline__ void op_run(const Prm& p, char* sm, uint64_t* bars, u
         }
       }
     };
-    run_body<T, DIM, OP, P, Q, BK>(p, c, rel);
+    if constexpr (P != 0) run_body<T, DIM, OP, P, P + QOFF, BK>(p, c, rel);
+    else body_of_order<T, DIM, OP, PLO, PHI, QOFF, BK>(TP, p, c, rel);
     __syncthreads();
     rel();
   }
@@ -1340,7 +1353,11 @@ __global__ void __maxnreg__(REG) op_kernel(const __grid_constant__ KParams<T, PL
   c.has_kap = p.kap_f != nullptr;
   c.lam = static_cast<T>(p.lam);
   c.geom_g = (OP == OP_HELM && p.geo_direct) ? p.geom : nullptr;
-  op_dispatch<T, DIM, OP, PLO, PHI, QOFF, BK>(run.P, p, sm, bars, soff, gcoef, gquad, c, run.t0, run.t1, run.G);
+  if constexpr (sizeof(T) == 8 && PLO < PHI)   // FP64 variable order: one run, every order (see body_of_order)
+    op_run<T, DIM, OP, 0, QOFF, BK, KParams<T, PLO, PHI, QOFF>, PLO, PHI>(p, sm, bars, soff, gcoef, gquad, c, run.t0,
+                                                                         run.t1, run.G);
+  else
+    op_dispatch<T, DIM, OP, PLO, PHI, QOFF, BK>(run.P, p, sm, bars, soff, gcoef, gquad, c, run.t0, run.t1, run.G);
 }
 
 }  // namespace spx

@@ -310,6 +310,24 @@ def test_autotune_keeps_results():
     assert rel_err(spx.helmholtz(c.plan, ut), operators.helmholtz(c.om, u)) <= 1e-5
 
 
+def test_autotune_streaming_ops_keeps_results():
+    """The autotuner's search over the FP32 BwdTrans / IProductWRTBase pair
+    kernels (tile, register class, input ring depth; timed after an L2
+    eviction) leaves results at the FP32 bar, and its choice is a valid tile."""
+    c = _case(3, 4, 4, 0.05)
+    u, ut = c.coef(29, torch.float32)
+    f, ft = c.quad(30, torch.float32)
+    q = torch.empty(c.plan.n_quad, dtype=torch.float32, device="cuda")
+    m = torch.empty(c.plan.n_coef, dtype=torch.float32, device="cuda")
+    c.plan.autotune("bwd_trans", torch.float32, ut, q, reps=2)
+    c.plan.autotune("iproduct", torch.float32, ft, m, reps=2)
+    for op in ("bwd_trans", "iproduct"):
+        eb, nt, st = c.plan.get_tile(op, torch.float32, 4)
+        assert 1 <= eb <= 64 and 32 <= nt <= 2048 and 0 <= st <= 4
+    assert rel_err(spx.bwd_trans(c.plan, ut), operators.bwd_trans(c.om, u)) <= 1e-5
+    assert rel_err(spx.iproduct(c.plan, ft), operators.iproduct(c.om, f)) <= 1e-5
+
+
 def test_unaligned_buffers():
     """Element blocks at arbitrary 8-byte offsets (views into larger buffers)."""
     c = _case(3, 3, 3, 0.05)

@@ -656,7 +656,7 @@ def measure_extras(spx, mesh, synth, torch, plans, geoms, coef, stream, hbm_peak
     for dt, sz in ((torch.float32, 4), (torch.float64, 8)):
         uu = torch.tensor(cv, device="cuda", dtype=dt)
         oo = torch.empty_like(uu)
-        pv.autotune("helmholtz", dt, uu, oo, reps=2)
+        pv.autotune("helmholtz", dt, uu, oo, reps=5)
         ms = timed(lambda: spx.helmholtz(pv, uu, out=oo), reps, stream)
         tag = "f32" if dt == torch.float32 else "f64"
         r = roof(ms, nb * sz, nfl, dt == torch.float64, hbm_peak, fp64_peak if dt == torch.float64 else fp32_peak)
@@ -965,7 +965,7 @@ def run_case(a):
             for P, eb in zip(range(2, 9), f[:7]):
                 plan.set_tile("helmholtz", dt, eb, nt, st, order=P)
         else:
-            plan.autotune("helmholtz", dt, u, y, reps=2)
+            plan.autotune("helmholtz", dt, u, y, reps=5)
         spx.helmholtz(plan, u, out=y)   # warm-up (module load, tile lists)
         ms = timed(lambda: spx.helmholtz(plan, u, out=y), max(1, a.steps), stream)
         orders = sorted(set(plan.orders.tolist()))

@@ -197,6 +197,10 @@ struct KParams {
   int grp_P[kMaxP];
   int grp_tile[kMaxP + 1];
   int grp_cta[kMaxP + 1];
+  // layers > 1: grp_cta counts SM slots instead of CTAs; CTA b sits in slot
+  // b mod nslot of layer b / nslot, and run g owns its slots in every layer
+  // (the CTAs a persistent grid places on one SM then share an order)
+  int layers, nslot;
   T tab[Layout::total];
 };
 
@@ -207,10 +211,13 @@ struct TileRun {
 #ifdef __CUDACC__
 template <class Prm>
 __device__ __forceinline__ TileRun tile_run(const Prm& p) {
+  const int b = blockIdx.x;
+  const int slot = p.layers > 1 ? b % p.nslot : b, layer = p.layers > 1 ? b / p.nslot : 0;
   int g = 0;
-  while (g + 1 < p.ngrp && int(blockIdx.x) >= p.grp_cta[g + 1]) ++g;
-  return TileRun{p.grp_P[g], p.grp_tile[g] + int(blockIdx.x) - p.grp_cta[g], p.grp_tile[g + 1],
-                 p.grp_cta[g + 1] - p.grp_cta[g]};
+  while (g + 1 < p.ngrp && slot >= p.grp_cta[g + 1]) ++g;
+  const int width = p.grp_cta[g + 1] - p.grp_cta[g];
+  return TileRun{p.grp_P[g], p.grp_tile[g] + layer * width + slot - p.grp_cta[g], p.grp_tile[g + 1],
+                 width * (p.layers > 1 ? p.layers : 1)};
 }
 #endif
 

@@ -90,7 +90,9 @@ inline int varp_split_ctas(const TileList& tl, int grid, int* grp_cta) {
 // present, or one for a uniform plan) and the grid split among them; returns
 // the grid size (0 if the list is malformed).
 template <class KP>
-int set_runs(KP& k, const spx_plan* plan, const TileList& tl, int grid, bool one_run = false) {
+int set_runs(KP& k, const spx_plan* plan, const TileList& tl, int grid, bool one_run = false, int layers = 1) {
+  k.layers = 0;
+  k.nslot = 0;
   if (one_run) {   // every CTA walks the whole list (orders mixed, heaviest first)
     k.ngrp = 1;
     k.grp_P[0] = 0;
@@ -111,6 +113,12 @@ int set_runs(KP& k, const spx_plan* plan, const TileList& tl, int grid, bool one
     k.ngrp = ng;
     for (int g = 0; g < ng; ++g) k.grp_P[g] = tl.grp_P[g];
     for (int g = 0; g <= ng; ++g) k.grp_tile[g] = tl.grp_tile[g];
+    if (layers > 1 && grid / layers >= ng) {   // split SM slots; every layer repeats the split
+      const int nslot = varp_split_ctas(tl, grid / layers, k.grp_cta);
+      k.layers = layers;
+      k.nslot = nslot;
+      return nslot * layers;
+    }
     grid = std::max(grid, ng);
   }
   return varp_split_ctas(tl, grid, k.grp_cta);
@@ -139,7 +147,7 @@ spx_status launch_varp_reg(PairParams<PLO, PHI, QOFF>& pp, const PairShape& s, c
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nthreads, s.smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "pair-kernel tile does not fit on an SM");
-  const int grid = set_runs(pp.k, plan, tl, nb * plan->num_sms);
+  const int grid = set_runs(pp.k, plan, tl, nb * plan->num_sms, false, nb);
   if (grid < 1) return fail(SPX_ERR_UNSUPPORTED, "tile list has no order runs");
   kern<<<grid, nthreads, s.smem, stream>>>(pp);
   e = cudaGetLastError();
@@ -326,7 +334,8 @@ spx_status launch_impl(const LaunchReq& r) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (nb < 1) return fail(SPX_ERR_UNSUPPORTED, "operator tile does not fit on an SM");
   // variable order: one order per CTA, except FP64 (one run over the mixed list; op_kernel.cuh body_of_order)
-  const int grid = set_runs(p, plan, tl, nb * plan->num_sms, std::is_same_v<T, double> && PLO < PHI);
+  constexpr bool kOneRun = std::is_same_v<T, double> && PLO < PHI;
+  const int grid = set_runs(p, plan, tl, nb * plan->num_sms, kOneRun, kOneRun ? 1 : nb);
   if (grid < 1) return fail(SPX_ERR_UNSUPPORTED, "tile list has no order runs");
   kern<<<grid, nthr, L.total, r.stream>>>(p);
   e = cudaGetLastError();

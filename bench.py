@@ -949,6 +949,27 @@ def run_case(a):
             res[op + "_ms"] = round(timed(fn, max(1, a.steps), stream), 4)
             res[op + "_tile"] = plan.get_tile(op, dt, P)
         print(json.dumps(res), flush=True)
+    elif a.case == "collapsed":
+        # Helmholtz on a collapsed-element workload (--workload prism3d_24_p4 | tet3d_16_p4 | tri2d_128_p4)
+        w = synth.WORKLOADS[a.workload]
+        N, P, shape, d = w["N"], w["P"], w["shape"], w["dim"]
+        plan = spx.Plan(d, (6 if shape == "tet" else 2) * N ** d, order=P, shape=shape)
+        g = spx.geom_factors(plan, mesh.collapsed_vertices(shape, N), want_xq=False)
+        plan.set_geometry(torch.float64, g["geom"], g["dxi"])
+        plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])
+        dt = torch.float64 if a.precision == "f64" else torch.float32
+        u = torch.tensor(synth.uniform(synth.rng(w["seed"]), plan.n_coef), device="cuda", dtype=dt)
+        y = torch.empty_like(u)
+        tile = a.tile64 if dt == torch.float64 else a.tile
+        if tile:
+            eb, nt, st = (int(x) for x in tile.split(","))
+            plan.set_tile("helmholtz", dt, eb, nt, st)
+        else:
+            plan.autotune("helmholtz", dt, u, y, reps=3)
+        spx.helmholtz(plan, u, out=y)   # warm-up
+        ms = timed(lambda: spx.helmholtz(plan, u, out=y), max(1, a.steps), stream)
+        print(json.dumps({"case": "collapsed", "workload": a.workload, "dtype": str(dt), "ms": round(ms, 4),
+                          "tile": plan.get_tile("helmholtz", dt, P)}), flush=True)
     elif a.case == "peaks":
         print(json.dumps({"case": "peaks", "fp_peaks": fp_peaks(torch)}), flush=True)
     elif a.case == "varp":
@@ -1063,8 +1084,9 @@ def main():
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--case", default="bench", choices=["bench", "cg", "varp", "helm", "ops", "peaks"],
-                    help="bench: the benchmark line; cg / varp / helm / ops / peaks: one short run for profiling")
+    ap.add_argument("--case", default="bench", choices=["bench", "cg", "varp", "helm", "ops", "collapsed", "peaks"],
+                    help="bench: the benchmark line; cg / varp / helm / ops / collapsed / peaks: one short run "
+                         "for profiling")
     ap.add_argument("--precision", default="f32_reliable",
                     help="cg: f64 | f32_refine | f32_reliable; varp, helm: f32 | f64")
     ap.add_argument("--cg-maxit", type=int, default=30)

@@ -34,6 +34,7 @@
 #include <mutex>
 #include <vector>
 
+#include "device_common.cuh"
 #include "spx_internal.h"
 
 namespace spx {
@@ -349,6 +350,20 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
     const Tile t = p.tiles[ti];
     const int ne = t.count;
     const int64_t e0 = t.first;
+    // the next tile's inputs and geometric factors into L2 while this one runs
+    // (its tile load and pointwise reads then wait on L2, not HBM)
+    if (tid == 0 && ti + int(gridDim.x) < p.n_tiles) {
+      const Tile tn = p.tiles[ti + gridDim.x];
+      const int64_t in_len = (OP == OP_BWD || OP == OP_HELM) ? NM : NQ;
+      prefetch_l2(p.in0 + tn.first * in_len, uint64_t(tn.count) * in_len * sizeof(T));
+      if (OP == OP_IPROD) {   // JW only
+        for (int j = 0; j < tn.count; ++j)
+          prefetch_l2(p.geom + ((tn.first + j) * NFG + NFG - 1) * int64_t(NQ), uint64_t(NQ) * sizeof(T));
+      } else if (OP != OP_BWD) {
+        const int64_t g_len = OP == OP_DERIV ? int64_t(DIM) * DIM * NQ : int64_t(NFG) * NQ;
+        prefetch_l2(p.geom + tn.first * g_len, uint64_t(tn.count) * g_len * sizeof(T));
+      }
+    }
     if constexpr (OP == OP_BWD || OP == OP_HELM) {
       load_tile(p.in0 + e0 * NM, b.C, ne * NM);
       __syncthreads();

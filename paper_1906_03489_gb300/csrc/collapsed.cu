@@ -32,6 +32,7 @@
 // tile's elements, outputs are stored straight to HBM.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -91,13 +92,80 @@ struct CLayout {
   static constexpr int tables = Q * n + 2 * n * Q * n + 2 * Q * Q + (2 * nt + 2);
 };
 
+// ---- values: one element (T) or an element pair (float2, FP32) --------------
+// FP32 kernels hold every value as a float2 of the same entry of two elements
+// of the tile (pair p = elements p and p + npair), so each FFMA2 does two
+// elements' work; the 1D tables stay scalar (a broadcast operand).
+template <typename T>
+struct ValueOf {
+  using type = T;
+};
+template <>
+struct ValueOf<float> {
+  using type = float2;
+};
+
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float2 vfma(float a, float2 x, float2 c) { return __ffma2_rn(make_float2(a, a), x, c); }
+__device__ __forceinline__ float2 vfma(float2 x, float a, float2 c) { return __ffma2_rn(x, make_float2(a, a), c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float2 vmul(float a, float2 x) { return __fmul2_rn(make_float2(a, a), x); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <typename V>
+__device__ __forceinline__ V vzero() {
+  if constexpr (std::is_same_v<V, float2>) return make_float2(0.f, 0.f);
+  else return V(0);
+}
+template <typename V>
+__device__ __forceinline__ V vfill(double a) {
+  if constexpr (std::is_same_v<V, float2>) return make_float2(float(a), float(a));
+  else return V(a);
+}
+
+// Where the values of (pair-)element e of a tile live in global memory: the
+// elements first + e and, for pairs, first + e + npair (if below count).
+struct PairMap {
+  int64_t first;
+  int npair, count;
+};
+
+template <typename T>
+__device__ __forceinline__ typename ValueOf<T>::type vload(const T* g, int64_t stride, const PairMap& pm, int e,
+                                                           int64_t off) {
+  if constexpr (std::is_same_v<T, double>) {
+    return g[(pm.first + e) * stride + off];
+  } else {
+    const float x = __ldg(g + (pm.first + e) * stride + off);
+    const float y = e + pm.npair < pm.count ? __ldg(g + (pm.first + e + pm.npair) * stride + off) : 0.f;
+    return make_float2(x, y);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T* g, int64_t stride, const PairMap& pm, int e, int64_t off,
+                                       typename ValueOf<T>::type v) {
+  if constexpr (std::is_same_v<T, double>) {
+    g[(pm.first + e) * stride + off] = v;
+  } else {
+    g[(pm.first + e) * stride + off] = v.x;
+    if (e + pm.npair < pm.count) g[(pm.first + e + pm.npair) * stride + off] = v.y;
+  }
+}
+
+// shared-memory carve-up: the tables (T, then the tet mode tables as ints,
+// rounded up to an even count of words) and the (pair-)elements' buffers (V)
 template <typename T, int SHAPE, int P>
 struct Bufs {
   using L = CLayout<SHAPE, P>;
-  T *B1, *Bb, *Bc, *D1, *D2, *C, *F, *H, *U, *G0, *G1, *G2, *V;
+  using V = typename ValueOf<T>::type;
+  T *B1, *Bb, *Bc, *D1, *D2;
+  V *C, *F, *H, *U, *G0, *G1, *G2, *Vb;
   int* toff;   // [nt + 1]
   int* tdeg;   // [nt]
-  __device__ Bufs(T* sm, int eb) {
+  static constexpr int table_words = (L::tables + 1) & ~1;
+  __device__ Bufs(T* sm, int npe) {
     B1 = sm;
     Bb = B1 + L::Q * L::n;
     Bc = Bb + L::n * L::Q * L::n;
@@ -105,43 +173,43 @@ struct Bufs {
     D2 = D1 + L::Q * L::Q;
     toff = reinterpret_cast<int*>(D2 + L::Q * L::Q);
     tdeg = toff + L::nt + 1;
-    C = D2 + L::Q * L::Q + (2 * L::nt + 2);
-    F = C + eb * L::NM;
-    H = F + eb * L::NF;
-    U = H + eb * L::NH;
-    G0 = U + eb * L::NQ;
-    G1 = G0 + eb * L::NQ;
-    G2 = G1 + eb * L::NQ;
-    V = G2 + eb * L::NQ;
+    C = reinterpret_cast<V*>(sm + table_words);
+    F = C + npe * L::NM;
+    H = F + npe * L::NF;
+    U = H + npe * L::NH;
+    G0 = U + npe * L::NQ;
+    G1 = G0 + npe * L::NQ;
+    G2 = G1 + npe * L::NQ;
+    Vb = G2 + npe * L::NQ;
   }
 };
 
 // ---- collapsed-direction stages ------------------------------------------
 // forward: F[e][.. p ..][k] = sum_q C[e][mode(p, q)] Bb[p][k][q] (+ the collapsed vertex in row P);
 // `outer` = the number of leading mode blocks (1 triangle, n prism: mode a + n m).
-template <typename T, int P, int OUTER>
-__device__ __forceinline__ void stage_b_fwd(const T* C, T* F, const T* Bb, int ne, int tid, int nthr) {
+template <typename T, typename V, int P, int OUTER>
+__device__ __forceinline__ void stage_b_fwd(const V* C, V* F, const T* Bb, int ne, int tid, int nthr) {
   constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
   constexpr int items = OUTER * n * Q;
   for (int w = tid; w < ne * items; w += nthr) {
     const int e = w / items, r = w - e * items;
     const int a = r % OUTER, pk = r / OUTER;     // a fastest
     const int p = pk % n, k = pk / n;
-    const T* c = C + e * OUTER * nt + a;         // mode m at c[OUTER * m]
+    const V* c = C + e * OUTER * nt + a;         // mode m at c[OUTER * m]
     const T* b = Bb + (p * Q + k) * n;
     const int o = Tri<P>::off(p), m = Tri<P>::cnt(p);
-    T acc = T(0);
+    V acc = vzero<V>();
 #pragma unroll
     for (int q = 0; q < n; ++q)
-      if (q < m) acc = fma(c[OUTER * (o + q)], b[q], acc);
-    if (p == P) acc = fma(c[OUTER * P], Bb[k * n + P], acc);   // collapsed vertex (0, P)
+      if (q < m) acc = vfma(c[OUTER * (o + q)], b[q], acc);
+    if (p == P) acc = vfma(c[OUTER * P], Bb[k * n + P], acc);   // collapsed vertex (0, P)
     F[e * OUTER * n * Q + a + OUTER * (p + n * k)] = acc;
   }
 }
 
 // transposed: out[e][mode(p, q)] = sum_k Bb[p][k][q] F[e][.. p ..][k] (+ row P for the collapsed vertex)
-template <typename T, int P, int OUTER>
-__device__ __forceinline__ void stage_b_bwd(const T* F, T* out, int64_t e_base, const T* Bb, int ne, int tid,
+template <typename T, typename V, int P, int OUTER>
+__device__ __forceinline__ void stage_b_bwd(const V* F, T* out, const PairMap& pm, const T* Bb, int ne, int tid,
                                             int nthr) {
   constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
   constexpr int items = OUTER * nt;
@@ -153,24 +221,24 @@ __device__ __forceinline__ void stage_b_bwd(const T* F, T* out, int64_t e_base, 
     for (int pp = 1; pp <= P; ++pp)
       if (mi >= Tri<P>::off(pp)) p = pp;
     const int q = mi - Tri<P>::off(p);
-    const T* f = F + e * OUTER * n * Q + a + OUTER * p;
-    T acc = T(0);
+    const V* f = F + e * OUTER * n * Q + a + OUTER * p;
+    V acc = vzero<V>();
 #pragma unroll
-    for (int k = 0; k < Q; ++k) acc = fma(Bb[(p * Q + k) * n + q], f[OUTER * n * k], acc);
+    for (int k = 0; k < Q; ++k) acc = vfma(f[OUTER * n * k], Bb[(p * Q + k) * n + q], acc);
     if (p == 0 && q == P) {   // collapsed vertex: also row P
-      const T* fP = F + e * OUTER * n * Q + a + OUTER * P;
+      const V* fP = F + e * OUTER * n * Q + a + OUTER * P;
 #pragma unroll
-      for (int k = 0; k < Q; ++k) acc = fma(Bb[k * n + P], fP[OUTER * n * k], acc);
+      for (int k = 0; k < Q; ++k) acc = vfma(fP[OUTER * n * k], Bb[k * n + P], acc);
     }
-    out[(e_base + e) * OUTER * nt + r] = acc;
+    vstore(out, OUTER * nt, pm, e, r, acc);
   }
 }
 
 // ---- tetrahedra: the eta3 stage over the triangle modes ---------------------
 // forward: F[e][m][k3] = sum_r C[e][toff[m] + r] Bc[k_m][k3][r]
 //          (+ the apex coefficient for the three triangle vertex modes, whose sum is 1)
-template <typename T, int P>
-__device__ __forceinline__ void stage_c_fwd(const T* C, T* F, const T* Bc, const int* toff, const int* tdeg, int ne,
+template <typename T, typename V, int P>
+__device__ __forceinline__ void stage_c_fwd(const V* C, V* F, const T* Bc, const int* toff, const int* tdeg, int ne,
                                             int tid, int nthr) {
   constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm, NM = (P + 1) * (P + 2) * (P + 3) / 6;
   constexpr int items = nt * Q;
@@ -178,40 +246,40 @@ __device__ __forceinline__ void stage_c_fwd(const T* C, T* F, const T* Bc, const
     const int e = w / items, r0 = w - e * items;
     const int m = r0 % nt, k3 = r0 / nt;
     const int k = tdeg[m], o = toff[m];
-    const T* c = C + e * NM;
+    const V* c = C + e * NM;
     const T* b = Bc + (k * Q + k3) * n;
-    T acc = T(0);
+    V acc = vzero<V>();
 #pragma unroll
     for (int r = 0; r < n; ++r)
-      if (r <= P - k) acc = fma(c[o + r], b[r], acc);
-    if (m == 0 || m == P || m == Tri<P>::off(P)) acc = fma(c[NM - 1], Bc[k3 * n], acc);   // apex
+      if (r <= P - k) acc = vfma(c[o + r], b[r], acc);
+    if (m == 0 || m == P || m == Tri<P>::off(P)) acc = vfma(c[NM - 1], Bc[k3 * n], acc);   // apex
     F[e * nt * Q + m + nt * k3] = acc;
   }
 }
 
 // forward, eta2: H[e][p][j][k3] = sum_q F[e][(p, q)][k3] Bb[p][j][q] (+ row P for the triangle's collapsed vertex)
-template <typename T, int P>
-__device__ __forceinline__ void stage_tb_fwd(const T* F, T* H, const T* Bb, int ne, int tid, int nthr) {
+template <typename T, typename V, int P>
+__device__ __forceinline__ void stage_tb_fwd(const V* F, V* H, const T* Bb, int ne, int tid, int nthr) {
   constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
   constexpr int items = n * Q * Q;
   for (int w = tid; w < ne * items; w += nthr) {
     const int e = w / items, r0 = w - e * items;
     const int p = r0 % n, j = (r0 / n) % Q, k3 = r0 / (n * Q);
-    const T* f = F + e * nt * Q + nt * k3;
+    const V* f = F + e * nt * Q + nt * k3;
     const T* b = Bb + (p * Q + j) * n;
     const int o = Tri<P>::off(p), mc = Tri<P>::cnt(p);
-    T acc = T(0);
+    V acc = vzero<V>();
 #pragma unroll
     for (int q = 0; q < n; ++q)
-      if (q < mc) acc = fma(f[o + q], b[q], acc);
-    if (p == P) acc = fma(f[P], Bb[j * n + P], acc);
+      if (q < mc) acc = vfma(f[o + q], b[q], acc);
+    if (p == P) acc = vfma(f[P], Bb[j * n + P], acc);
     H[e * n * Q * Q + r0] = acc;
   }
 }
 
 // transposed, eta2: F[e][(p, q)][k3] = sum_j Bb[p][j][q] H[e][p][j][k3] (+ row P into (0, P))
-template <typename T, int P>
-__device__ __forceinline__ void stage_tb_bwd(const T* H, T* F, const T* Bb, int ne, int tid, int nthr) {
+template <typename T, typename V, int P>
+__device__ __forceinline__ void stage_tb_bwd(const V* H, V* F, const T* Bb, int ne, int tid, int nthr) {
   constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm;
   constexpr int items = nt * Q;
   for (int w = tid; w < ne * items; w += nthr) {
@@ -222,14 +290,14 @@ __device__ __forceinline__ void stage_tb_bwd(const T* H, T* F, const T* Bb, int 
     for (int pp = 1; pp <= P; ++pp)
       if (mi >= Tri<P>::off(pp)) p = pp;
     const int q = mi - Tri<P>::off(p);
-    const T* h = H + e * n * Q * Q + p + n * Q * k3;
-    T acc = T(0);
+    const V* h = H + e * n * Q * Q + p + n * Q * k3;
+    V acc = vzero<V>();
 #pragma unroll
-    for (int j = 0; j < Q; ++j) acc = fma(Bb[(p * Q + j) * n + q], h[n * j], acc);
+    for (int j = 0; j < Q; ++j) acc = vfma(h[n * j], Bb[(p * Q + j) * n + q], acc);
     if (p == 0 && q == P) {
-      const T* hP = H + e * n * Q * Q + P + n * Q * k3;
+      const V* hP = H + e * n * Q * Q + P + n * Q * k3;
 #pragma unroll
-      for (int j = 0; j < Q; ++j) acc = fma(Bb[j * n + P], hP[n * j], acc);
+      for (int j = 0; j < Q; ++j) acc = vfma(hP[n * j], Bb[j * n + P], acc);
     }
     F[e * nt * Q + mi + nt * k3] = acc;
   }
@@ -237,27 +305,28 @@ __device__ __forceinline__ void stage_tb_bwd(const T* H, T* F, const T* Bb, int 
 
 // transposed, eta3: out[e][toff[m] + r] = sum_k3 Bc[k_m][k3][r] F[e][m][k3]; the apex
 // collects the three triangle vertex modes against (1 + z)/2
-template <typename T, int P>
-__device__ __forceinline__ void stage_c_bwd(const T* F, T* out, int64_t e_base, const T* Bc, const int* toff,
+template <typename T, typename V, int P>
+__device__ __forceinline__ void stage_c_bwd(const V* F, T* out, const PairMap& pm, const T* Bc, const int* toff,
                                             const int* tdeg, int ne, int tid, int nthr) {
   constexpr int n = P + 1, Q = P + 2, nt = Tri<P>::nm, NM = (P + 1) * (P + 2) * (P + 3) / 6;
   for (int w = tid; w < ne * NM; w += nthr) {
     const int e = w / NM, mi = w - e * NM;
-    const T* f = F + e * nt * Q;
-    T acc = T(0);
+    const V* f = F + e * nt * Q;
+    V acc = vzero<V>();
     if (mi == NM - 1) {
       const int v1 = P, v2 = Tri<P>::off(P);
 #pragma unroll
-      for (int k3 = 0; k3 < Q; ++k3) acc = fma(Bc[k3 * n], f[nt * k3] + f[v1 + nt * k3] + f[v2 + nt * k3], acc);
+      for (int k3 = 0; k3 < Q; ++k3)
+        acc = vfma(vadd(vadd(f[nt * k3], f[v1 + nt * k3]), f[v2 + nt * k3]), Bc[k3 * n], acc);
     } else {
       int m = 0;
       for (int mm = 1; mm < nt; ++mm)
         if (mi >= toff[mm]) m = mm;
       const int r = mi - toff[m], k = tdeg[m];
 #pragma unroll
-      for (int k3 = 0; k3 < Q; ++k3) acc = fma(Bc[(k * Q + k3) * n + r], f[m + nt * k3], acc);
+      for (int k3 = 0; k3 < Q; ++k3) acc = vfma(f[m + nt * k3], Bc[(k * Q + k3) * n + r], acc);
     }
-    out[(e_base + e) * NM + mi] = acc;
+    vstore(out, NM, pm, e, mi, acc);
   }
 }
 
@@ -270,13 +339,15 @@ __device__ __forceinline__ void stage_c_bwd(const T* F, T* out, int64_t e_base, 
 // constant-bank operand of the FMA, no load per multiply-add); FP64 kernels
 // pass the shared-memory copy (a broadcast load per multiply-add, hidden by
 // the FP64 pipe; constant-bank FP64 operands made the compiler hold many
-// table values in registers and spill).
-template <int AX, int N0, int N1, int N2, int M, bool TR, bool ACC, typename T>
-__device__ __forceinline__ void stage_dense(const T* x, T* y, const T* A, int ne, int tid, int nthr,
-                                            int64_t ystride, int64_t ybase) {
+// table values in registers and spill).  OUT_G: y is the operator's output in
+// global memory, written through the pair map.
+template <int AX, int N0, int N1, int N2, int M, bool TR, bool ACC, bool OUT_G = false, typename T, typename V,
+          typename Y>
+__device__ __forceinline__ void stage_dense(const V* x, Y* y, const T* A, int ne, int tid, int nthr,
+                                            const PairMap* pm = nullptr) {
   constexpr int NA = AX == 0 ? N0 : (AX == 1 ? N1 : N2);
   constexpr int O0 = AX == 0 ? M : N0, O1 = AX == 1 ? M : N1, O2 = AX == 2 ? M : N2;
-  constexpr int XS = N0 * N1 * N2;
+  constexpr int XS = N0 * N1 * N2, YS = O0 * O1 * O2;
   constexpr int SA = AX == 0 ? 1 : (AX == 1 ? N0 : N0 * N1);
   constexpr int SO = AX == 0 ? 1 : (AX == 1 ? O0 : O0 * O1);
   constexpr int NP = XS / NA;   // pencils per element
@@ -286,48 +357,62 @@ __device__ __forceinline__ void stage_dense(const T* x, T* y, const T* A, int ne
     const int i0 = AX == 0 ? 0 : r % N0;
     const int i1 = AX == 1 ? 0 : (AX == 0 ? r % N1 : (r / N0) % N1);
     const int i2 = AX == 2 ? 0 : (AX == 0 ? r / N1 : r / N0);
-    const T* xe = x + e * XS + i0 + N0 * (i1 + N1 * i2);
-    T* yo = y + ybase + e * ystride + i0 + O0 * (i1 + O1 * i2);
-    T v[NA];
+    const V* xe = x + e * XS + i0 + N0 * (i1 + N1 * i2);
+    const int yo = i0 + O0 * (i1 + O1 * i2);
+    V v[NA];
 #pragma unroll
     for (int c = 0; c < NA; ++c) v[c] = xe[c * SA];
+    auto put = [&](int m, V acc) {
+      if constexpr (OUT_G) {
+        vstore(y, YS, *pm, e, yo + m * SO, acc);
+      } else {
+        V* ye = y + e * YS + yo + m * SO;
+        if (ACC) *ye = vadd(*ye, acc);
+        else *ye = acc;
+      }
+    };
     if constexpr (sizeof(T) == 4) {   // A in the parameter block: every index a constant
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        T acc = (TR ? A[m] : A[m * NA]) * v[0];
+        V acc = vmul(TR ? A[m] : A[m * NA], v[0]);
 #pragma unroll
-        for (int c = 1; c < NA; ++c) acc = fma(TR ? A[c * M + m] : A[m * NA + c], v[c], acc);
-        if (ACC) yo[m * SO] += acc;
-        else yo[m * SO] = acc;
+        for (int c = 1; c < NA; ++c) acc = vfma(TR ? A[c * M + m] : A[m * NA + c], v[c], acc);
+        put(m, acc);
       }
     } else {   // A in shared memory: one output at a time keeps the table loads few
 #pragma unroll 1
       for (int m = 0; m < M; ++m) {
-        T acc = (TR ? A[m] : A[m * NA]) * v[0];
+        V acc = vmul(TR ? A[m] : A[m * NA], v[0]);
 #pragma unroll
-        for (int c = 1; c < NA; ++c) acc = fma(TR ? A[c * M + m] : A[m * NA + c], v[c], acc);
-        if (ACC) yo[m * SO] += acc;
-        else yo[m * SO] = acc;
+        for (int c = 1; c < NA; ++c) acc = vfma(TR ? A[c * M + m] : A[m * NA + c], v[c], acc);
+        put(m, acc);
       }
     }
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void load_tile(const T* g, T* s, int count) {
-  for (int i = threadIdx.x; i < count; i += blockDim.x) s[i] = g[i];
+// a tile's inputs (len values per element, consecutive elements) into the
+// (pair-)element buffer s
+template <typename T, typename V>
+__device__ __forceinline__ void load_tile(const T* g, V* s, int len, const PairMap& pm) {
+  for (int i = threadIdx.x; i < pm.npair * len; i += blockDim.x) {
+    const int e = i / len;
+    s[i] = vload(g, len, pm, e, i - e * len);
+  }
 }
 
 // ---- the kernel -------------------------------------------------------------
-// OP: OP_BWD, OP_IPROD, OP_DERIV, OP_HELM.
+// OP: OP_BWD, OP_IPROD, OP_DERIV, OP_HELM.  FP32: element pairs (ValueOf).
 template <typename T, int SHAPE, int OP, int P>
 __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ CParams<T, P> p) {
   using L = CLayout<SHAPE, P>;
+  using V = typename ValueOf<T>::type;
+  constexpr int LN = std::is_same_v<V, T> ? 1 : 2;   // elements per value
   constexpr int n = L::n, Q = L::Q, nt = L::nt, NQ = L::NQ, NM = L::NM;
   constexpr int DIM = SHAPE == kTri ? 2 : 3;
   constexpr int NFG = DIM == 3 ? 7 : 4;
   extern __shared__ __align__(16) unsigned char csm[];
-  Bufs<T, SHAPE, P> b(reinterpret_cast<T*>(csm), p.eb);
+  Bufs<T, SHAPE, P> b(reinterpret_cast<T*>(csm), (p.eb + LN - 1) / LN);
   const int tid = threadIdx.x, nthr = blockDim.x;
   // tables of the dense stages (see stage_dense)
   constexpr bool kParamTab = sizeof(T) == 4;
@@ -348,8 +433,8 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
   __syncthreads();
   for (int ti = blockIdx.x; ti < p.n_tiles; ti += gridDim.x) {
     const Tile t = p.tiles[ti];
-    const int ne = t.count;
-    const int64_t e0 = t.first;
+    const int ne = (t.count + LN - 1) / LN;   // (pair-)elements of the tile
+    const PairMap pm{t.first, ne, t.count};
     // the next tile's inputs and geometric factors into L2 while this one runs
     // (its tile load and pointwise reads then wait on L2, not HBM)
     if (tid == 0 && ti + int(gridDim.x) < p.n_tiles) {
@@ -365,60 +450,62 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
       }
     }
     if constexpr (OP == OP_BWD || OP == OP_HELM) {
-      load_tile(p.in0 + e0 * NM, b.C, ne * NM);
+      load_tile(p.in0, b.C, NM, pm);
       __syncthreads();
       // collapsed direction, then the tensor directions -> U (or straight to HBM)
-      T* dst = OP == OP_BWD ? p.out0 : b.U;
-      const int64_t dbase = OP == OP_BWD ? e0 * NQ : 0;
+      constexpr bool G = OP == OP_BWD;
       if constexpr (SHAPE == kTri) {
-        stage_b_fwd<T, P, 1>(b.C, b.F, b.Bb, ne, tid, nthr);
+        stage_b_fwd<T, V, P, 1>(b.C, b.F, b.Bb, ne, tid, nthr);
         __syncthreads();
-        stage_dense<0, n, Q, 1, Q, false, false>(b.F, dst, tB1, ne, tid, nthr, NQ, dbase);   // F[p][j] -> u[i][j]
+        if constexpr (G) stage_dense<0, n, Q, 1, Q, false, false, true>(b.F, p.out0, tB1, ne, tid, nthr, &pm);
+        else stage_dense<0, n, Q, 1, Q, false, false>(b.F, b.U, tB1, ne, tid, nthr);   // F[p][j] -> u[i][j]
       } else if constexpr (SHAPE == kTet) {
-        stage_c_fwd<T, P>(b.C, b.F, b.Bc, b.toff, b.tdeg, ne, tid, nthr);                     // F[m][k3]
+        stage_c_fwd<T, V, P>(b.C, b.F, b.Bc, b.toff, b.tdeg, ne, tid, nthr);   // F[m][k3]
         __syncthreads();
-        stage_tb_fwd<T, P>(b.F, b.H, b.Bb, ne, tid, nthr);                                     // H[p][j][k3]
+        stage_tb_fwd<T, V, P>(b.F, b.H, b.Bb, ne, tid, nthr);   // H[p][j][k3]
         __syncthreads();
-        stage_dense<0, n, Q, Q, Q, false, false>(b.H, dst, tB1, ne, tid, nthr, NQ, dbase);   // u[i][j][k3]
+        if constexpr (G) stage_dense<0, n, Q, Q, Q, false, false, true>(b.H, p.out0, tB1, ne, tid, nthr, &pm);
+        else stage_dense<0, n, Q, Q, Q, false, false>(b.H, b.U, tB1, ne, tid, nthr);   // u[i][j][k3]
       } else {
-        stage_b_fwd<T, P, n>(b.C, b.F, b.Bb, ne, tid, nthr);                                 // F[a][p][k]
+        stage_b_fwd<T, V, P, n>(b.C, b.F, b.Bb, ne, tid, nthr);   // F[a][p][k]
         __syncthreads();
-        stage_dense<1, n, n, Q, Q, false, false>(b.F, b.H, tB1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
+        stage_dense<1, n, n, Q, Q, false, false>(b.F, b.H, tB1, ne, tid, nthr);   // H[a][j][k]
         __syncthreads();
-        stage_dense<0, n, Q, Q, Q, false, false>(b.H, dst, tB1, ne, tid, nthr, NQ, dbase);     // u[i][j][k]
+        if constexpr (G) stage_dense<0, n, Q, Q, Q, false, false, true>(b.H, p.out0, tB1, ne, tid, nthr, &pm);
+        else stage_dense<0, n, Q, Q, Q, false, false>(b.H, b.U, tB1, ne, tid, nthr);   // u[i][j][k]
       }
       __syncthreads();
     } else {
-      load_tile(p.in0 + e0 * NQ, OP == OP_DERIV ? b.U : b.V, ne * NQ);
+      load_tile(p.in0, OP == OP_DERIV ? b.U : b.Vb, NQ, pm);
       __syncthreads();
     }
     if constexpr (OP == OP_DERIV || OP == OP_HELM) {
       // gradient along the collapsed directions: G0, G1 (, G2)
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, Q, false, false>(b.U, b.G0, tD1, ne, tid, nthr, NQ, 0);
-        stage_dense<1, Q, Q, 1, Q, false, false>(b.U, b.G1, tD2, ne, tid, nthr, NQ, 0);
+        stage_dense<0, Q, Q, 1, Q, false, false>(b.U, b.G0, tD1, ne, tid, nthr);
+        stage_dense<1, Q, Q, 1, Q, false, false>(b.U, b.G1, tD2, ne, tid, nthr);
       } else {   // eta2 on GLL points (prism) or Gauss-Radau points (tetrahedron)
-        stage_dense<0, Q, Q, Q, Q, false, false>(b.U, b.G0, tD1, ne, tid, nthr, NQ, 0);
-        stage_dense<1, Q, Q, Q, Q, false, false>(b.U, b.G1, SHAPE == kTet ? tD2 : tD1, ne, tid, nthr, NQ, 0);
-        stage_dense<2, Q, Q, Q, Q, false, false>(b.U, b.G2, tD2, ne, tid, nthr, NQ, 0);
+        stage_dense<0, Q, Q, Q, Q, false, false>(b.U, b.G0, tD1, ne, tid, nthr);
+        stage_dense<1, Q, Q, Q, Q, false, false>(b.U, b.G1, SHAPE == kTet ? tD2 : tD1, ne, tid, nthr);
+        stage_dense<2, Q, Q, Q, Q, false, false>(b.U, b.G2, tD2, ne, tid, nthr);
       }
       __syncthreads();
     }
     if constexpr (OP == OP_DERIV) {
       T* outs[3] = {p.out0, p.out1, p.out2};
+      constexpr int64_t KS = int64_t(DIM) * DIM * NQ;   // d eta_a / d x_m: block a d + m
       for (int w = tid; w < ne * NQ; w += nthr) {
         const int e = w / NQ, q = w - e * NQ;
-        const T* K = p.geom + (e0 + e) * DIM * DIM * NQ + q;   // d eta_a / d x_m, block a d + m
-        T d[DIM];
+        V d[DIM];
         d[0] = b.G0[w];
         d[1] = b.G1[w];
         if (DIM == 3) d[DIM - 1] = b.G2[w];
 #pragma unroll
         for (int m = 0; m < DIM; ++m) {
-          T acc = T(0);
+          V acc = vmul(vload(p.geom, KS, pm, e, int64_t(m) * NQ + q), d[0]);
 #pragma unroll
-          for (int a = 0; a < DIM; ++a) acc = fma(K[(a * DIM + m) * NQ], d[a], acc);
-          outs[m][(e0 + e) * NQ + q] = acc;
+          for (int a = 1; a < DIM; ++a) acc = vfma(vload(p.geom, KS, pm, e, int64_t(a * DIM + m) * NQ + q), d[a], acc);
+          vstore(outs[m], NQ, pm, e, q, acc);
         }
       }
       __syncthreads();
@@ -426,67 +513,68 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
     }
     if constexpr (OP == OP_HELM) {
       // pointwise: g_a = kappa sum_b G_ab d_b (into G0, G1, G2), V = lambda JW u
+      constexpr int64_t GS = int64_t(NFG) * NQ;
       for (int w = tid; w < ne * NQ; w += nthr) {
         const int e = w / NQ, q = w - e * NQ;
-        const T* G = p.geom + (e0 + e) * NFG * NQ + q;
-        const T kk = p.kap_f ? p.kap_f[(e0 + e) * NQ + q] : T(1);
-        const T ll = p.lam_f ? p.lam_f[(e0 + e) * NQ + q] : static_cast<T>(p.lam);
+        auto g = [&](int f) { return vload(p.geom, GS, pm, e, int64_t(f) * NQ + q); };
+        const V kk = p.kap_f ? vload(p.kap_f, NQ, pm, e, q) : vfill<V>(1.0);
+        const V ll = p.lam_f ? vload(p.lam_f, NQ, pm, e, q) : vfill<V>(p.lam);
         if constexpr (DIM == 2) {
-          const T d0 = b.G0[w], d1 = b.G1[w];
-          const T g00 = G[0], g01 = G[NQ], g11 = G[2 * NQ], jw = G[3 * NQ];
-          b.G0[w] = kk * fma(g01, d1, g00 * d0);
-          b.G1[w] = kk * fma(g11, d1, g01 * d0);
-          b.V[w] = ll * jw * b.U[w];
+          const V d0 = b.G0[w], d1 = b.G1[w];
+          const V g00 = g(0), g01 = g(1), g11 = g(2), jw = g(3);
+          b.G0[w] = vmul(kk, vfma(g01, d1, vmul(g00, d0)));
+          b.G1[w] = vmul(kk, vfma(g11, d1, vmul(g01, d0)));
+          b.Vb[w] = vmul(vmul(ll, jw), b.U[w]);
         } else {
-          const T d0 = b.G0[w], d1 = b.G1[w], d2 = b.G2[w];
-          const T g00 = G[0], g01 = G[NQ], g02 = G[2 * NQ], g11 = G[3 * NQ], g12 = G[4 * NQ], g22 = G[5 * NQ];
-          const T jw = G[6 * NQ];
-          b.G0[w] = kk * fma(g02, d2, fma(g01, d1, g00 * d0));
-          b.G1[w] = kk * fma(g12, d2, fma(g11, d1, g01 * d0));
-          b.G2[w] = kk * fma(g22, d2, fma(g12, d1, g02 * d0));
-          b.V[w] = ll * jw * b.U[w];
+          const V d0 = b.G0[w], d1 = b.G1[w], d2 = b.G2[w];
+          const V g00 = g(0), g01 = g(1), g02 = g(2), g11 = g(3), g12 = g(4), g22 = g(5), jw = g(6);
+          b.G0[w] = vmul(kk, vfma(g02, d2, vfma(g01, d1, vmul(g00, d0))));
+          b.G1[w] = vmul(kk, vfma(g12, d2, vfma(g11, d1, vmul(g01, d0))));
+          b.G2[w] = vmul(kk, vfma(g22, d2, vfma(g12, d1, vmul(g02, d0))));
+          b.Vb[w] = vmul(vmul(ll, jw), b.U[w]);
         }
       }
       __syncthreads();
       // transposed gradient added to V
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, Q, true, true>(b.G0, b.V, tD1, ne, tid, nthr, NQ, 0);
+        stage_dense<0, Q, Q, 1, Q, true, true>(b.G0, b.Vb, tD1, ne, tid, nthr);
         __syncthreads();
-        stage_dense<1, Q, Q, 1, Q, true, true>(b.G1, b.V, tD2, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, 1, Q, true, true>(b.G1, b.Vb, tD2, ne, tid, nthr);
       } else {
-        stage_dense<0, Q, Q, Q, Q, true, true>(b.G0, b.V, tD1, ne, tid, nthr, NQ, 0);
+        stage_dense<0, Q, Q, Q, Q, true, true>(b.G0, b.Vb, tD1, ne, tid, nthr);
         __syncthreads();
-        stage_dense<1, Q, Q, Q, Q, true, true>(b.G1, b.V, SHAPE == kTet ? tD2 : tD1, ne, tid, nthr, NQ, 0);
+        stage_dense<1, Q, Q, Q, Q, true, true>(b.G1, b.Vb, SHAPE == kTet ? tD2 : tD1, ne, tid, nthr);
         __syncthreads();
-        stage_dense<2, Q, Q, Q, Q, true, true>(b.G2, b.V, tD2, ne, tid, nthr, NQ, 0);
+        stage_dense<2, Q, Q, Q, Q, true, true>(b.G2, b.Vb, tD2, ne, tid, nthr);
       }
       __syncthreads();
     }
     if constexpr (OP == OP_IPROD) {
+      constexpr int64_t GS = int64_t(NFG) * NQ;
       for (int w = tid; w < ne * NQ; w += nthr) {
         const int e = w / NQ, q = w - e * NQ;
-        b.V[w] *= p.geom[(e0 + e) * NFG * NQ + (NFG - 1) * NQ + q];
+        b.Vb[w] = vmul(b.Vb[w], vload(p.geom, GS, pm, e, int64_t(NFG - 1) * NQ + q));
       }
       __syncthreads();
     }
     if constexpr (OP == OP_IPROD || OP == OP_HELM) {
       // transposed tensor directions, then the collapsed direction -> HBM
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, n, true, false>(b.V, b.F, tB1, ne, tid, nthr, n * Q, 0);   // F[p][k]
+        stage_dense<0, Q, Q, 1, n, true, false>(b.Vb, b.F, tB1, ne, tid, nthr);   // F[p][k]
         __syncthreads();
-        stage_b_bwd<T, P, 1>(b.F, p.out0, e0, b.Bb, ne, tid, nthr);
+        stage_b_bwd<T, V, P, 1>(b.F, p.out0, pm, b.Bb, ne, tid, nthr);
       } else if constexpr (SHAPE == kTet) {
-        stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, tB1, ne, tid, nthr, n * Q * Q, 0);  // H[p][j][k3]
+        stage_dense<0, Q, Q, Q, n, true, false>(b.Vb, b.H, tB1, ne, tid, nthr);   // H[p][j][k3]
         __syncthreads();
-        stage_tb_bwd<T, P>(b.H, b.F, b.Bb, ne, tid, nthr);                                    // F[m][k3]
+        stage_tb_bwd<T, V, P>(b.H, b.F, b.Bb, ne, tid, nthr);   // F[m][k3]
         __syncthreads();
-        stage_c_bwd<T, P>(b.F, p.out0, e0, b.Bc, b.toff, b.tdeg, ne, tid, nthr);
+        stage_c_bwd<T, V, P>(b.F, p.out0, pm, b.Bc, b.toff, b.tdeg, ne, tid, nthr);
       } else {
-        stage_dense<0, Q, Q, Q, n, true, false>(b.V, b.H, tB1, ne, tid, nthr, n * Q * Q, 0);  // H[a][j][k]
+        stage_dense<0, Q, Q, Q, n, true, false>(b.Vb, b.H, tB1, ne, tid, nthr);   // H[a][j][k]
         __syncthreads();
-        stage_dense<1, n, Q, Q, n, true, false>(b.H, b.F, tB1, ne, tid, nthr, n * n * Q, 0);  // F[a][p][k]
+        stage_dense<1, n, Q, Q, n, true, false>(b.H, b.F, tB1, ne, tid, nthr);   // F[a][p][k]
         __syncthreads();
-        stage_b_bwd<T, P, n>(b.F, p.out0, e0, b.Bb, ne, tid, nthr);
+        stage_b_bwd<T, V, P, n>(b.F, p.out0, pm, b.Bb, ne, tid, nthr);
       }
     }
     __syncthreads();   // the tile's buffers are reused by the next tile
@@ -506,7 +594,9 @@ namespace spx {
 template <typename T, int SHAPE, int P>
 size_t collapsed_smem_t(int eb) {
   using L = CLayout<SHAPE, P>;
-  return size_t(L::tables + eb * L::per_elem) * sizeof(T);
+  constexpr int LN = sizeof(T) == 4 ? 2 : 1;   // FP32: buffers of element pairs (float2)
+  const int npe = (eb + LN - 1) / LN;
+  return size_t(((L::tables + 1) & ~1) + npe * LN * L::per_elem) * sizeof(T);
 }
 
 #if defined(SPX_CT)

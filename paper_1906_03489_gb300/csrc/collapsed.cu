@@ -27,9 +27,11 @@
 //
 // One kernel per (shape, operator, order, precision): a CTA walks tiles of
 // consecutive elements; the basis tables are copied to shared memory once per
-// CTA (they are indexed with run-time mode indices); inputs are loaded with
-// coalesced reads, every stage is a loop of independent work items over the
-// tile's elements, outputs are stored straight to HBM.
+// CTA (the collapsed-direction stages index them with run-time mode indices);
+// inputs are loaded with coalesced reads, every stage is a loop of independent
+// work items over the tile's elements (the dense tensor-direction stages one
+// thread per pencil), outputs are stored straight to HBM.  FP32 kernels hold
+// two elements per value (float2, FFMA2), FP64 kernels one.
 #include <algorithm>
 #include <mutex>
 #include <type_traits>

@@ -256,7 +256,10 @@ spx_status spx_plan_set_geometry(spx_plan *plan, spx_dtype dtype, const void *ge
  *  - FP32 3D Helmholtz (element-pair kernel): ceil(eb / 2) * Q^2 threads;
  *    there `nthreads` (32..1024) is the number of threads per SM that the
  *    register budget must allow (<= 512: 128 registers per thread, <= 640:
- *    96, else 80) and `stages` (0..4) the L2 prefetch distance in tiles;
+ *    96, else 80) and `stages` (0..4) the L2 prefetch distance in tiles.  In
+ *    a variable-order plan (one kernel at 128 registers, orders above the
+ *    threshold one element per thread) `nthreads` picks the highest order
+ *    run two elements per thread instead: <= 512: 5, <= 640: 6, else 8;
  *  - FP32 3D BwdTrans and IProductWRTBase of a uniform-order plan with the
  *    modified basis (the same element-pair layout): ceil(eb / 2) * Q^2
  *    threads, `nthreads` (32..2048) the threads per SM of the register budget

@@ -88,8 +88,17 @@ struct CLayout {
   // after the first (collapsed-direction) stage: tri [p][k], prism [a][p][k], tet [m][k3]
   static constexpr int NF = SHAPE == kTri ? n * Q : (SHAPE == kPrism ? n * n * Q : nt * Q);
   static constexpr int NH = SHAPE == kTri ? 0 : n * Q * Q;       // after the second stage
+  // the buffers of quadrature-point values (U, G0, G1, G2, V) hold rows along
+  // eta1 of QP >= Q values.  Triangles take QP odd: pencils along eta1 then
+  // start in distinct shared-memory banks (a row of an even Q puts them 2Q
+  // words apart).  Measured (FP32, P = 4): triangles 0.0168 -> 0.0150 ms;
+  // prisms the same and tetrahedra slower (the larger buffers cost tiles), so
+  // they keep QP = Q.
+  static constexpr int QP = (SHAPE != kTri || Q % 2) ? Q : Q + 1;
+  static constexpr int NQP = SHAPE == kTri ? QP * Q : QP * Q * Q;
+  __host__ __device__ static constexpr int sq(int q) { return q % Q + QP * (q / Q); }   // point q in a buffer
   // buffers: C (modes), F, H, U, G0, G1, G2, V
-  static constexpr int per_elem = NM + NF + NH + 5 * NQ;
+  static constexpr int per_elem = NM + NF + NH + 5 * NQP;
   // tables: B1, Bb, Bc, D1, D2 (values of T), then the tet mode tables (ints, rounded up)
   static constexpr int tables = Q * n + 2 * n * Q * n + 2 * Q * Q + (2 * nt + 2);
 };
@@ -179,10 +188,10 @@ struct Bufs {
     F = C + npe * L::NM;
     H = F + npe * L::NF;
     U = H + npe * L::NH;
-    G0 = U + npe * L::NQ;
-    G1 = G0 + npe * L::NQ;
-    G2 = G1 + npe * L::NQ;
-    Vb = G2 + npe * L::NQ;
+    G0 = U + npe * L::NQP;
+    G1 = G0 + npe * L::NQP;
+    G2 = G1 + npe * L::NQP;
+    Vb = G2 + npe * L::NQP;
   }
 };
 
@@ -343,24 +352,27 @@ __device__ __forceinline__ void stage_c_bwd(const V* F, T* out, const PairMap& p
 // the FP64 pipe; constant-bank FP64 operands made the compiler hold many
 // table values in registers and spill).  OUT_G: y is the operator's output in
 // global memory, written through the pair map.
-template <int AX, int N0, int N1, int N2, int M, bool TR, bool ACC, bool OUT_G = false, typename T, typename V,
-          typename Y>
+// X0, Y0: the row strides (axis-0 extents as stored) of x and y, at least
+// N0 and the output's axis-0 extent (padded buffers, CLayout::QP).
+template <int AX, int N0, int N1, int N2, int M, bool TR, bool ACC, bool OUT_G = false, int X0 = N0,
+          int Y0 = (AX == 0 ? M : N0), typename T, typename V, typename Y>
 __device__ __forceinline__ void stage_dense(const V* x, Y* y, const T* A, int ne, int tid, int nthr,
                                             const PairMap* pm = nullptr) {
   constexpr int NA = AX == 0 ? N0 : (AX == 1 ? N1 : N2);
   constexpr int O0 = AX == 0 ? M : N0, O1 = AX == 1 ? M : N1, O2 = AX == 2 ? M : N2;
-  constexpr int XS = N0 * N1 * N2, YS = O0 * O1 * O2;
-  constexpr int SA = AX == 0 ? 1 : (AX == 1 ? N0 : N0 * N1);
-  constexpr int SO = AX == 0 ? 1 : (AX == 1 ? O0 : O0 * O1);
-  constexpr int NP = XS / NA;   // pencils per element
+  static_assert(X0 >= N0 && Y0 >= O0 && (!OUT_G || Y0 == O0), "row strides");
+  constexpr int XS = X0 * N1 * N2, YS = Y0 * O1 * O2;
+  constexpr int SA = AX == 0 ? 1 : (AX == 1 ? X0 : X0 * N1);
+  constexpr int SO = AX == 0 ? 1 : (AX == 1 ? Y0 : Y0 * O1);
+  constexpr int NP = N0 * N1 * N2 / NA;   // pencils per element
   for (int w = tid; w < ne * NP; w += nthr) {
     const int e = w / NP, r = w - e * NP;
     // the pencil's two other coordinates (the same extents in x and y), fastest first
     const int i0 = AX == 0 ? 0 : r % N0;
     const int i1 = AX == 1 ? 0 : (AX == 0 ? r % N1 : (r / N0) % N1);
     const int i2 = AX == 2 ? 0 : (AX == 0 ? r / N1 : r / N0);
-    const V* xe = x + e * XS + i0 + N0 * (i1 + N1 * i2);
-    const int yo = i0 + O0 * (i1 + O1 * i2);
+    const V* xe = x + e * XS + i0 + X0 * (i1 + N1 * i2);
+    const int yo = i0 + Y0 * (i1 + O1 * i2);
     V v[NA];
 #pragma unroll
     for (int c = 0; c < NA; ++c) v[c] = xe[c * SA];
@@ -393,6 +405,15 @@ __device__ __forceinline__ void stage_dense(const V* x, Y* y, const T* A, int ne
   }
 }
 
+// a tile's quadrature-point values (NQ per element) into a padded buffer
+template <typename T, typename V, int Q, int QP>
+__device__ __forceinline__ void load_tile_q(const T* g, V* s, int NQ, int NQP, const PairMap& pm) {
+  for (int i = threadIdx.x; i < pm.npair * NQ; i += blockDim.x) {
+    const int e = i / NQ, q = i - e * NQ;
+    s[e * NQP + q % Q + QP * (q / Q)] = vload(g, NQ, pm, e, q);
+  }
+}
+
 // a tile's inputs (len values per element, consecutive elements) into the
 // (pair-)element buffer s
 template <typename T, typename V>
@@ -410,7 +431,7 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
   using L = CLayout<SHAPE, P>;
   using V = typename ValueOf<T>::type;
   constexpr int LN = std::is_same_v<V, T> ? 1 : 2;   // elements per value
-  constexpr int n = L::n, Q = L::Q, nt = L::nt, NQ = L::NQ, NM = L::NM;
+  constexpr int n = L::n, Q = L::Q, nt = L::nt, NQ = L::NQ, NM = L::NM, QP = L::QP, NQP = L::NQP;
   constexpr int DIM = SHAPE == kTri ? 2 : 3;
   constexpr int NFG = DIM == 3 ? 7 : 4;
   extern __shared__ __align__(16) unsigned char csm[];
@@ -460,36 +481,37 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
         stage_b_fwd<T, V, P, 1>(b.C, b.F, b.Bb, ne, tid, nthr);
         __syncthreads();
         if constexpr (G) stage_dense<0, n, Q, 1, Q, false, false, true>(b.F, p.out0, tB1, ne, tid, nthr, &pm);
-        else stage_dense<0, n, Q, 1, Q, false, false>(b.F, b.U, tB1, ne, tid, nthr);   // F[p][j] -> u[i][j]
+        else stage_dense<0, n, Q, 1, Q, false, false, false, n, QP>(b.F, b.U, tB1, ne, tid, nthr);   // u[i][j]
       } else if constexpr (SHAPE == kTet) {
         stage_c_fwd<T, V, P>(b.C, b.F, b.Bc, b.toff, b.tdeg, ne, tid, nthr);   // F[m][k3]
         __syncthreads();
         stage_tb_fwd<T, V, P>(b.F, b.H, b.Bb, ne, tid, nthr);   // H[p][j][k3]
         __syncthreads();
         if constexpr (G) stage_dense<0, n, Q, Q, Q, false, false, true>(b.H, p.out0, tB1, ne, tid, nthr, &pm);
-        else stage_dense<0, n, Q, Q, Q, false, false>(b.H, b.U, tB1, ne, tid, nthr);   // u[i][j][k3]
+        else stage_dense<0, n, Q, Q, Q, false, false, false, n, QP>(b.H, b.U, tB1, ne, tid, nthr);   // u[i][j][k3]
       } else {
         stage_b_fwd<T, V, P, n>(b.C, b.F, b.Bb, ne, tid, nthr);   // F[a][p][k]
         __syncthreads();
         stage_dense<1, n, n, Q, Q, false, false>(b.F, b.H, tB1, ne, tid, nthr);   // H[a][j][k]
         __syncthreads();
         if constexpr (G) stage_dense<0, n, Q, Q, Q, false, false, true>(b.H, p.out0, tB1, ne, tid, nthr, &pm);
-        else stage_dense<0, n, Q, Q, Q, false, false>(b.H, b.U, tB1, ne, tid, nthr);   // u[i][j][k]
+        else stage_dense<0, n, Q, Q, Q, false, false, false, n, QP>(b.H, b.U, tB1, ne, tid, nthr);   // u[i][j][k]
       }
       __syncthreads();
     } else {
-      load_tile(p.in0, OP == OP_DERIV ? b.U : b.Vb, NQ, pm);
+      load_tile_q<T, V, Q, QP>(p.in0, OP == OP_DERIV ? b.U : b.Vb, NQ, NQP, pm);
       __syncthreads();
     }
     if constexpr (OP == OP_DERIV || OP == OP_HELM) {
       // gradient along the collapsed directions: G0, G1 (, G2)
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, Q, false, false>(b.U, b.G0, tD1, ne, tid, nthr);
-        stage_dense<1, Q, Q, 1, Q, false, false>(b.U, b.G1, tD2, ne, tid, nthr);
+        stage_dense<0, Q, Q, 1, Q, false, false, false, QP, QP>(b.U, b.G0, tD1, ne, tid, nthr);
+        stage_dense<1, Q, Q, 1, Q, false, false, false, QP, QP>(b.U, b.G1, tD2, ne, tid, nthr);
       } else {   // eta2 on GLL points (prism) or Gauss-Radau points (tetrahedron)
-        stage_dense<0, Q, Q, Q, Q, false, false>(b.U, b.G0, tD1, ne, tid, nthr);
-        stage_dense<1, Q, Q, Q, Q, false, false>(b.U, b.G1, SHAPE == kTet ? tD2 : tD1, ne, tid, nthr);
-        stage_dense<2, Q, Q, Q, Q, false, false>(b.U, b.G2, tD2, ne, tid, nthr);
+        stage_dense<0, Q, Q, Q, Q, false, false, false, QP, QP>(b.U, b.G0, tD1, ne, tid, nthr);
+        stage_dense<1, Q, Q, Q, Q, false, false, false, QP, QP>(b.U, b.G1, SHAPE == kTet ? tD2 : tD1, ne, tid,
+                                                                nthr);
+        stage_dense<2, Q, Q, Q, Q, false, false, false, QP, QP>(b.U, b.G2, tD2, ne, tid, nthr);
       }
       __syncthreads();
     }
@@ -497,11 +519,11 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
       T* outs[3] = {p.out0, p.out1, p.out2};
       constexpr int64_t KS = int64_t(DIM) * DIM * NQ;   // d eta_a / d x_m: block a d + m
       for (int w = tid; w < ne * NQ; w += nthr) {
-        const int e = w / NQ, q = w - e * NQ;
+        const int e = w / NQ, q = w - e * NQ, sw = e * NQP + L::sq(q);
         V d[DIM];
-        d[0] = b.G0[w];
-        d[1] = b.G1[w];
-        if (DIM == 3) d[DIM - 1] = b.G2[w];
+        d[0] = b.G0[sw];
+        d[1] = b.G1[sw];
+        if (DIM == 3) d[DIM - 1] = b.G2[sw];
 #pragma unroll
         for (int m = 0; m < DIM; ++m) {
           V acc = vmul(vload(p.geom, KS, pm, e, int64_t(m) * NQ + q), d[0]);
@@ -516,8 +538,8 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
     if constexpr (OP == OP_HELM) {
       // pointwise: g_a = kappa sum_b G_ab d_b (into G0, G1, G2), V = lambda JW u
       constexpr int64_t GS = int64_t(NFG) * NQ;
-      for (int w = tid; w < ne * NQ; w += nthr) {
-        const int e = w / NQ, q = w - e * NQ;
+      for (int w0 = tid; w0 < ne * NQ; w0 += nthr) {
+        const int e = w0 / NQ, q = w0 - e * NQ, w = e * NQP + L::sq(q);
         auto g = [&](int f) { return vload(p.geom, GS, pm, e, int64_t(f) * NQ + q); };
         const V kk = p.kap_f ? vload(p.kap_f, NQ, pm, e, q) : vfill<V>(1.0);
         const V ll = p.lam_f ? vload(p.lam_f, NQ, pm, e, q) : vfill<V>(p.lam);
@@ -539,40 +561,41 @@ __global__ void __launch_bounds__(512) collapsed_kernel(const __grid_constant__ 
       __syncthreads();
       // transposed gradient added to V
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, Q, true, true>(b.G0, b.Vb, tD1, ne, tid, nthr);
+        stage_dense<0, Q, Q, 1, Q, true, true, false, QP, QP>(b.G0, b.Vb, tD1, ne, tid, nthr);
         __syncthreads();
-        stage_dense<1, Q, Q, 1, Q, true, true>(b.G1, b.Vb, tD2, ne, tid, nthr);
+        stage_dense<1, Q, Q, 1, Q, true, true, false, QP, QP>(b.G1, b.Vb, tD2, ne, tid, nthr);
       } else {
-        stage_dense<0, Q, Q, Q, Q, true, true>(b.G0, b.Vb, tD1, ne, tid, nthr);
+        stage_dense<0, Q, Q, Q, Q, true, true, false, QP, QP>(b.G0, b.Vb, tD1, ne, tid, nthr);
         __syncthreads();
-        stage_dense<1, Q, Q, Q, Q, true, true>(b.G1, b.Vb, SHAPE == kTet ? tD2 : tD1, ne, tid, nthr);
+        stage_dense<1, Q, Q, Q, Q, true, true, false, QP, QP>(b.G1, b.Vb, SHAPE == kTet ? tD2 : tD1, ne, tid,
+                                                              nthr);
         __syncthreads();
-        stage_dense<2, Q, Q, Q, Q, true, true>(b.G2, b.Vb, tD2, ne, tid, nthr);
+        stage_dense<2, Q, Q, Q, Q, true, true, false, QP, QP>(b.G2, b.Vb, tD2, ne, tid, nthr);
       }
       __syncthreads();
     }
     if constexpr (OP == OP_IPROD) {
       constexpr int64_t GS = int64_t(NFG) * NQ;
       for (int w = tid; w < ne * NQ; w += nthr) {
-        const int e = w / NQ, q = w - e * NQ;
-        b.Vb[w] = vmul(b.Vb[w], vload(p.geom, GS, pm, e, int64_t(NFG - 1) * NQ + q));
+        const int e = w / NQ, q = w - e * NQ, sw = e * NQP + L::sq(q);
+        b.Vb[sw] = vmul(b.Vb[sw], vload(p.geom, GS, pm, e, int64_t(NFG - 1) * NQ + q));
       }
       __syncthreads();
     }
     if constexpr (OP == OP_IPROD || OP == OP_HELM) {
       // transposed tensor directions, then the collapsed direction -> HBM
       if constexpr (SHAPE == kTri) {
-        stage_dense<0, Q, Q, 1, n, true, false>(b.Vb, b.F, tB1, ne, tid, nthr);   // F[p][k]
+        stage_dense<0, Q, Q, 1, n, true, false, false, QP>(b.Vb, b.F, tB1, ne, tid, nthr);   // F[p][k]
         __syncthreads();
         stage_b_bwd<T, V, P, 1>(b.F, p.out0, pm, b.Bb, ne, tid, nthr);
       } else if constexpr (SHAPE == kTet) {
-        stage_dense<0, Q, Q, Q, n, true, false>(b.Vb, b.H, tB1, ne, tid, nthr);   // H[p][j][k3]
+        stage_dense<0, Q, Q, Q, n, true, false, false, QP>(b.Vb, b.H, tB1, ne, tid, nthr);   // H[p][j][k3]
         __syncthreads();
         stage_tb_bwd<T, V, P>(b.H, b.F, b.Bb, ne, tid, nthr);   // F[m][k3]
         __syncthreads();
         stage_c_bwd<T, V, P>(b.F, p.out0, pm, b.Bc, b.toff, b.tdeg, ne, tid, nthr);
       } else {
-        stage_dense<0, Q, Q, Q, n, true, false>(b.Vb, b.H, tB1, ne, tid, nthr);   // H[a][j][k]
+        stage_dense<0, Q, Q, Q, n, true, false, false, QP>(b.Vb, b.H, tB1, ne, tid, nthr);   // H[a][j][k]
         __syncthreads();
         stage_dense<1, n, Q, Q, n, true, false>(b.H, b.F, tB1, ne, tid, nthr);   // F[a][p][k]
         __syncthreads();

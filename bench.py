@@ -754,6 +754,27 @@ def measure_nodal(spx, mesh, synth, torch, stream, hbm_peak, fp64_peak, fp32_pea
         r["gdofs"] = round(plan.n_coef / ms / 1e6, 3)
         r["tile_eb_threads_stages"] = list(plan.get_tile("helmholtz", dt, P))
         out["f64" if fp64 else "f32"] = r
+    del plan, g
+    # the same basis on Q = P + 2 points: no parity of the modified basis, no
+    # collocation, so the library's generic body (direct 1D contractions)
+    Q2 = P + 2
+    plan = spx.Plan(3, N ** 3, order=P, q_offset=2, basis={P: spx.nodal_basis_tables(P, Q2)})
+    g = spx.geom_factors(plan, mesh.structured_nodes(3, N, P, w["amp"]), want_xq=False)
+    plan.set_geometry(torch.float64, g["geom"], g["dxi"])
+    plan.set_geometry(torch.float32, g["geom32"], g["dxi32"])
+    gen = {"Q": Q2, "body": "generic (any caller basis without the modified basis's parity)"}
+    for dt, sz in ((torch.float64, 8), (torch.float32, 4)):
+        u = torch.tensor(coef, device="cuda", dtype=dt)
+        y = torch.empty_like(u)
+        plan.autotune("helmholtz", dt, u, y, reps=3)
+        ms = timed(lambda: spx.helmholtz(plan, u, out=y), 30, stream)
+        fp64 = dt == torch.float64
+        r = roof(ms, E * (2 * (P + 1) ** 3 + 7 * Q2 ** 3) * sz, E * helm_flops_per_elem(P, Q2), fp64, hbm_peak,
+                 fp64_peak if fp64 else fp32_peak)
+        r["gdofs"] = round(plan.n_coef / ms / 1e6, 3)
+        r["tile_eb_threads_stages"] = list(plan.get_tile("helmholtz", dt, P))
+        gen["f64" if fp64 else "f32"] = r
+    out["q_plus_2_generic"] = gen
     return out
 
 

@@ -815,10 +815,24 @@ def measure_collapsed(spx, mesh, synth, torch, stream, hbm_peak, fp64_peak, fp32
             u = torch.tensor(coef, device="cuda", dtype=dt)
             y = torch.empty_like(u)
             plan.autotune("helmholtz", dt, u, y, reps=3)
-            ms = timed(lambda: spx.helmholtz(plan, u, out=y), 30, stream)
             fp64 = dt == torch.float64
-            r = roof(ms, E * (2 * nm + (7 if d == 3 else 4) * Q ** d) * sz, E * collapsed_flops_per_elem(shape, P),
-                     fp64, hbm_peak, fp64_peak if fp64 else fp32_peak)
+            nbytes = E * (2 * nm + (7 if d == 3 else 4) * Q ** d) * sz
+            # k copies of the operands and geometric factors (> 2 x L2), launched in turn from a CUDA graph
+            k = max(2, -(-2 * L2_BYTES // nbytes))
+            gk = ("geom", "dxi") if fp64 else ("geom32", "dxi32")
+            us = [u.clone() for _ in range(k)]
+            ys = [torch.empty_like(u) for _ in range(k)]
+            geos = [(g[gk[0]].clone(), g[gk[1]].clone()) for _ in range(k)]
+
+            def call(i, us=us, ys=ys, geos=geos, dt=dt):
+                plan.set_geometry(dt, *geos[i])
+                spx.helmholtz(plan, us[i], out=ys[i])
+            ms = timed_rotating(torch, call, k, 60, stream)
+            plan.set_geometry(dt, g[gk[0]], g[gk[1]])
+            del us, ys, geos
+            r = roof(ms, nbytes, E * collapsed_flops_per_elem(shape, P), fp64, hbm_peak,
+                     fp64_peak if fp64 else fp32_peak)
+            r["timing"] = f"{k} copies of the operands launched in turn from a CUDA graph"
             r["gdofs"] = round(plan.n_coef / ms / 1e6, 3)
             r["tile_eb_threads_stages"] = list(plan.get_tile("helmholtz", dt, P))
             rec["f64" if fp64 else "f32"] = r
